@@ -1,0 +1,124 @@
+"""Pins for the oracle's sparse convolutions, networks and gradients (CPU only).
+
+Sparse SubM3 / down2 / up2 equal the library's dense conv3d / conv_transpose3d on the zero-filled
+grid, read at the active sites (the masked-dense definition, Sec. 2.3); SubM3 also equals a direct
+loop; the analytic gradients equal central finite differences in float64.
+"""
+import itertools
+
+import numpy as np
+import pytest
+import torch
+import torch.nn.functional as F
+
+import npvs_inputs as I
+from oracle import network as N
+
+torch.set_default_dtype(torch.float64)
+
+
+def random_level(rng, dims, frac):
+    B, Dz, Hy, Wx = dims
+    m = rng.random(dims) < frac
+    m[0, 0, 0, 0] = True
+    return N.Level(np.argwhere(m), dims), m
+
+
+def dense_of(level, x):
+    B, Dz, Hy, Wx = level.dims
+    g = torch.zeros(B, x.shape[1], Dz, Hy, Wx)
+    c = level.coords
+    g[c[:, 0], :, c[:, 1], c[:, 2], c[:, 3]] = x
+    return g
+
+
+def test_subm3_equals_masked_conv3d_and_loops():
+    rng = np.random.default_rng(0)
+    lv, _ = random_level(rng, (2, 4, 5, 6), 0.3)
+    cin, cout = 3, 5
+    x = torch.tensor(rng.normal(size=(lv.n, cin)))
+    W = torch.tensor(rng.normal(size=(27, cin, cout)))
+    b = torch.tensor(rng.normal(size=cout))
+    y = N.subm3(lv, x, W, b)
+    wt = W.reshape(3, 3, 3, cin, cout).permute(4, 3, 0, 1, 2)     # out, in, kz, ky, kx
+    ref = F.conv3d(dense_of(lv, x), wt, b, padding=1)
+    c = lv.coords
+    torch.testing.assert_close(y, ref[c[:, 0], :, c[:, 1], c[:, 2], c[:, 3]], rtol=1e-12, atol=1e-12)
+    # direct loops on a few sites
+    pos = {tuple(cc.tolist()): i for i, cc in enumerate(c)}
+    for n in range(0, lv.n, max(1, lv.n // 7)):
+        bb, z, yy, xx = c[n].tolist()
+        acc = b.clone()
+        for k, (dz, dy, dx) in enumerate(itertools.product((-1, 0, 1), repeat=3)):
+            m = pos.get((bb, z + dz, yy + dy, xx + dx))
+            if m is not None:
+                acc = acc + x[m] @ W[k]
+        torch.testing.assert_close(y[n], acc, rtol=1e-12, atol=1e-12)
+
+
+def test_down2_and_up2_equal_strided_convs():
+    rng = np.random.default_rng(1)
+    fine, _ = random_level(rng, (2, 4, 6, 8), 0.25)
+    coarse = fine.parent()
+    cin, cout = 4, 3
+    x = torch.tensor(rng.normal(size=(fine.n, cin)))
+    W = torch.tensor(rng.normal(size=(8, cin, cout)))
+    b = torch.tensor(rng.normal(size=cout))
+    y = N.down2(fine, coarse, x, W, b)
+    wt = W.reshape(2, 2, 2, cin, cout).permute(4, 3, 0, 1, 2)
+    ref = F.conv3d(dense_of(fine, x), wt, b, stride=2)
+    P = coarse.coords
+    torch.testing.assert_close(y, ref[P[:, 0], :, P[:, 1], P[:, 2], P[:, 3]], rtol=1e-12, atol=1e-12)
+    # the parent set is exactly the set of floor(p / 2)
+    exp = sorted({(b_, z // 2, y_ // 2, x_ // 2) for b_, z, y_, x_ in fine.coords.tolist()})
+    assert [tuple(p) for p in P.tolist()] == exp
+    # up2: transposed conv onto the fine set
+    z = torch.tensor(rng.normal(size=(coarse.n, cout)))
+    Wu = torch.tensor(rng.normal(size=(8, cout, cin)))
+    bu = torch.tensor(rng.normal(size=cin))
+    yu = N.up2(coarse, fine, z, Wu, bu)
+    wtu = Wu.reshape(2, 2, 2, cout, cin).permute(3, 4, 0, 1, 2)   # in, out, kz, ky, kx
+    refu = F.conv_transpose3d(dense_of(coarse, z), wtu, bu, stride=2)
+    c = fine.coords
+    torch.testing.assert_close(yu, refu[c[:, 0], :, c[:, 1], c[:, 2], c[:, 3]], rtol=1e-12, atol=1e-12)
+
+
+def small_unet():
+    return I.unet_layers(8, [4, 6, 8], 8)
+
+
+@pytest.mark.parametrize("which", ["plain", "unet"])
+def test_gradients_match_central_differences(which):
+    rng = np.random.default_rng(2)
+    layers = I.plain_layers([8, 6, 5, 8]) if which == "plain" else small_unet()
+    n_levels = 1 if which == "plain" else 3
+    lv0, _ = random_level(rng, (1, 4, 8, 8), 0.3)
+    levels = [lv0]
+    for _ in range(n_levels - 1):
+        levels.append(levels[-1].parent())
+    ws, bs = I.kaiming_uniform(layers, seed=0, bias_scale=0.1)
+    W, B = N.to_torch_params(ws, bs, requires_grad=True)
+    x = torch.tensor(rng.random((lv0.n, 8)))
+    tgt = torch.tensor(rng.normal(size=(lv0.n, 8)))
+
+    def loss_fn():
+        return ((N.forward(layers, W, B, levels, x) - tgt) ** 2).sum()
+
+    L = loss_fn()
+    L.backward()
+    for li in range(len(layers)):
+        for P in (W[li], B[li]):
+            flat = P.detach().view(-1)
+            for idx in rng.choice(flat.numel(), size=min(4, flat.numel()), replace=False):
+                h = 1e-6 * max(1.0, abs(float(flat[idx])))
+                old = float(flat[idx])
+                with torch.no_grad():
+                    flat[idx] = old + h
+                    lp = float(loss_fn())
+                    flat[idx] = old - h
+                    lm = float(loss_fn())
+                    flat[idx] = old
+                fd = (lp - lm) / (2 * h)
+                g = float(P.grad.view(-1)[idx])
+                # central-difference rounding error ~ eps * L / h
+                assert abs(g - fd) <= 1e-5 * max(abs(g), abs(fd)) + 1e-8 * abs(float(L.detach())), (layers[li].name, g, fd)
