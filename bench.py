@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""NeuralPVS hot-path benchmark: PVS frames/s and ms/frame at 256x256x128 froxels on one GB300.
+
+A step is one frame of the whole per-frame path: frustum setup (host, precomputed per viewcell),
+froxelization of a 2,001-box procedural city (s = 8), interleave (d = 4, occupancy + depth ->
+128 channels), rulebooks of 4 levels, the sparse U-Net 32/64/128/256 (BF16 tensor cores, FP32
+accumulation), de-interleave + sigmoid + threshold + G mask. Inputs (boxes, cameras) are resident
+in HBM; L2 is flushed between timed steps. `e2e` repeats the measurement through the public API
+with host buffers (box and camera upload, PVS bit download inside the timed region). The same
+line reports the plain FP32 path, the roofline of the dominant kernel and the FP64 CPU oracle.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent replica (the path has no exchange step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+import npvs_inputs as I  # noqa: E402
+
+METRIC = "PVS frames/s at 256x256x128 froxels (BF16 path)"
+WORKLOAD = "city256"
+N_VIEWCELLS = 8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        reasons = set()
+        for r in rows:
+            for name, v in (("hw_slowdown", r[5]), ("hw_thermal_slowdown", r[6]), ("sw_thermal_slowdown", r[7]),
+                            ("sw_power_cap", r[8])):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "samples": len(rows),
+                "reasons": sorted(reasons)}
+
+
+def layer_algorithmic(fp, wl):
+    """Per stage: (bytes, flops, bound) from the actual rulebooks of the last frame (SURVEY-style
+    algorithmic counts: each operand byte once, FLOPs = 2 * pairs * cin * cout)."""
+    out = {}
+    lv_of = fp._level_of_layers()
+    n = [int(lv.n_rows.item()) for lv in fp.levels]
+    b = 2 if fp.dtype == 1 else 4
+    for l in wl.layers:
+        li = lv_of[l.name]
+        if l.kind == "subm3":
+            nb = fp.levels[li].nbr[:n[li]]
+            pairs = int((nb >= 0).sum().item())
+            n_in = n_out = n[li]
+            taps = 27
+        elif l.kind == "down2":
+            pairs = n[li - 1]
+            n_in, n_out, taps = n[li - 1], n[li], 8
+        elif l.kind == "up2":
+            pairs = n[li]
+            n_in, n_out, taps = n[li + 1], n[li], 8
+        else:
+            pairs = n[li]
+            n_in = n_out = n[li]
+            taps = 1
+        ob = 4 if l.kind == "head1" else b
+        byts = n_in * l.cin * b + n_out * l.cout * ob + taps * l.cin * l.cout * b + 4 * taps * n_out
+        if l.kind == "up2":
+            byts += n_out * l.cout * b
+        out["conv:" + l.name] = dict(bytes=byts, flops=2 * pairs * l.cin * l.cout)
+    W, H, D = wl.W, wl.H, wl.D
+    out["interleave"] = dict(bytes=W * H * D // 8 + n[0] * (wl.feat_ch * b + 16), flops=0)
+    out["deinterleave"] = dict(bytes=n[0] * wl.d ** 3 * 4 + 2 * W * H * D // 8, flops=0)
+    tot = sum(n)
+    out["rulebooks"] = dict(bytes=16 * tot + 8 * tot + 27 * 8 * tot + 4 * 27 * tot, flops=0)
+    return out
+
+
+def make_frame_inputs(device):
+    from paper_2509_24677_gb300 import ops
+    wl = I.workload(WORKLOAD)
+    boxes = I.city_boxes(0)
+    vcs = I.city_viewcells(0, N_VIEWCELLS)
+    cams = [ops.npvs_camera_setup(v, wl.D) for v in vcs]
+    return wl, boxes, vcs, cams
+
+
+def cpu_oracle_frame_estimate(budget_s: float):
+    """Times the FP64 oracle on a bounded sample of one frame of the same workload: the
+    froxelization of a random sample of froxel columns (scaled to the whole grid) plus interleave,
+    network and de-interleave of the full frame (on G from a one-ray-per-column raster). Returns
+    (ms per frame, description, cores)."""
+    from oracle import camera as ocam
+    from oracle import froxel as ofx
+    from oracle import interleave as oil
+    from oracle import network as onet
+    wl = I.workload(WORKLOAD)
+    boxes = I.city_boxes(0)
+    vc = I.city_viewcells(0, 1)[0]
+    cam = ocam.frustum(vc, wl.D)
+    ws, bs = I.kaiming_uniform(wl.layers, seed=0)
+    W_, B_ = onet.to_torch_params(ws, bs)
+    rng = np.random.default_rng(0)
+    t0 = time.perf_counter()
+    G1 = ofx.froxelize(cam, boxes, wl.W, wl.H, wl.D, 1)[None]
+    coords, feats, _ = oil.interleave(G1, wl.W, wl.d, wl.in_ch)
+    levels = onet.build_levels(coords, (1, wl.D // wl.d, wl.H // wl.d, wl.W // wl.d), 4)
+    with torch.no_grad():
+        logits = onet.forward(list(wl.layers), W_, B_, levels, torch.tensor(feats)).numpy()
+    oil.pvs_from_logits(coords, logits, G1, wl.W, wl.d)
+    t_rest = time.perf_counter() - t0
+    # froxel columns at full supersampling, sized to the remaining budget
+    probe = 256
+    cols = np.stack([rng.integers(0, wl.W, probe), rng.integers(0, wl.H, probe)], 1)
+    t0 = time.perf_counter()
+    ofx.froxel_columns(cam, boxes, wl.W, wl.H, wl.D, wl.supersample, cols)
+    per_col = (time.perf_counter() - t0) / probe
+    n_cols = int(max(probe, min(wl.W * wl.H, (budget_s - t_rest) / max(per_col, 1e-9))))
+    cols = np.stack([rng.integers(0, wl.W, n_cols), rng.integers(0, wl.H, n_cols)], 1)
+    t0 = time.perf_counter()
+    ofx.froxel_columns(cam, boxes, wl.W, wl.H, wl.D, wl.supersample, cols)
+    t_cols = time.perf_counter() - t0
+    ms = 1e3 * (t_cols * (wl.W * wl.H) / n_cols + t_rest)
+    desc = (f"FP64/binary32-mirror oracle: froxelization of {n_cols} of {wl.W * wl.H} froxel columns "
+            f"(s=8, scaled to the grid) + interleave, U-Net and de-interleave of one full frame")
+    return ms, desc, os.cpu_count(), t_cols + t_rest
+
+
+def run_reference(args):
+    ws_, rank, _ = dist_env()
+    if rank != 0:
+        return
+    steps = []
+    per_step = max(2.0, min(12.0, 150.0 / max(1, args.steps + args.warmup)))
+    for i in range(args.warmup + args.steps):
+        ms, desc, cores, _ = cpu_oracle_frame_estimate(per_step)
+        if i >= args.warmup:
+            steps.append(ms)
+    ms = statistics.mean(steps)
+    fps = 1000.0 / ms
+    line = {"impl": "reference", "metric": METRIC, "value": round(fps, 4), "unit": "frames/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "city256: 256x256x128 froxels, 2,001-box city seed 0, d=4, U-Net 32/64/128/256",
+                       "batch": 1},
+            "cpu_baseline": {"value": round(fps, 4), "unit": "frames/s", "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": round(fps, 4), "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    from paper_2509_24677_gb300 import _lib as L
+    from paper_2509_24677_gb300 import ops, pipeline as P
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+        torch.cuda.set_device(local)
+    else:
+        torch.cuda.set_device(0)
+    dev = f"cuda:{torch.cuda.current_device()}"
+    wl, boxes, vcs, cams = make_frame_inputs(dev)
+    ws, bs = I.kaiming_uniform(wl.layers, seed=0)
+    net = P.Net(wl.layers, ws, bs, dev)
+    boxes_d = torch.from_numpy(boxes).to(dev)
+    off_d = torch.tensor([0, len(boxes)], dtype=torch.int32, device=dev)
+    cams_d = [ops.cameras_to_device([c], dev) for c in cams]
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    hbm_gbs, tf_bf16, peak_src = load_peaks()
+
+    fp = P.FramePipeline(wl, net, 1, L.BF16, device=dev)
+    fp32 = P.FramePipeline(wl, net, 1, L.F32, device=dev)
+    cam_buf = torch.empty_like(cams_d[0])
+    cam_buf.copy_(cams_d[0])
+    # untimed first frames (lazy weight packing, kernel attributes), then one CUDA graph per path
+    for f in (fp, fp32):
+        f.run(boxes_d, off_d, cam_buf)
+        if ops.npvs_check_status(f.status) != 0:
+            raise RuntimeError("device status set on the first frame")
+    tuned = fp.autotune(boxes_d, off_d, cam_buf)     # per-layer kernel configuration (untimed)
+    l0 = ops.npvs_launch_count()
+    g16 = fp.capture(boxes_d, off_d, cam_buf)
+    launches_per_frame = (ops.npvs_launch_count() - l0) // 2      # warm-up run + captured run
+    g32 = fp32.capture(boxes_d, off_d, cam_buf)
+    timer = P.StageTimer()
+    g16t = fp.capture(boxes_d, off_d, cam_buf, timer=timer)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+
+    def timed_replays(graph, steps, warmup, per_step=None):
+        out = []
+        for i in range(warmup + steps):
+            flush.zero_()
+            cam_buf.copy_(cams_d[i % len(cams_d)])
+            s = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            s.record(st)
+            graph.replay()
+            e.record(st)
+            if per_step is not None:
+                torch.cuda.synchronize()
+                if i >= warmup:
+                    per_step()
+            if i >= warmup:
+                out.append((s, e))
+        torch.cuda.synchronize()
+        return [s.elapsed_time(e) for s, e in out]
+
+    # ---- device-timed BF16 frames (the headline) ----------------------------------------------
+    clocks = Clocks(torch.cuda.current_device())
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_bf16 = timed_replays(g16, args.steps, args.warmup)
+    clk = clocks.stop()
+    launches_timed = launches_per_frame * args.steps
+    ms = statistics.mean(t_bf16)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    if ops.npvs_check_status(fp.status) != 0:
+        raise RuntimeError("device status set during the timed frames")
+
+    # ---- per-stage times (stage events captured in a second graph of the same frame) ----------
+    acc = {}
+
+    def add_stage_times():
+        for k, v in timer.totals().items():
+            acc[k] = acc.get(k, 0.0) + v
+
+    timed_replays(g16t, args.steps, 2, add_stage_times)
+    stage_ms = {k: v / args.steps for k, v in acc.items()}
+
+    # ---- FP32 path, same inputs ------------------------------------------------------------------
+    t_f32 = timed_replays(g32, max(5, args.steps // 2), 2)
+    ms32 = statistics.mean(t_f32)
+
+    # ---- end to end through the public API with host buffers -------------------------------------
+    boxes_h = torch.from_numpy(boxes).pin_memory()
+    cams_h = [ops.cameras_to_device([c], "cpu").pin_memory() for c in cams]
+    pvs_h = torch.empty(fp.pvs.numel(), dtype=torch.int32).pin_memory()
+    ev = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(st)
+        boxes_d.copy_(boxes_h, non_blocking=True)
+        fp.frame_from_host(g16, cam_buf, cams_h[i % len(cams_h)], pvs_h)
+        e.record(st)
+        if i >= args.warmup:
+            ev.append((s, e))
+    torch.cuda.synchronize()
+    ms_e2e = statistics.mean(s.elapsed_time(e) for s, e in ev)
+    h2d = boxes_h.numel() * 4 + cams_h[0].numel()
+    d2h = pvs_h.numel() * 4
+
+    # ---- roofline of the dominant kernel ---------------------------------------------------------
+    alg = layer_algorithmic(fp, wl)
+    dom = max((k for k in stage_ms if k in alg), key=lambda k: stage_ms[k])
+    a = alg[dom]
+    t_s = stage_ms[dom] * 1e-3
+    t_tensor = a["flops"] / (tf_bf16 * 1e12)
+    t_hbm = a["bytes"] / (hbm_gbs * 1e9)
+    if t_tensor > t_hbm:
+        roof = {"bound": "tensor", "achieved": round(a["flops"] / t_s / 1e12, 3), "peak": tf_bf16, "unit": "TFLOP/s"}
+    else:
+        roof = {"bound": "hbm", "achieved": round(a["bytes"] / t_s / 1e9, 2), "peak": hbm_gbs, "unit": "GB/s"}
+    roof["frac"] = round(roof["achieved"] / roof["peak"], 5)
+    roof["traffic"] = None
+    roof["kernel"] = dom
+    roof["peak_source"] = peak_src
+    frame_bytes = sum(v["bytes"] for v in alg.values())
+    frame_flops = sum(v["flops"] for v in alg.values())
+    frame_roof_ms = max(frame_flops / (tf_bf16 * 1e12), frame_bytes / (hbm_gbs * 1e9)) * 1e3
+
+    line = {
+        "metric": METRIC, "value": round(world * 1000.0 / ms, 3), "unit": "frames/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "city256: 256x256x128 froxels (s=8), 2,001-box procedural city seed 0, "
+                               f"{N_VIEWCELLS} street viewcells cycled, d=4 (128 ch), sparse U-Net 32/64/128/256",
+                   "batch": 1, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "launch": "one CUDA graph replay per frame"},
+        "e2e": {"value": round(world * 1000.0 / ms_e2e, 3), "unit": "frames/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches_timed),
+        "launches_per_frame": int(launches_per_frame),
+        "fp32_path": {"ms_per_frame": round(ms32, 4), "frames_per_s": round(1000.0 / ms32, 3)},
+        "stage_ms": {k: round(v, 4) for k, v in sorted(stage_ms.items(), key=lambda kv: -kv[1])},
+        "roofline": roof,
+        "frame_roofline": {"bytes": frame_bytes, "flops": frame_flops, "roof_ms": round(frame_roof_ms, 5),
+                           "frac": round(frame_roof_ms / ms, 5)},
+        "active_sites": [int(lv.n_rows.item()) for lv in fp.levels],
+        "autotuned": {k: [v[0].get("tune_form", 0), round(v[1], 2)] for k, v in tuned.items()},
+    }
+    if clk:
+        line["clocks"] = clk
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cms, desc, cores, spent = cpu_oracle_frame_estimate(args.cpu_seconds)
+        line["cpu_baseline"] = {"value": round(1000.0 / cms, 5), "unit": "frames/s", "cores": cores, "kind": "oracle",
+                                "sample": desc, "seconds": round(spent, 1)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,265 @@
+/*
+ * npvs — C ABI of the GB300 (sm_103a) NeuralPVS hot path.
+ *
+ * The path (Sec. 3 of the paper): a viewcell defines an enclosing frustum (Sec. 3.2); the scene is
+ * froxelized into a binary geometry grid G (Sec. 3.2); G is interleaved into a coarse sparse grid
+ * with d^3 channels per site (Sec. 3.3, "3D volume-preserving interleaving"); a sparse 3-D
+ * convolutional network f_theta runs on it (Sec. 3.3, Sec. 2.3); the result is de-interleaved,
+ * passed through a sigmoid and thresholded at tau (Sec. 3.1), and ANDed with G (Sec. 3.2,
+ * supp(V) within supp(G)). Training adds the weighted Dice + repulsive visibility loss
+ * (Sec. 3.3), hand-written backward kernels and Adam (Sec. 4.2).
+ *
+ * Conventions for every entry point:
+ *  - Pointers marked "device" are CUDA device (or managed) memory owned by the caller; the
+ *    library never allocates, frees or retains them past the call. Pointers marked "host" are
+ *    read during the call only.
+ *  - `stream` is a cudaStream_t passed as void*. All device work is enqueued on it; no entry
+ *    point synchronises the device except npvs_check_status.
+ *  - Argument errors are returned synchronously (NPVS_ERR_INVALID_ARG / NPVS_ERR_UNSUPPORTED)
+ *    and nothing is enqueued. A launch failure returns NPVS_ERR_CUDA. Data-dependent errors found
+ *    on the device (a capacity overflow) are OR-ed as bit (1 << status) into the caller's
+ *    device status word `status` (nullable); kernels never trap.
+ *  - npvs_last_error() returns a message for the last non-OK status on the calling thread.
+ *  - Row counts produced on the device (n_rows, n_active) are clamped to the capacity given;
+ *    consumers read them from device memory, so a whole frame can be captured in a CUDA graph.
+ *
+ * Layouts:
+ *  - Froxel bits: uint32 [B][D][H][W/32]; froxel (x, y, k) of batch b is bit (x & 31) of word
+ *    ((b*D + k)*H + y)*(W/32) + x/32. x runs along the camera's right axis, y along up, k is the
+ *    depth slice.
+ *  - Sparse level: coords int32 [cap][4] = (b, z, y, x) sorted by the linear index
+ *    ((b*Z + z)*Y + y)*X + x; feature rows [cap][C] row-major; table int32 [B*Z*Y*X] holding each
+ *    site's row or -1 (a direct-mapped hash table keyed by the linear index).
+ *  - Interleaved channel of froxel (d X + dx, d Y + dy, d Z + dz) in input channel c:
+ *    c*d^3 + (dz*d + dy)*d + dx. Input channel 0 is occupancy in {0,1}; channel 1 (in_ch = 2) is
+ *    the normalised depth (2k+1)/(2D) of slice k at occupied froxels and 0 elsewhere.
+ *  - Weights (F32, F64): [taps][cin][cout] row-major, taps 27 (SubM3, tap ((dz+1)*3+(dy+1))*3+(dx+1)
+ *    for neighbour offset (dz,dy,dx)), 8 (down/up, tap (cz*2+cy)*2+cx for child offset), 1 (head).
+ *    BF16 weights are first packed by npvs_pack_weights into the tensor-core tile layout.
+ */
+#ifndef NPVS_H
+#define NPVS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NPVS_OK = 0,
+    NPVS_ERR_INVALID_ARG = 1,
+    NPVS_ERR_UNSUPPORTED = 2,
+    NPVS_ERR_CAPACITY = 3,
+    NPVS_ERR_WORKSPACE = 4,
+    NPVS_ERR_CUDA = 5,
+    NPVS_ERR_TIMEOUT = 6
+} npvs_status;
+
+typedef enum { NPVS_F32 = 0, NPVS_BF16 = 1, NPVS_F64 = 2 } npvs_dtype;
+
+#define NPVS_MAX_SLICES 256
+
+/* Froxel grid: W (multiple of 32) x H x D depth slices, batch B. */
+typedef struct {
+    int32_t W, H, D, B;
+} npvs_grid;
+
+/* Coarse (sparse-level) grid: X x Y x Z sites, batch B. */
+typedef struct {
+    int32_t X, Y, Z, B;
+} npvs_dims;
+
+/* Cube viewcell (Sec. 3.2): centre, half-size, heading yaw (radians about +y; yaw 0 looks along
+ * +z; pitch 0), camera FOV theta and rotation allowance beta in degrees, near / far distances. */
+typedef struct {
+    double centre[3];
+    double half_size;
+    double yaw;
+    double fov_deg;
+    double rot_deg;
+    double near_;
+    double far_;
+} npvs_viewcell;
+
+/* Enclosing frustum (Sec. 3.2): apex c', orthonormal basis, tan of the half-angle
+ * phi = (theta + 2 beta)/2, and the D+1 increasing slice bounds (slice k covers
+ * [slices[k], slices[k+1])). Plain old data; copy an array of them to the device for
+ * npvs_froxelize. */
+typedef struct {
+    float origin[3];
+    float right[3];
+    float up[3];
+    float fwd[3];
+    float tan_half;
+    int32_t n_slices;
+    float slices[NPVS_MAX_SLICES + 1];
+} npvs_camera;
+
+/* A sparse level (device pointers; capacity = rows allocated). */
+typedef struct {
+    npvs_dims dims;
+    int32_t capacity;
+    int32_t* coords;  /* device [capacity][4] */
+    int32_t* n_rows;  /* device scalar */
+    int32_t* table;   /* device [B*Z*Y*X] */
+} npvs_level;
+
+typedef enum { NPVS_RB_SUBM3 = 0, NPVS_RB_DOWN2 = 1 } npvs_rulebook_kind;
+
+typedef enum {
+    NPVS_CONV_SUBM3 = 0, /* submanifold 3x3x3: output set = input set */
+    NPVS_CONV_DOWN2 = 1, /* 2x2x2 stride 2: output set = parents */
+    NPVS_CONV_UP2 = 2,   /* transposed 2x2x2 stride 2 onto the finer level's set */
+    NPVS_CONV_HEAD1 = 3  /* 1x1x1 */
+} npvs_conv_kind;
+
+/* One sparse convolution (Sec. 2.3; masked dense definition y[p] = b + sum_t W_t^T x[p + t]).
+ *  map:  SUBM3 -> neighbour rows [cap_out][27] (-1 = none), from npvs_build_rulebook(SUBM3)
+ *        DOWN2 -> child rows of each parent [cap_out][8]
+ *        UP2   -> parent*8 + child-tap of each fine row [cap_out] (the "up map"); map2 -> the
+ *                 child rows of each coarse row [cap_in][8] (the down map of the same level pair)
+ *        HEAD1 -> NULL
+ *  n_out: device row count of the output level; cap_out its capacity (grid sizing).
+ *  x: [cap_in][cin]; y: [cap_out][cout]; skip (nullable): [cap_out][cout] added after ReLU.
+ *  dtype: F32 / F64 (SIMT FMA kernels, weights [taps][cin][cout]) or BF16 (tcgen05 kernels,
+ *  weights packed by npvs_pack_weights, FP32 accumulation); out_f32: with BF16, write FP32 y. */
+typedef struct {
+    int32_t kind;
+    int32_t dtype;
+    int32_t cin, cout;
+    int32_t relu;
+    int32_t out_f32;
+    const int32_t* map;
+    const int32_t* map2;
+    const int32_t* n_out;
+    int32_t cap_out;
+    const int32_t* n_in;
+    int32_t cap_in;
+    int32_t* status; /* nullable device status word (NPVS_ERR_TIMEOUT from bounded waits) */
+    void* workspace; /* nullable device scratch of npvs_conv_workspace_bytes(desc) bytes for BF16
+                        convs: split-K partial tiles and counters, and the product-form tiles T.
+                        It must be zero-filled before its first use; every call leaves the
+                        counters at zero again. Calls sharing one workspace must not overlap on
+                        the device. NULL: gather form without split-K. */
+    size_t workspace_bytes;
+    int32_t tune_stages;    /* BF16: shared-memory pipeline stages, 3..12 (0 = the most that fit) */
+    int32_t tune_max_split; /* BF16: largest split-K factor (0 = 8; 1 = never split) */
+    int32_t tune_lag;       /* BF16 cp.async gather: groups in flight per thread before a stage is
+                               published (0 = 2; clamped to stages - 1) */
+    int32_t tune_gather;    /* BF16 gather form: 0 auto, 1 TMA tile::gather4 (cin % 32 == 0),
+                               2 cp.async */
+    int32_t tune_gather_warps; /* BF16: gather warps per CTA, 4 or 8 (0 = 8) */
+    int32_t tune_form;      /* BF16 SUBM3 / DOWN2 / UP2: 0 auto (product form when the workspace
+                               holds T), 1 gather (UP2: scatter-epilogue) form, 2 product form */
+} npvs_conv_desc;
+
+/* ---- status and errors --------------------------------------------------------------------- */
+
+/* Message for the last non-OK status returned on the calling thread ("" if none). */
+const char* npvs_last_error(void);
+
+/* Library version string. */
+const char* npvs_version(void);
+
+/* Number of CUDA kernel launches this library has issued in this process (memsets excluded). */
+unsigned long long npvs_launch_count(void);
+
+/* Synchronises `stream`, reads the device status word (int32, device) and clears it. Returns
+ * NPVS_OK if it was 0, else the lowest status whose bit was set. */
+npvs_status npvs_check_status(int32_t* status, void* stream);
+
+/* ---- a1: frustum setup (host) --------------------------------------------------------------- */
+
+/* Sec. 3.2 first paragraph: c' = c - fwd * (h / tan(theta/2) + h) for a cube viewcell of
+ * half-size h (lateral radius r = h, plus h to enclose the cube's depth); phi = (theta+2 beta)/2;
+ * exponential slices z_k = near * (far/near)^(k/D). Computed in binary64 on the host, rounded
+ * once to binary32. Returns NPVS_ERR_INVALID_ARG for D outside [1, NPVS_MAX_SLICES] or
+ * non-positive near / far <= near. */
+npvs_status npvs_camera_setup(const npvs_viewcell* vc, int32_t n_slices, npvs_camera* out);
+
+/* ---- a2: froxelization ---------------------------------------------------------------------- */
+
+/* Workspace bytes npvs_froxelize needs for n_boxes boxes. */
+size_t npvs_froxelize_workspace_bytes(int32_t n_boxes);
+
+/* Sec. 3.2 froxelization with s x s supersampling per froxel column: for every supersampled
+ * pixel (a, b) of batch element e and every face of e's boxes (front and back, no depth test),
+ * the ray c' + t dir, dir = fwd + (n_x tan) right + (n_y tan) up, n_x = (2a+1-sW)/(sW),
+ * hits the face plane P at t = (P - c'_i)/dir_i; if the other two coordinates lie in the closed
+ * face rectangle and slices[0] <= t < slices[D], bit (a/s, b/s, max{k: slices[k] <= t}) is set.
+ * Every operation is one binary32 operation with round-to-nearest in that order, so the
+ * result is bit-exact.
+ *  boxes: device float [n_boxes][6] (min xyz, max xyz); box_offsets: device int32 [B+1], element
+ *  e owns boxes [box_offsets[e], box_offsets[e+1]); cams: device npvs_camera [B] with
+ *  n_slices == grid.D; occ_bits: device, zeroed and written here.
+ *  Errors: W % 32 != 0, D > NPVS_MAX_SLICES, s < 1, s*W or s*H > 65536, workspace too small. */
+npvs_status npvs_froxelize(const float* boxes, const int32_t* box_offsets, int32_t n_boxes,
+                           const npvs_camera* cams, npvs_grid grid, int32_t supersample,
+                           uint32_t* occ_bits, void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---- a3: interleave / a7: de-interleave ------------------------------------------------------ */
+
+size_t npvs_interleave_workspace_bytes(npvs_grid grid, int32_t d);
+
+/* Sec. 3.3 g_d on the sparse grid: the coarse site (X, Y, Z) of batch b is active iff any of its
+ * d^3 froxels is occupied; active sites are compacted in linear order into coords and their
+ * in_ch * d^3 features (layout above) are written as feat_dtype (F32 or BF16; the depth value is
+ * the binary32 quotient (2k+1)/(2D), rounded to nearest-even for BF16). d must divide 32, W, H
+ * and D. n_active (device) receives min(count, capacity); overflow sets NPVS_ERR_CAPACITY in
+ * status. table (device [B*(D/d)*(H/d)*(W/d)], nullable) receives each site's row or -1. */
+npvs_status npvs_interleave(const uint32_t* occ_bits, npvs_grid grid, int32_t d, int32_t in_ch,
+                            int32_t feat_dtype, int32_t capacity, int32_t* coords, void* feats,
+                            int32_t* n_active, int32_t* table, int32_t* status, void* workspace,
+                            size_t workspace_bytes, void* stream);
+
+/* Sec. 3.3 g_d^-1 with the Sec. 3.1 threshold and the Sec. 3.2 mask: for every froxel, p =
+ * sigmoid(logit) of its site's channel (0 for inactive sites) in binary32 (CUDA expf);
+ * pvs bit = (p >= tau) AND mask bit. logits: device float [cap][d^3]; table: level-0 table;
+ * mask_bits / pvs_bits: froxel bits; probs_out (nullable) device float [cap][d^3] receives p for
+ * rows < n_active. */
+npvs_status npvs_deinterleave(const float* logits, const int32_t* table, const int32_t* n_active,
+                              npvs_grid grid, int32_t d, float tau, const uint32_t* mask_bits,
+                              uint32_t* pvs_bits, float* probs_out, int32_t capacity, void* stream);
+
+/* ---- a4: rulebooks ------------------------------------------------------------------------- */
+
+size_t npvs_rulebook_workspace_bytes(npvs_dims dims);
+
+/* SUBM3 (out_level, map2 unused): fills in->table from in->coords (-1 elsewhere) and writes the
+ * neighbour map map [in->capacity][27]: entry k of row n is the row of site coords[n] + offset_k
+ * or -1 (absent or outside the grid).
+ * DOWN2: from in->table builds the parent level: out->coords / out->n_rows / out->table for the
+ * sites {floor(p/2)} in linear order (out->dims must be in->dims halved; all even), map
+ * [out->capacity][8] = rows of each parent's children (tap (cz*2+cy)*2+cx, -1 if absent), and
+ * map2 [in->capacity] = parent_row*8 + tap of every fine row (the up map). Overflow of
+ * out->capacity sets NPVS_ERR_CAPACITY in status. */
+npvs_status npvs_build_rulebook(int32_t kind, const npvs_level* in, const npvs_level* out,
+                                int32_t* map, int32_t* map2, int32_t* status, void* workspace,
+                                size_t workspace_bytes, void* stream);
+
+/* ---- a5/a6: sparse convolution ------------------------------------------------------------- */
+
+/* Bytes of the BF16 convolution workspace for this convolution (split-K region, plus for SUBM3 /
+ * DOWN2 / UP2 the FP32 product tiles T of cap_in x taps x cout, taps 27 / 8 / 8). NULL: the
+ * split-K region only. */
+size_t npvs_conv_workspace_bytes(const npvs_conv_desc* desc);
+
+/* Bytes of a packed BF16 weight tensor for a forward conv of this shape. */
+size_t npvs_packed_weight_bytes(int32_t kind, int32_t cin, int32_t cout);
+
+/* Packs FP32 weights [taps][cin][cout] (device) into the BF16 tensor-core layout (device,
+ * npvs_packed_weight_bytes) with round-to-nearest-even. */
+npvs_status npvs_pack_weights(int32_t kind, int32_t cin, int32_t cout, const float* w,
+                              void* packed, void* stream);
+
+/* y = act(b + conv(x)) (+ skip); see npvs_conv_desc. Output-stationary: every output row is
+ * written exactly once (no atomics); rows >= *n_out are not touched. */
+npvs_status npvs_sparse_conv_fwd(const npvs_conv_desc* desc, const void* x, const void* w,
+                                 const float* bias, const void* skip, void* y, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NPVS_H */

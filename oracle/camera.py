@@ -44,7 +44,6 @@ def frustum(vc, D: int) -> Camera:
     delta = vc.half / math.tan(0.5 * theta) + vc.half
     c = np.asarray(vc.centre, dtype=np.float64)
     origin = c - delta * f
-    k = np.arange(D + 1, dtype=np.float64)
-    z = vc.near * np.power(vc.far / vc.near, k / D)
+    z = [vc.near * math.pow(vc.far / vc.near, k / D) for k in range(D + 1)]
     f32 = lambda a: np.asarray(a, dtype=np.float64).astype(np.float32)
     return Camera(f32(origin), f32(r), f32(u), f32(f), np.float32(math.tan(phi)), f32(z))

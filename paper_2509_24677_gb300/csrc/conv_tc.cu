@@ -1,0 +1,982 @@
+// a5/a6: BF16 sparse convolution on the 5th-generation tensor cores (tcgen05, TMEM accumulators).
+//
+// Two formulations of y[p] = b + sum_t W_t^T x[p + delta_t] (Sec. 2.3, masked dense definition):
+//  * product form (default for submanifold and strided convs): a dense GEMM over the input rows,
+//    T[n][t * cout + o] = sum_c x[n][c] W_t[c][o], with A loaded as whole 128-row TMA tiles, then
+//    a gather-reduce y[m] = b + sum_t T[map[m][t]][t] over existing neighbours only, in fixed tap
+//    order (conv_reduce_kernel);
+//  * gather form: an implicit GEMM whose 128-row output tile accumulates sum_t X_t W_t over k-blocks
+//    of BKE flat (tap, channel) columns (BKE = 64, or 32 when cin = 32), gathering neighbour rows.
+//   gather     when cin is a multiple of 32, warp 0 alone feeds the pipeline with the TMA engine:
+//              per stage each lane issues one cp.async.bulk.tensor tile::gather4 that brings 4
+//              neighbour rows x[map(n, t)] (absent neighbours are out-of-range rows, filled with
+//              zeros) into the stage, swizzled by the tensor map (128B, or 64B for 64-byte rows),
+//              and lane 0 adds the weight block with one cp.async.bulk from a pre-swizzled HBM
+//              image; everything completes on the stage's transaction-count barrier. For cin of 8
+//              or 16, warps 0-3 gather 16-byte chunks with cp.async instead.
+//   warp 8     allocates TMEM and issues tcgen05.mma (M=128, N=BN, K=16, FP32 accumulate) from one
+//              thread; tcgen05.commit releases stages and hands a finished tile over;
+//   warps 4-7  epilogue: tcgen05.ld of their 32 TMEM lanes, bias, ReLU, skip add, store.
+// The CTA is persistent over work units; stage and accumulator hand-offs use mbarriers and every
+// wait is bounded in time (on expiry the kernel flags NPVS_ERR_TIMEOUT, issues nothing new,
+// drains what is in flight, frees its TMEM and returns).
+// The transposed stride-2 convolution (UP2) runs in scatter form: rows are coarse sites, the
+// GEMM has 8 * cout columns (one block per child tap), and the epilogue stores block j to the
+// child row given by the down map, so every output row is still written exactly once.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cstring>
+
+#include "conv_tc.cuh"
+
+namespace npvs {
+
+static inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+namespace {
+
+// Warp roles: PW gather warps (4 or 8), then 4 epilogue warps (warp % 4 selects the TMEM lane
+// quadrant they may read), then the MMA warp.
+constexpr int threads_for(int PW) { return 32 * (PW + 5); }
+constexpr int kBM = 128;
+constexpr int kSplitSlots = kNumSMs;
+
+struct TcParams {
+    int kind, cin, cout, relu, out_f32;
+    int scatter;   // epilogue: GEMM column block j -> child row map2[n][j] (transposed stride-2 conv)
+    int tout;      // epilogue: raw FP32 accumulators into T [rows][Ntot] (product form)
+    int KB, Kflat, Ntot, Npad, BN, n_tiles, stages;
+    int gmode;     // A operand: 0 cp.async gather, 1 TMA gather4, 2 TMA dense tile (rows m0..m0+127)
+    int BKE, RB;   // k-block width (elements) and its row bytes
+    int rows_x;    // rows of x (the out-of-range row used for absent neighbours)
+    int taps;      // stride of the gather map (27, 8) or 0 when row n reads input row n
+    uint32_t acc_cols;  // TMEM columns of one accumulator (two are allocated)
+    const int32_t* map;
+    const int32_t* map2;
+    const int32_t* n_rows;
+    int cap_rows;
+    const __nv_bfloat16* x;
+    const __nv_bfloat16* w;
+    const float* bias;
+    const __nv_bfloat16* skip;
+    void* y;
+    float* T;
+    int32_t* status;
+    int max_split;   // upper bound of the k-split factor
+    float* part;     // split-K partial tiles [kSplitSlots][128][BN] (nullable: no split)
+    int* counters;   // split-K arrival counters [4 * kSplitSlots], zero between launches
+};
+
+// ---- PTX wrappers ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for phase `parity` of an mbarrier. The bound is kept with the SM cycle counter (cheap to
+// read on every poll): ~4e9 cycles, about 2 s at the maximum clock, and 2e7 cycles once the CTA
+// has already timed out. On expiry the CTA records the timeout and carries on without waiting.
+__device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+    if (mbar_try_wait(bar, parity)) return;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        const long long lim = *abort_flag ? 20000000ll : 4000000000ll;
+        if (clock64() - t0 > lim) {
+            *abort_flag = 1;
+            return;
+        }
+    }
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor of a K-major operand with rows of RB bytes (128: 128-byte
+// swizzle, 64: 64-byte swizzle); 8-row groups are 8 * RB bytes apart.
+__device__ __forceinline__ uint64_t make_sdesc(uint32_t saddr, int RB) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;                        // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)((8 * RB) >> 4) << 32;          // stride byte offset
+    d |= (uint64_t)1 << 46;                        // descriptor version
+    d |= (uint64_t)(RB == 128 ? 2 : 4) << 61;      // 128-byte or 64-byte swizzle
+    return d;
+}
+
+__device__ __forceinline__ void tma_gather4(uint32_t dst, const CUtensorMap* tm, int col, int r0, int r1, int r2,
+                                            int r3, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(col), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(bar)
+        : "memory");
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major.
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// ---- the kernel -----------------------------------------------------------------------------
+
+__device__ __forceinline__ void tma_tile2d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+
+// Epilogue for 16 consecutive GEMM columns (from ng; bias of those columns in sb) of GEMM row n:
+// bias, ReLU, skip, store.
+__device__ __forceinline__ void store16(const TcParams& p, int n, int ng, const float* sb, const float (&acc)[16]) {
+    int orow = n, o0 = ng;
+    if (p.scatter) {
+        const int j = ng / p.cout;
+        if (j >= 8) return;
+        orow = p.map2[(size_t)n * 8 + j];
+        o0 = ng - j * p.cout;
+        if (orow < 0) return;
+    }
+    const size_t base = (size_t)orow * p.cout + o0;
+    const bool full16 = o0 + 16 <= p.cout;
+    float sk[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) sk[q] = 0.0f;
+    if (p.skip) {
+        if (full16) {
+            __align__(16) __nv_bfloat16 h[16];
+            *reinterpret_cast<uint4*>(h) = *reinterpret_cast<const uint4*>(p.skip + base);
+            *reinterpret_cast<uint4*>(h + 8) = *reinterpret_cast<const uint4*>(p.skip + base + 8);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) sk[q] = __bfloat162float(h[q]);
+        } else {
+            for (int q = 0; q < 16 && o0 + q < p.cout; ++q) sk[q] = __bfloat162float(p.skip[base + q]);
+        }
+    }
+    float f[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        float a = acc[q] + sb[q];
+        if (p.relu) a = fmaxf(a, 0.0f);
+        f[q] = a + sk[q];
+    }
+    if (p.out_f32) {
+        float* yo = reinterpret_cast<float*>(p.y) + base;
+        if (full16) {
+#pragma unroll
+            for (int q = 0; q < 16; q += 4) *reinterpret_cast<float4*>(yo + q) = make_float4(f[q], f[q + 1], f[q + 2], f[q + 3]);
+        } else {
+            for (int q = 0; q < 16 && o0 + q < p.cout; ++q) yo[q] = f[q];
+        }
+    } else {
+        __nv_bfloat16* yo = reinterpret_cast<__nv_bfloat16*>(p.y) + base;
+        if (full16) {
+            __align__(16) __nv_bfloat16 h[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) h[q] = __float2bfloat16_rn(f[q]);
+            *reinterpret_cast<uint4*>(yo) = *reinterpret_cast<uint4*>(h);
+            *reinterpret_cast<uint4*>(yo + 8) = *reinterpret_cast<uint4*>(h + 8);
+        } else {
+            for (int q = 0; q < 16 && o0 + q < p.cout; ++q) yo[q] = __float2bfloat16_rn(f[q]);
+        }
+    }
+}
+
+// Work units: (row tile, column tile, k-chunk). Layers with few row tiles may split their k-blocks
+// over up to gridDim.x CTAs; each writes an FP32 partial tile, and for every 32-row slice the last
+// epilogue warp to finish (atomic counter) sums the partials in k-chunk order, so results do not
+// depend on timing.
+//
+// Synchronisation: stage hand-offs use mbarriers (TMA modes: one expect_tx arrival and the copies'
+// transaction bytes; cp.async mode: one arrival per gather warp once all its lanes' groups completed
+// and were fenced to the async proxy, and a transaction barrier for the weight block); stage release
+// and accumulator hand-over use tcgen05.commit. Two TMEM accumulators alternate between units so
+// the epilogue of one unit overlaps the MMAs of the next. Below the CTA level only warp-local
+// barriers are used and abort decisions are warp-uniform, so a timed-out wait never strands
+// another warp. After a timeout nothing new is issued; teardown waits for the outstanding copies
+// and MMAs before TMEM is freed.
+template <int LAG, int PW>
+__global__ void __launch_bounds__(threads_for(PW), 1)
+    conv_tc_kernel(const TcParams p, const __grid_constant__ CUtensorMap tmap) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int S = p.stages;
+    const uint32_t a_bytes = (uint32_t)kBM * p.RB, b_bytes = (uint32_t)p.BN * p.RB;
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + (size_t)S * a_bytes;
+    int* map_s = reinterpret_cast<int*>(sB + (size_t)S * b_bytes);
+    float* s_bias = reinterpret_cast<float*>(map_s + kBM * p.taps + 4);  // [4 warps][256]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(s_bias + 4 * 256);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * S + 5);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    const uint32_t full0 = smem_u32(bars), bfull0 = smem_u32(bars + S), empty0 = smem_u32(bars + 2 * S);
+    const uint32_t tfull0 = smem_u32(bars + 3 * S), tempty0 = smem_u32(bars + 3 * S + 2);
+    const uint32_t mdone = smem_u32(bars + 3 * S + 4);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_rows = min(*p.n_rows, p.cap_rows);
+    const int tiles = ((n_rows + kBM - 1) / kBM) * p.n_tiles;
+    int ksplit = 1, kbc = p.KB;
+    if (p.part != nullptr && !p.tout && tiles > 0 && 2 * tiles <= (int)gridDim.x && p.max_split > 1) {
+        ksplit = min(min(p.KB, p.max_split), (int)gridDim.x / tiles);
+        kbc = (p.KB + ksplit - 1) / ksplit;
+        ksplit = (p.KB + kbc - 1) / kbc;
+    }
+    const int units = tiles * ksplit;
+    if ((int)blockIdx.x >= units) return;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full0 + 8 * s, p.gmode ? 1 : PW);  // TMA: one expect_tx; cp.async: one per warp
+            mbar_init(bfull0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull0 + 8 * b, 1);
+            mbar_init(tempty0 + 8 * b, 4);  // one arrival per epilogue warp
+        }
+        mbar_init(mdone, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == PW + 4) {
+        tmem_alloc(smem_u32(tmem_slot), 2 * p.acc_cols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp < PW && p.gmode == 2) {
+        // ------------------------------------------------------------------ TMA dense A tile
+        if (warp == 0) {
+            uint32_t it = 0;
+            bool stop = false;
+            for (int u = blockIdx.x; u < units && !stop; u += gridDim.x) {
+                const int tile = u / ksplit, kc = u - tile * ksplit;
+                const int mt = tile / p.n_tiles, nt = tile - mt * p.n_tiles;
+                const int kb0 = kc * kbc, kb1 = min(p.KB, kb0 + kbc);
+                for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                    const int s = (int)(it % S);
+                    mbar_wait(empty0 + 8 * s, ((it / S) & 1) ^ 1, abort_flag);
+                    if (__any_sync(0xffffffffu, *abort_flag)) {
+                        stop = true;
+                        break;
+                    }
+                    if (lane == 0) {
+                        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full0 + 8 * s),
+                                     "r"(a_bytes + b_bytes)
+                                     : "memory");
+                        const __nv_bfloat16* wsrc = p.w + ((size_t)kb * p.Npad + (size_t)nt * p.BN) * p.BKE;
+                        bulk_g2s(smem_u32(sB + (size_t)s * b_bytes), wsrc, b_bytes, full0 + 8 * s);
+                        tma_tile2d(smem_u32(sA + (size_t)s * a_bytes), &tmap, kb * p.BKE, mt * kBM, full0 + 8 * s);
+                    }
+                    __syncwarp();
+                }
+            }
+            if (lane == 0)  // nothing the TMA engine writes may still be landing when the CTA leaves
+                for (uint32_t j = it >= (uint32_t)S ? it - S : 0; j < it; ++j)
+                    mbar_wait(full0 + 8 * (j % S), (j / S) & 1, abort_flag);
+            __syncwarp();
+        }
+    } else if (warp < PW && p.gmode == 1) {
+        // ------------------------------------------------------------------ TMA gather
+        // the 32 row quads of a tile are spread over the gather warps (32 / PW lanes each); a lane
+        // stages its quad's neighbour-map rows (lane-private) and issues its gather4 each stage
+        constexpr int QPW = 32 / PW;
+        const bool act = lane < QPW;
+        const int q4 = warp * QPW + (act ? lane : 0);
+        uint32_t it = 0;
+        bool stop = false;
+        for (int u = blockIdx.x; u < units && !stop; u += gridDim.x) {
+            const int tile = u / ksplit, kc = u - tile * ksplit;
+            const int mt = tile / p.n_tiles, nt = tile - mt * p.n_tiles;
+            const int m0 = mt * kBM;
+            const int kb0 = kc * kbc, kb1 = min(p.KB, kb0 + kbc);
+            if (p.taps && act) {
+                for (int rr = 0; rr < 4; ++rr) {
+                    const int r = 4 * q4 + rr;
+                    const bool ok = m0 + r < n_rows;
+                    const int32_t* src = p.map + (size_t)(m0 + r) * p.taps;
+                    for (int t = 0; t < p.taps; ++t) map_s[r * p.taps + t] = ok ? src[t] : -1;
+                }
+            }
+            for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                const int s = (int)(it % S);
+                mbar_wait(empty0 + 8 * s, ((it / S) & 1) ^ 1, abort_flag);
+                if (__any_sync(0xffffffffu, *abort_flag)) {
+                    stop = true;
+                    break;
+                }
+                if (warp == 0 && lane == 0) {
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full0 + 8 * s),
+                                 "r"(a_bytes + b_bytes)
+                                 : "memory");
+                    const __nv_bfloat16* wsrc = p.w + ((size_t)kb * p.Npad + (size_t)nt * p.BN) * p.BKE;
+                    bulk_g2s(smem_u32(sB + (size_t)s * b_bytes), wsrc, b_bytes, full0 + 8 * s);
+                }
+                const int t = p.taps ? (kb * p.BKE) / p.cin : 0;
+                const int ci = kb * p.BKE - t * p.cin;
+                int rows[4];
+#pragma unroll
+                for (int rr = 0; rr < 4; ++rr) {
+                    const int r = 4 * q4 + rr, n = m0 + r;
+                    int src = -1;
+                    if (n < n_rows) src = p.taps ? map_s[r * p.taps + t] : n;
+                    rows[rr] = src >= 0 ? src : p.rows_x;
+                }
+                if (act)
+                    tma_gather4(smem_u32(sA + (size_t)s * a_bytes + 4 * q4 * p.RB), &tmap, ci, rows[0], rows[1],
+                                rows[2], rows[3], full0 + 8 * s);
+            }
+        }
+        if (warp == 0 && lane == 0)  // nothing the TMA engine writes may still be landing when the CTA leaves
+            for (uint32_t j = it >= (uint32_t)S ? it - S : 0; j < it; ++j)
+                mbar_wait(full0 + 8 * (j % S), (j / S) & 1, abort_flag);
+        __syncwarp();
+    } else if (warp < PW) {
+        // ------------------------------------------------------------------ cp.async gather
+        // thread (warp w, lane): 16-byte chunk c = lane & 7 of rows r0 + 4 PW q, r0 = 4 w + lane / 8
+        constexpr int RSTEP = 4 * PW, NQ = kBM / RSTEP;
+        const int tid = threadIdx.x, c = tid & 7, r0 = tid >> 3;
+        uint32_t it = 0;
+        bool stop = false;
+        for (int u = blockIdx.x; u < units && !stop; u += gridDim.x) {
+            const int tile = u / ksplit, kc = u - tile * ksplit;
+            const int mt = tile / p.n_tiles, nt = tile - mt * p.n_tiles;
+            const int m0 = mt * kBM;
+            const int kb0 = kc * kbc, kb1 = min(p.KB, kb0 + kbc);
+            if (p.taps) {  // this warp's rows of the neighbour map, once per unit
+                __syncwarp();
+                for (int e = lane; e < 4 * NQ * p.taps; e += 32) {
+                    const int j = e / p.taps, t = e - j * p.taps;
+                    const int r = 4 * warp + (j & 3) + RSTEP * (j >> 2);
+                    map_s[r * p.taps + t] = (m0 + r < n_rows) ? p.map[(size_t)(m0 + r) * p.taps + t] : -1;
+                }
+                __syncwarp();
+            }
+            for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                const int s = (int)(it % S);
+                mbar_wait(empty0 + 8 * s, ((it / S) & 1) ^ 1, abort_flag);
+                if (__any_sync(0xffffffffu, *abort_flag)) {
+                    stop = true;
+                    break;
+                }
+                if (tid == 0) {
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bfull0 + 8 * s),
+                                 "r"(b_bytes)
+                                 : "memory");
+                    const __nv_bfloat16* wsrc = p.w + ((size_t)kb * p.Npad + (size_t)nt * p.BN) * p.BKE;
+                    bulk_g2s(smem_u32(sB + (size_t)s * b_bytes), wsrc, b_bytes, bfull0 + 8 * s);
+                }
+                const int k = kb * 64 + c * 8;
+                const bool kvalid = k < p.Kflat;
+                const int t = p.taps ? k / p.cin : 0;
+                const int ci = k - t * p.cin;
+                uint8_t* a_stage = sA + (size_t)s * a_bytes;
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const int r = r0 + RSTEP * q, n = m0 + r;
+                    int src_row = -1;
+                    if (kvalid && n < n_rows) src_row = p.taps ? map_s[r * p.taps + t] : n;
+                    const void* src = src_row >= 0 ? (const void*)(p.x + (size_t)src_row * p.cin + ci) : (const void*)p.x;
+                    cp_async16(smem_u32(a_stage + r * 128 + ((c ^ (r & 7)) << 4)), src, src_row >= 0 ? 16u : 0u);
+                }
+                cp_async_commit();
+                if (it >= (uint32_t)LAG) {
+                    cp_async_wait<LAG>();
+                    fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(full0 + 8 * ((it - LAG) % S));
+                }
+            }
+        }
+        cp_async_wait<0>();
+        fence_proxy_async();
+        __syncwarp();
+        if (!stop && lane == 0)
+            for (uint32_t j = it >= (uint32_t)LAG ? it - LAG : 0; j < it; ++j) mbar_arrive(full0 + 8 * (j % S));
+        if (tid == 0)  // no weight copy may still be landing when the CTA leaves
+            for (uint32_t j = it >= (uint32_t)S ? it - S : 0; j < it; ++j)
+                mbar_wait(bfull0 + 8 * (j % S), (j / S) & 1, abort_flag);
+    } else if (warp < PW + 4) {
+        // ------------------------------------------------------------------ epilogue
+        const int ew = warp - PW, r = ew * 32 + lane;
+        float* wb = s_bias + ew * 256;
+        uint32_t tc = 0;
+        for (int u = blockIdx.x; u < units; u += gridDim.x, ++tc) {
+            const int tile = u / ksplit;
+            const int mt = tile / p.n_tiles, nt = tile - mt * p.n_tiles;
+            const int n = mt * kBM + r;
+            const uint32_t buf = tc & 1;
+            const uint32_t taddr_row = tmem + buf * p.acc_cols + ((uint32_t)(ew * 32) << 16);
+            if (!p.tout) {
+                __syncwarp();
+                for (int c2 = lane; c2 < p.BN; c2 += 32) {
+                    const int col = nt * p.BN + c2;
+                    const int o = p.scatter ? col % p.cout : col;
+                    wb[c2] = (p.bias && o < p.cout && col < p.Ntot) ? p.bias[o] : 0.0f;
+                }
+                __syncwarp();
+            }
+            mbar_wait(tfull0 + 8 * buf, (tc >> 1) & 1, abort_flag);
+            if (__any_sync(0xffffffffu, *abort_flag)) break;
+            tc_fence_after();
+            if (p.tout) {
+                for (int c0 = 0; c0 < p.BN; c0 += 16) {
+                    uint32_t v[16];
+                    tmem_ld16(taddr_row + (uint32_t)c0, v);
+                    tmem_ld_wait();
+                    const int ng = nt * p.BN + c0;
+                    if (n >= n_rows || ng >= p.Ntot) continue;
+                    float* dst = p.T + (size_t)n * p.Ntot + ng;
+                    if (ng + 16 <= p.Ntot) {
+#pragma unroll
+                        for (int q = 0; q < 16; q += 4)
+                            *reinterpret_cast<float4*>(dst + q) =
+                                make_float4(__uint_as_float(v[q]), __uint_as_float(v[q + 1]),
+                                            __uint_as_float(v[q + 2]), __uint_as_float(v[q + 3]));
+                    } else {
+                        for (int q = 0; q < 16 && ng + q < p.Ntot; ++q) dst[q] = __uint_as_float(v[q]);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
+            } else if (ksplit == 1) {
+                for (int c0 = 0; c0 < p.BN; c0 += 16) {
+                    uint32_t v[16];
+                    tmem_ld16(taddr_row + (uint32_t)c0, v);
+                    tmem_ld_wait();
+                    if (n >= n_rows) continue;
+                    float acc[16];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) acc[q] = __uint_as_float(v[q]);
+                    store16(p, n, nt * p.BN + c0, wb + c0, acc);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
+            } else {
+                float* part = p.part + ((size_t)u * kBM + r) * p.BN;
+                for (int c0 = 0; c0 < p.BN; c0 += 16) {
+                    uint32_t v[16];
+                    tmem_ld16(taddr_row + (uint32_t)c0, v);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int q = 0; q < 16; q += 4)
+                        __stcg(reinterpret_cast<float4*>(part + c0 + q),
+                               make_float4(__uint_as_float(v[q]), __uint_as_float(v[q + 1]), __uint_as_float(v[q + 2]),
+                                           __uint_as_float(v[q + 3])));
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty0 + 8 * buf);  // the accumulator is free again
+                __threadfence();
+                __syncwarp();
+                int last = 0;
+                if (lane == 0) last = atomicAdd(p.counters + tile * 4 + ew, 1) == ksplit - 1;
+                last = __shfl_sync(0xffffffffu, last, 0);
+                if (last) {
+                    __threadfence();
+                    if (n < n_rows) {
+                        const float* base = p.part + ((size_t)(tile * ksplit) * kBM + r) * p.BN;
+                        for (int c0 = 0; c0 < p.BN; c0 += 16) {
+                            float acc[16];
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) acc[q] = 0.0f;
+                            for (int k2 = 0; k2 < ksplit; ++k2) {
+                                const float* src = base + (size_t)k2 * kBM * p.BN + c0;
+#pragma unroll
+                                for (int q = 0; q < 16; q += 4) {
+                                    float4 v4 = __ldcg(reinterpret_cast<const float4*>(src + q));
+                                    acc[q] += v4.x;
+                                    acc[q + 1] += v4.y;
+                                    acc[q + 2] += v4.z;
+                                    acc[q + 3] += v4.w;
+                                }
+                            }
+                            store16(p, n, nt * p.BN + c0, wb + c0, acc);
+                        }
+                    }
+                    if (lane == 0) p.counters[tile * 4 + ew] = 0;
+                }
+            }
+        }
+    } else {
+        if (lane == 0) {
+            // -------------------------------------------------------------- MMA issuer
+            const uint32_t idesc = make_idesc(kBM, p.BN);
+            const int kk_steps = p.BKE / 16;
+            uint32_t it = 0, tc = 0;
+            bool stop = false;
+            for (int u = blockIdx.x; u < units && !stop; u += gridDim.x, ++tc) {
+                const int kc = u - (u / ksplit) * ksplit;
+                const int kb0 = kc * kbc, kb1 = min(p.KB, kb0 + kbc);
+                const uint32_t buf = tc & 1;
+                const uint32_t acc = tmem + buf * p.acc_cols;
+                mbar_wait(tempty0 + 8 * buf, ((tc >> 1) & 1) ^ 1, abort_flag);
+                if (*abort_flag) break;
+                tc_fence_after();
+                for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                    const int s = (int)(it % S);
+                    mbar_wait(full0 + 8 * s, (it / S) & 1, abort_flag);
+                    if (p.gmode == 0) mbar_wait(bfull0 + 8 * s, (it / S) & 1, abort_flag);
+                    if (*abort_flag) {
+                        stop = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(sA + (size_t)s * a_bytes), b0 = smem_u32(sB + (size_t)s * b_bytes);
+                    for (int k = 0; k < kk_steps; ++k)
+                        tc_mma(acc, make_sdesc(a0 + 32 * k, p.RB), make_sdesc(b0 + 32 * k, p.RB), idesc,
+                               (kb > kb0 || k > 0) ? 1u : 0u);
+                    tc_commit(empty0 + 8 * s);
+                }
+                if (!stop) tc_commit(tfull0 + 8 * buf);
+            }
+            // every MMA this CTA issued has completed before TMEM is released
+            tc_commit(mdone);
+            mbar_wait(mdone, 0, abort_flag);
+        }
+        __syncwarp();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == PW + 4) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 2 * p.acc_cols);
+    }
+    if (threadIdx.x == 0 && *abort_flag) raise_status(p.status, NPVS_ERR_TIMEOUT);
+}
+
+// y[m][o] = b[o] + sum_t T[map[m][t]][t * cout + o] (taps in fixed order), then ReLU and skip.
+// taps == 0: the transposed conv, y[m][o] = b[o] + T[u >> 3][(u & 7) * cout + o] with u = map[m] the
+// up map (parent row * 8 + child tap). One thread per (row, 4 channels); only existing neighbours
+// are read.
+template <typename OutT>
+__global__ void __launch_bounds__(256) conv_reduce_kernel(const float* __restrict__ T, int ldT,
+                                                          const int32_t* __restrict__ map, int taps,
+                                                          const int32_t* __restrict__ n_out_p, int cap_out, int cout,
+                                                          const float* __restrict__ bias, int relu,
+                                                          const __nv_bfloat16* __restrict__ skip, OutT* __restrict__ y) {
+    const int n_out = min(*n_out_p, cap_out);
+    const int G = cout >> 2;
+    const long long total = (long long)n_out * G;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int m = (int)(e / G), o = (int)(e - (long long)m * G) * 4;
+        float4 acc = bias ? *reinterpret_cast<const float4*>(bias + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (taps == 0) {
+            const int u = __ldg(map + m);
+            if (u >= 0) {
+                const float4 v = __ldcg(reinterpret_cast<const float4*>(T + (size_t)(u >> 3) * ldT + (u & 7) * cout + o));
+                acc.x += v.x;
+                acc.y += v.y;
+                acc.z += v.z;
+                acc.w += v.w;
+            }
+        } else {
+            const int32_t* mp = map + (size_t)m * taps;
+#pragma unroll 9
+            for (int t = 0; t < taps; ++t) {
+                const int n = __ldg(mp + t);
+                if (n >= 0) {
+                    const float4 v = __ldcg(reinterpret_cast<const float4*>(T + (size_t)n * ldT + t * cout + o));
+                    acc.x += v.x;
+                    acc.y += v.y;
+                    acc.z += v.z;
+                    acc.w += v.w;
+                }
+            }
+        }
+        if (relu) {
+            acc.x = fmaxf(acc.x, 0.f);
+            acc.y = fmaxf(acc.y, 0.f);
+            acc.z = fmaxf(acc.z, 0.f);
+            acc.w = fmaxf(acc.w, 0.f);
+        }
+        const size_t off = (size_t)m * cout + o;
+        if (skip) {
+            __align__(8) __nv_bfloat16 h[4];
+            *reinterpret_cast<uint2*>(h) = *reinterpret_cast<const uint2*>(skip + off);
+            acc.x += __bfloat162float(h[0]);
+            acc.y += __bfloat162float(h[1]);
+            acc.z += __bfloat162float(h[2]);
+            acc.w += __bfloat162float(h[3]);
+        }
+        if constexpr (sizeof(OutT) == 4) {
+            *reinterpret_cast<float4*>(y + off) = acc;
+        } else {
+            __align__(8) __nv_bfloat16 h[4] = {__float2bfloat16_rn(acc.x), __float2bfloat16_rn(acc.y),
+                                                __float2bfloat16_rn(acc.z), __float2bfloat16_rn(acc.w)};
+            *reinterpret_cast<uint2*>(y + off) = *reinterpret_cast<uint2*>(h);
+        }
+    }
+}
+
+// Packed weights: per k-block a [Npad][BKE] BF16 tile, K-major, each row's 16-byte chunks permuted
+// exactly as the 128-byte (BKE = 64) or 64-byte (BKE = 32) shared-memory swizzle places them, so a
+// stage is one linear bulk copy. Column-block forms (the transposed conv and the product form)
+// have n = j * cout + o and k = ci; the direct forms have n = o and k = t * cin + ci.
+__global__ void pack_weights_kernel(int kind, int cin, int cout, TcShape sh, const float* __restrict__ w,
+                                    __nv_bfloat16* __restrict__ out) {
+    const size_t total = (size_t)sh.KB * sh.Npad * sh.BKE;
+    const int nchunk = sh.BKE / 8;
+    const bool colblocks = sh.J > 1;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int kk = (int)(e % sh.BKE);
+        const size_t rest = e / sh.BKE;
+        const int n = (int)(rest % sh.Npad), kb = (int)(rest / sh.Npad);
+        const int k = kb * sh.BKE + kk;
+        float v = 0.0f;
+        if (k < sh.Kflat && n < sh.Ntot) {
+            if (colblocks) {
+                const int j = n / cout, o = n - j * cout;
+                v = w[((size_t)j * cin + k) * cout + o];
+            } else {
+                const int t = k / cin, ci = k - t * cin;
+                v = w[((size_t)t * cin + ci) * cout + n];
+            }
+        }
+        const int sw = ((n * sh.RB) >> 7) & (nchunk - 1);
+        const size_t dst = ((size_t)kb * sh.Npad + n) * sh.BKE + ((((kk >> 3) ^ sw) << 3) | (kk & 7));
+        out[dst] = __float2bfloat16_rn(v);
+    }
+}
+
+constexpr int kMaxStages = 12;
+constexpr size_t kMaxSmem = 227 * 1024;
+
+size_t tc_smem_bytes(int BN, int RB, int taps, int S) {
+    return 1024 + (size_t)S * (kBM + BN) * RB + (size_t)kBM * taps * 4 + 16 + 4 * 256 * 4 + (3 * S + 5) * 8 + 16;
+}
+
+int tc_stages(int BN, int RB, int taps) {
+    for (int S = kMaxStages; S > 4; --S)
+        if (tc_smem_bytes(BN, RB, taps, S) <= kMaxSmem) return S;
+    return 4;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+    }
+    return fn;
+}
+
+template <int LAG, int PW>
+npvs_status launch_tc(const TcParams& p, const CUtensorMap& tm, int grid, size_t smem, cudaStream_t st) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(conv_tc_kernel<LAG, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+        attr_set = true;
+    }
+    conv_tc_kernel<LAG, PW><<<grid, threads_for(PW), smem, st>>>(p, tm);
+    return check_launch("conv_tc_kernel");
+}
+
+template <int PW>
+npvs_status launch_tc_lag(int lag, const TcParams& p, const CUtensorMap& tm, int grid, size_t smem, cudaStream_t st) {
+    switch (lag) {
+        case 1: return launch_tc<1, PW>(p, tm, grid, smem, st);
+        case 2: return launch_tc<2, PW>(p, tm, grid, smem, st);
+        case 3: return launch_tc<3, PW>(p, tm, grid, smem, st);
+        case 4: return launch_tc<4, PW>(p, tm, grid, smem, st);
+        case 6: return launch_tc<6, PW>(p, tm, grid, smem, st);
+        default: return fail(NPVS_ERR_INVALID_ARG, "npvs_sparse_conv_fwd: unsupported pipeline lag");
+    }
+}
+
+// Bytes of one packed image (form 0: direct / transposed; form 1: product form).
+size_t packed_image_bytes(int kind, int cin, int cout, int form) {
+    TcShape sh = tc_shape(kind, cin, cout, form);
+    return Arena::round((size_t)sh.KB * sh.Npad * sh.BKE * sizeof(__nv_bfloat16));
+}
+
+bool has_product_form(int kind) { return kind == NPVS_CONV_SUBM3 || kind == NPVS_CONV_DOWN2; }
+
+size_t split_region_bytes() {
+    return Arena::round(4 * kSplitSlots * sizeof(int)) + Arena::round((size_t)kSplitSlots * kBM * 256 * sizeof(float));
+}
+
+size_t product_region_bytes(const npvs_conv_desc& d) {
+    if (!has_product_form(d.kind) && d.kind != NPVS_CONV_UP2) return 0;
+    const int J = d.kind == NPVS_CONV_SUBM3 ? 27 : 8;
+    const int rows = d.cap_in > 0 ? d.cap_in : d.cap_out;
+    return Arena::round((size_t)rows * J * d.cout * sizeof(float));
+}
+
+// One tcgen05 GEMM launch.
+npvs_status run_gemm(TcParams& p, const TcShape& sh, const npvs_conv_desc& d, const void* x, int lag, cudaStream_t st) {
+    p.KB = sh.KB;
+    p.Kflat = sh.Kflat;
+    p.Ntot = sh.Ntot;
+    p.Npad = sh.Npad;
+    p.BN = sh.BN;
+    p.n_tiles = sh.n_tiles;
+    p.BKE = sh.BKE;
+    p.RB = sh.RB;
+    p.stages = tc_stages(sh.BN, sh.RB, p.taps);
+    if (d.tune_stages >= 3 && d.tune_stages < p.stages) p.stages = d.tune_stages;
+    lag = std::min(lag, p.stages - 1);
+    if (lag == 5) lag = 4;  // instantiated lags: 1, 2, 3, 4, 6 (all < stages)
+    p.acc_cols = 32;
+    while ((int)p.acc_cols < sh.BN) p.acc_cols <<= 1;
+    if (p.cap_rows <= 0) return NPVS_OK;
+    const size_t smem = tc_smem_bytes(sh.BN, sh.RB, p.taps, p.stages);
+    alignas(64) CUtensorMap tm;
+    std::memset(&tm, 0, sizeof(tm));
+    if (p.gmode != 0) {
+        EncodeTiledFn enc = encode_tiled();
+        NPVS_REQUIRE(enc != nullptr, NPVS_ERR_CUDA, "BF16 conv: cuTensorMapEncodeTiled unavailable");
+        const cuuint64_t gdim[2] = {(cuuint64_t)d.cin, (cuuint64_t)p.rows_x};
+        const cuuint64_t gstride[1] = {(cuuint64_t)d.cin * 2};
+        const cuuint32_t box[2] = {(cuuint32_t)sh.BKE, p.gmode == 2 ? (cuuint32_t)kBM : 1u};
+        const cuuint32_t estride[2] = {1, 1};
+        CUresult r = enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(x), gdim, gstride, box, estride,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         sh.RB == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            set_error("BF16 conv: cuTensorMapEncodeTiled failed (%d)", (int)r);
+            return NPVS_ERR_CUDA;
+        }
+    }
+    const long long tiles_cap = (long long)ceil_div(p.cap_rows, kBM) * sh.n_tiles;
+    const int grid = (int)std::min<long long>(tiles_cap * (p.part ? sh.KB : 1), kNumSMs);
+    return d.tune_gather_warps == 4 ? launch_tc_lag<4>(lag, p, tm, grid, smem, st)
+                                    : launch_tc_lag<8>(lag, p, tm, grid, smem, st);
+}
+
+}  // namespace
+
+TcShape tc_shape(int kind, int cin, int cout, int form) {
+    TcShape s;
+    s.form = form;
+    if (form == 1) {  // product form of SUBM3 / DOWN2: T = x [W_0 | W_1 | ...]
+        s.J = kind == NPVS_CONV_SUBM3 ? 27 : 8;
+        s.taps_eff = 1;
+        s.Ntot = s.J * cout;
+    } else if (kind == NPVS_CONV_UP2) {
+        s.J = 8;
+        s.taps_eff = 1;
+        s.Ntot = 8 * cout;
+    } else {
+        s.J = 1;
+        s.taps_eff = kind == NPVS_CONV_SUBM3 ? 27 : (kind == NPVS_CONV_HEAD1 ? 1 : 8);
+        s.Ntot = cout;
+    }
+    s.tma = cin % 32 == 0;
+    s.BKE = (s.tma && cin % 64 != 0) ? 32 : 64;
+    s.RB = 2 * s.BKE;
+    s.Kflat = s.taps_eff * cin;
+    s.KB = (s.Kflat + s.BKE - 1) / s.BKE;
+    s.BN = 0;
+    if (form == 1)  // an exact divisor keeps T free of padding columns
+        for (int bn = 256; bn >= 16; bn -= 16)
+            if (s.Ntot % bn == 0) {
+                s.BN = bn;
+                break;
+            }
+    if (s.BN) {
+        s.Npad = s.Ntot;
+    } else if (s.Ntot <= 256) {
+        s.BN = round_up(s.Ntot, 16);
+        s.Npad = s.BN;
+    } else {
+        s.BN = 256;
+        s.Npad = round_up(s.Ntot, 256);
+    }
+    s.n_tiles = s.Npad / s.BN;
+    return s;
+}
+
+npvs_status conv_tc_fwd(const npvs_conv_desc& d, const void* x, const void* w, const float* bias, const void* skip,
+                        void* y, cudaStream_t st) {
+    NPVS_REQUIRE(d.cin % 8 == 0, NPVS_ERR_UNSUPPORTED, "BF16 conv: cin must be a multiple of 8");
+    NPVS_REQUIRE(d.cout % 8 == 0, NPVS_ERR_UNSUPPORTED, "BF16 conv: cout must be a multiple of 8");
+    const bool up = d.kind == NPVS_CONV_UP2;
+    NPVS_REQUIRE(!up || (d.cout % 16 == 0 && d.map2 && d.n_in), NPVS_ERR_UNSUPPORTED,
+                 "BF16 UP2 conv: needs cout % 16 == 0, the down map (map2) and n_in");
+    const int rows_x = d.cap_in > 0 ? d.cap_in : ((d.kind == NPVS_CONV_SUBM3 || d.kind == NPVS_CONV_HEAD1) ? d.cap_out : 0);
+    NPVS_REQUIRE(rows_x > 0, NPVS_ERR_INVALID_ARG, "BF16 conv: cap_in (rows of x) is required for this kind");
+    const int* n_x = d.n_in ? d.n_in : ((d.kind == NPVS_CONV_SUBM3 || d.kind == NPVS_CONV_HEAD1) ? d.n_out : nullptr);
+
+    // workspace: split-K region, then (product form) the FP32 product tiles T
+    float* part = nullptr;
+    int* counters = nullptr;
+    float* T = nullptr;
+    if (d.workspace != nullptr) {
+        Arena ar(d.workspace, d.workspace_bytes);
+        counters = ar.take<int>(4 * kSplitSlots);
+        part = ar.take<float>((size_t)kSplitSlots * kBM * 256);
+        NPVS_REQUIRE(counters && part, NPVS_ERR_WORKSPACE, "npvs_sparse_conv_fwd: workspace too small");
+        const size_t tb = product_region_bytes(d);
+        if (tb && ar.size - Arena::round(ar.used) >= tb) T = ar.take<float>(tb / sizeof(float));
+    }
+    // product form when asked for, or by default where it applies and the workspace holds T
+    const bool product = (has_product_form(d.kind) || up) && d.tune_form != 1 && T != nullptr && n_x != nullptr;
+    NPVS_REQUIRE(!(d.tune_form == 2 && !product), NPVS_ERR_WORKSPACE,
+                 "npvs_sparse_conv_fwd: product form needs n_in and a workspace of npvs_conv_workspace_bytes()");
+
+    TcParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.kind = d.kind;
+    p.cin = d.cin;
+    p.cout = d.cout;
+    p.relu = d.relu;
+    p.out_f32 = d.out_f32;
+    p.x = (const __nv_bfloat16*)x;
+    p.bias = bias;
+    p.skip = (const __nv_bfloat16*)skip;
+    p.y = y;
+    p.status = d.status;
+    p.rows_x = rows_x;
+    p.max_split = d.tune_max_split > 0 ? d.tune_max_split : 8;
+    const int lag = d.tune_lag > 0 ? d.tune_lag : 2;
+    const size_t img0 = packed_image_bytes(d.kind, d.cin, d.cout, 0);
+
+    if (product) {
+        // T[n][j*cout + o] = sum_c x[n][c] W_j[c][o] over the input rows, then the gather-reduce
+        TcShape sh = tc_shape(d.kind, d.cin, d.cout, up ? 0 : 1);  // the up conv's packing is column blocks
+        p.w = up ? (const __nv_bfloat16*)w
+                 : reinterpret_cast<const __nv_bfloat16*>(reinterpret_cast<const char*>(w) + img0);
+        p.taps = 0;
+        p.tout = 1;
+        p.T = T;
+        p.n_rows = n_x;
+        p.cap_rows = rows_x;
+        p.gmode = sh.tma ? 2 : 0;
+        NPVS_TRY(run_gemm(p, sh, d, x, lag, st));
+        const int taps = d.kind == NPVS_CONV_SUBM3 ? 27 : (up ? 0 : 8);
+        const long long work = (long long)d.cap_out * (d.cout / 4);
+        const int grid = (int)std::max<long long>(1, std::min<long long>(ceil_div(work, 256), kNumSMs * 8));
+        if (d.out_f32)
+            conv_reduce_kernel<float><<<grid, 256, 0, st>>>(T, sh.Ntot, d.map, taps, d.n_out, d.cap_out, d.cout, bias,
+                                                            d.relu, (const __nv_bfloat16*)skip, (float*)y);
+        else
+            conv_reduce_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(T, sh.Ntot, d.map, taps, d.n_out, d.cap_out, d.cout,
+                                                                    bias, d.relu, (const __nv_bfloat16*)skip,
+                                                                    (__nv_bfloat16*)y);
+        return check_launch("conv_reduce_kernel");
+    }
+
+    TcShape sh = tc_shape(d.kind, d.cin, d.cout, 0);
+    p.w = (const __nv_bfloat16*)w;
+    p.scatter = up;
+    p.taps = (d.kind == NPVS_CONV_SUBM3) ? 27 : (d.kind == NPVS_CONV_DOWN2 ? 8 : 0);
+    p.map = d.map;
+    p.map2 = d.map2;
+    p.n_rows = up ? d.n_in : d.n_out;
+    p.cap_rows = up ? d.cap_in : d.cap_out;
+    p.part = part;
+    p.counters = counters;
+    if (!sh.tma) p.gmode = 0;
+    else if (p.taps == 0) p.gmode = 2;      // rows of x read in order: dense tiles
+    else p.gmode = (d.tune_gather == 2 && sh.BKE == 64) ? 0 : 1;
+    return run_gemm(p, sh, d, x, lag, st);
+}
+
+}  // namespace npvs
+
+using namespace npvs;
+
+extern "C" size_t npvs_conv_workspace_bytes(const npvs_conv_desc* d) {
+    return split_region_bytes() + (d ? product_region_bytes(*d) : 0) + 256;
+}
+
+extern "C" size_t npvs_packed_weight_bytes(int32_t kind, int32_t cin, int32_t cout) {
+    size_t b = packed_image_bytes(kind, cin, cout, 0);
+    if (has_product_form(kind)) b += packed_image_bytes(kind, cin, cout, 1);
+    return b;
+}
+
+extern "C" npvs_status npvs_pack_weights(int32_t kind, int32_t cin, int32_t cout, const float* w, void* packed,
+                                         void* stream) {
+    NPVS_REQUIRE(w && packed && cin > 0 && cout > 0, NPVS_ERR_INVALID_ARG, "npvs_pack_weights: bad arguments");
+    NPVS_REQUIRE(kind >= NPVS_CONV_SUBM3 && kind <= NPVS_CONV_HEAD1, NPVS_ERR_UNSUPPORTED,
+                 "npvs_pack_weights: unknown kind");
+    const int nforms = has_product_form(kind) ? 2 : 1;
+    char* out = (char*)packed;
+    for (int f = 0; f < nforms; ++f) {
+        TcShape sh = tc_shape(kind, cin, cout, f);
+        const size_t total = (size_t)sh.KB * sh.Npad * sh.BKE;
+        const int grid = (int)std::min<size_t>((total + 255) / 256, (size_t)kNumSMs * 16);
+        pack_weights_kernel<<<grid, 256, 0, as_stream(stream)>>>(kind, cin, cout, sh, w, (__nv_bfloat16*)out);
+        NPVS_TRY(check_launch("pack_weights_kernel"));
+        out += packed_image_bytes(kind, cin, cout, f);
+    }
+    return NPVS_OK;
+}

@@ -1,0 +1,42 @@
+// tcgen05 (5th-generation tensor core) BF16 sparse convolution: launcher and weight packing.
+#pragma once
+#include "common.cuh"
+
+namespace npvs {
+
+__device__ __forceinline__ int conv_taps(int kind) {
+    return kind == NPVS_CONV_SUBM3 ? 27 : (kind == NPVS_CONV_HEAD1 ? 1 : 8);
+}
+
+// Input row feeding output row n through tap t (-1: none).
+__device__ __forceinline__ int gather_row(int kind, const int32_t* __restrict__ map, int n, int t) {
+    switch (kind) {
+        case NPVS_CONV_SUBM3: return map[(size_t)n * 27 + t];
+        case NPVS_CONV_DOWN2: return map[(size_t)n * 8 + t];
+        case NPVS_CONV_UP2: {
+            int u = map[n];
+            return (u >= 0 && (u & 7) == t) ? (u >> 3) : -1;
+        }
+        default: return n;
+    }
+}
+
+// GEMM view of a convolution: rows x (Kflat = taps_eff * cin) x Ntot.
+//   G-form (SUBM3, DOWN2, HEAD1): row = output row, k = tap * cin + ci, n = co.
+//   S-form (UP2): row = coarse input row, k = ci, n = child_tap * cout + co; the epilogue scatters
+//   column block child_tap to the child's row (down map).
+struct TcShape {
+    int form;  // 0: direct / transposed, 1: product form (T = x [W_0 | W_1 | ...])
+    int J;     // column blocks of the GEMM (1, 8 for the transposed conv, taps for the product form)
+    int taps_eff, Kflat, KB, Ntot, Npad, BN, n_tiles;
+    int tma;  // gather with TMA tile::gather4 (cin % 32 == 0) instead of cp.async
+    int BKE;  // k-block width in elements (64; 32 when cin is an odd multiple of 32)
+    int RB;   // bytes of one k-block row (2 * BKE)
+};
+
+TcShape tc_shape(int kind, int cin, int cout, int form);
+
+npvs_status conv_tc_fwd(const npvs_conv_desc& d, const void* x, const void* w, const float* bias,
+                        const void* skip, void* y, cudaStream_t st);
+
+}  // namespace npvs

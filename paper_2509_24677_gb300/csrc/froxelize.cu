@@ -1,0 +1,247 @@
+// a2: froxelization of a box scene into the geometry grid G (Sec. 3.2, froxelization paragraph).
+//
+// Work decomposition: every box face gets a conservative bounding rectangle of froxel columns
+// (the face clipped against half the near distance and projected); a prefix sum over the
+// per-face column counts gives a flat list of (face, column) items; each item casts the s x s
+// supersampled rays of its column against its one face. Every floating-point step of the ray
+// test is an explicit round-to-nearest binary32 intrinsic in a fixed order, so the resulting
+// bits do not depend on how the work is split. A hit sets its bit with atomicOr.
+#include "common.cuh"
+
+namespace npvs {
+namespace {
+
+struct __align__(16) FaceRec {
+    int b, axis;
+    float P, lo1, hi1, lo2, hi2;
+    int x0, y0, nx, ny, pad;
+};
+
+constexpr int kScanChunk = 1024;
+
+__device__ __forceinline__ int batch_of_box(const int32_t* off, int B, int j) {
+    int lo = 0, hi = B - 1;  // largest e with off[e] <= j
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= j) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void face_setup_kernel(const float* __restrict__ boxes, const int32_t* __restrict__ box_off,
+                                  int n_boxes, const npvs_camera* __restrict__ cams, npvs_grid g,
+                                  FaceRec* __restrict__ faces, int* __restrict__ counts) {
+    int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= n_boxes * 6) return;
+    int j = f / 6, fl = f % 6, axis = fl >> 1, side = fl & 1;
+    FaceRec rec;
+    rec.nx = rec.ny = 0;
+    rec.x0 = rec.y0 = 0;
+    rec.pad = 0;
+    int cnt = 0;
+    if (j >= box_off[0] && j < box_off[g.B]) {
+        int b = batch_of_box(box_off, g.B, j);
+        const npvs_camera& c = cams[b];
+        const float* bx = boxes + 6 * (size_t)j;
+        int j1 = (axis + 1) % 3, j2 = (axis + 2) % 3;
+        rec.b = b;
+        rec.axis = axis;
+        rec.P = bx[axis + 3 * side];
+        rec.lo1 = bx[j1];
+        rec.hi1 = bx[j1 + 3];
+        rec.lo2 = bx[j2];
+        rec.hi2 = bx[j2 + 3];
+        // face corners in camera coordinates
+        float cx[4], cy[4], cz[4];
+        for (int q = 0; q < 4; ++q) {
+            float p[3];
+            p[axis] = rec.P;
+            p[j1] = (q & 1) ? rec.hi1 : rec.lo1;
+            p[j2] = (q & 2) ? rec.hi2 : rec.lo2;
+            float v0 = p[0] - c.origin[0], v1 = p[1] - c.origin[1], v2 = p[2] - c.origin[2];
+            cx[q] = v0 * c.right[0] + v1 * c.right[1] + v2 * c.right[2];
+            cy[q] = v0 * c.up[0] + v1 * c.up[1] + v2 * c.up[2];
+            cz[q] = v0 * c.fwd[0] + v1 * c.fwd[1] + v2 * c.fwd[2];
+        }
+        const int order[4] = {0, 1, 3, 2};  // polygon order of the quad
+        const float zc = 0.5f * c.slices[0];
+        const float zfar = 1.01f * c.slices[c.n_slices];
+        float xmin = 1e30f, xmax = -1e30f, ymin = 1e30f, ymax = -1e30f;
+        bool any = false, all_far = true;
+        for (int e = 0; e < 4; ++e) {
+            int A = order[e], Bq = order[(e + 1) & 3];
+            bool inA = cz[A] >= zc, inB = cz[Bq] >= zc;
+            float px[2], py[2], pz[2];
+            int np = 0;
+            if (inA) { px[np] = cx[A]; py[np] = cy[A]; pz[np] = cz[A]; ++np; }
+            if (inA != inB) {
+                float t = (zc - cz[A]) / (cz[Bq] - cz[A]);
+                px[np] = cx[A] + t * (cx[Bq] - cx[A]);
+                py[np] = cy[A] + t * (cy[Bq] - cy[A]);
+                pz[np] = zc;
+                ++np;
+            }
+            for (int q = 0; q < np; ++q) {
+                any = true;
+                if (pz[q] < zfar) all_far = false;
+                float sx = px[q] / (pz[q] * c.tan_half), sy = py[q] / (pz[q] * c.tan_half);
+                xmin = fminf(xmin, sx); xmax = fmaxf(xmax, sx);
+                ymin = fminf(ymin, sy); ymax = fmaxf(ymax, sy);
+            }
+        }
+        if (any && !all_far) {
+            // froxel column coordinate (n + 1) / 2 * W, one column of margin each side
+            float gx0 = (xmin + 1.f) * 0.5f * g.W, gx1 = (xmax + 1.f) * 0.5f * g.W;
+            float gy0 = (ymin + 1.f) * 0.5f * g.H, gy1 = (ymax + 1.f) * 0.5f * g.H;
+            gx0 = fmaxf(fminf(gx0, 1e8f), -1e8f); gx1 = fmaxf(fminf(gx1, 1e8f), -1e8f);
+            gy0 = fmaxf(fminf(gy0, 1e8f), -1e8f); gy1 = fmaxf(fminf(gy1, 1e8f), -1e8f);
+            int x0 = max((int)floorf(gx0) - 1, 0), x1 = min((int)floorf(gx1) + 1, g.W - 1);
+            int y0 = max((int)floorf(gy0) - 1, 0), y1 = min((int)floorf(gy1) + 1, g.H - 1);
+            if (x0 <= x1 && y0 <= y1) {
+                rec.x0 = x0; rec.y0 = y0; rec.nx = x1 - x0 + 1; rec.ny = y1 - y0 + 1;
+                cnt = rec.nx * rec.ny;
+            }
+        }
+    } else {
+        rec.b = 0; rec.axis = 0; rec.P = rec.lo1 = rec.hi1 = rec.lo2 = rec.hi2 = 0.f;
+    }
+    faces[f] = rec;
+    counts[f] = cnt;
+}
+
+// Per-chunk exclusive scan of counts into 64-bit offsets; chunk sums for the second level.
+__global__ void chunk_scan_kernel(const int* __restrict__ counts, long long* __restrict__ offs, int n,
+                                  int* __restrict__ chunk_sum) {
+    __shared__ int sw[33];
+    int i = blockIdx.x * kScanChunk + threadIdx.x;
+    int v = i < n ? counts[i] : 0;
+    int tot;
+    int ex = block_exclusive_scan(v, sw, &tot);
+    if (i < n) offs[i] = ex;
+    if (threadIdx.x == 0) chunk_sum[blockIdx.x] = tot;
+}
+
+__global__ void chunk_add_kernel(long long* __restrict__ offs, int n, const int* __restrict__ chunk_off,
+                                 const int* __restrict__ counts, long long* __restrict__ total) {
+    int i = blockIdx.x * kScanChunk + threadIdx.x;
+    if (i < n) {
+        long long o = offs[i] + chunk_off[blockIdx.x];
+        offs[i] = o;
+        if (i == n - 1) *total = o + counts[i];
+    }
+}
+
+__device__ __forceinline__ int slice_of(const float* __restrict__ z, int D, float t) {
+    int lo = 0, hi = D - 1;  // max k in [0, D-1] with z[k] <= t (z[0] <= t holds)
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (z[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) froxel_items_kernel(
+    const FaceRec* __restrict__ faces, const long long* __restrict__ offs, int n_faces,
+    const long long* __restrict__ total_p, const npvs_camera* __restrict__ cams, npvs_grid g, int s,
+    uint32_t* __restrict__ bits) {
+    const long long total = *total_p;
+    const int sW = s * g.W, sH = s * g.H, WW = g.W >> 5;
+    const float fsW = (float)sW, fsH = (float)sH;
+    for (long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x; item < total;
+         item += (long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = n_faces - 1;  // face = max f with offs[f] <= item
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (offs[mid] <= item) lo = mid; else hi = mid - 1;
+        }
+        const FaceRec fr = faces[lo];
+        int local = (int)(item - offs[lo]);
+        int x = fr.x0 + local % fr.nx, y = fr.y0 + local / fr.nx;
+        const npvs_camera& c = cams[fr.b];
+        const int ax = fr.axis, j1 = ax == 2 ? 0 : ax + 1, j2 = ax == 0 ? 2 : ax - 1;
+        const float o_ax = c.origin[ax], o1 = c.origin[j1], o2 = c.origin[j2];
+        const float f_ax = c.fwd[ax], f1 = c.fwd[j1], f2 = c.fwd[j2];
+        const float r_ax = c.right[ax], r1 = c.right[j1], r2 = c.right[j2];
+        const float u_ax = c.up[ax], u1 = c.up[j1], u2 = c.up[j2];
+        const float tanh_ = c.tan_half;
+        const float z0 = c.slices[0], zD = c.slices[g.D];
+        const float num = __fsub_rn(fr.P, o_ax);
+        size_t word_base = (((size_t)fr.b * g.D) * g.H + y) * WW + (x >> 5);
+        const uint32_t bit = 1u << (x & 31);
+        int last_k = -1;
+        for (int bb = y * s; bb < y * s + s; ++bb) {
+            float ny = __fdiv_rn((float)(2 * bb + 1 - sH), fsH);
+            float sy = __fmul_rn(ny, tanh_);
+            for (int a = x * s; a < x * s + s; ++a) {
+                float nx = __fdiv_rn((float)(2 * a + 1 - sW), fsW);
+                float sx = __fmul_rn(nx, tanh_);
+                float d_ax = __fadd_rn(__fadd_rn(f_ax, __fmul_rn(sx, r_ax)), __fmul_rn(sy, u_ax));
+                if (d_ax == 0.0f) continue;
+                float t = __fdiv_rn(num, d_ax);
+                if (!(t >= z0 && t < zD)) continue;
+                float d1 = __fadd_rn(__fadd_rn(f1, __fmul_rn(sx, r1)), __fmul_rn(sy, u1));
+                float h1 = __fadd_rn(o1, __fmul_rn(t, d1));
+                if (!(h1 >= fr.lo1 && h1 <= fr.hi1)) continue;
+                float d2 = __fadd_rn(__fadd_rn(f2, __fmul_rn(sx, r2)), __fmul_rn(sy, u2));
+                float h2 = __fadd_rn(o2, __fmul_rn(t, d2));
+                if (!(h2 >= fr.lo2 && h2 <= fr.hi2)) continue;
+                int k = slice_of(c.slices, g.D, t);
+                if (k != last_k) {
+                    atomicOr(bits + word_base + (size_t)k * g.H * WW, bit);
+                    last_k = k;
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+}  // namespace npvs
+
+using namespace npvs;
+
+static size_t froxel_ws(int n_boxes) {
+    size_t F = (size_t)n_boxes * 6;
+    size_t nchunk = (F + kScanChunk - 1) / kScanChunk;
+    return Arena::round(F * sizeof(FaceRec)) + Arena::round(F * sizeof(int)) +
+           Arena::round(F * sizeof(long long)) + 2 * Arena::round((nchunk + 1) * sizeof(int)) +
+           Arena::round(sizeof(long long)) + 256;
+}
+
+extern "C" size_t npvs_froxelize_workspace_bytes(int32_t n_boxes) { return froxel_ws(n_boxes); }
+
+extern "C" npvs_status npvs_froxelize(const float* boxes, const int32_t* box_offsets, int32_t n_boxes,
+                                      const npvs_camera* cams, npvs_grid g, int32_t s, uint32_t* occ_bits,
+                                      void* workspace, size_t workspace_bytes, void* stream) {
+    NPVS_REQUIRE(box_offsets && cams && occ_bits, NPVS_ERR_INVALID_ARG, "npvs_froxelize: NULL pointer");
+    NPVS_REQUIRE(n_boxes >= 0 && (n_boxes == 0 || boxes), NPVS_ERR_INVALID_ARG, "npvs_froxelize: bad boxes");
+    NPVS_REQUIRE(g.W > 0 && g.H > 0 && g.D > 0 && g.B > 0 && g.W % 32 == 0, NPVS_ERR_UNSUPPORTED,
+                 "npvs_froxelize: need W % 32 == 0 and positive sizes");
+    NPVS_REQUIRE(g.D <= NPVS_MAX_SLICES, NPVS_ERR_UNSUPPORTED, "npvs_froxelize: D > NPVS_MAX_SLICES");
+    NPVS_REQUIRE(s >= 1 && (long long)s * g.W <= 65536 && (long long)s * g.H <= 65536,
+                 NPVS_ERR_UNSUPPORTED, "npvs_froxelize: supersampled size out of range");
+    NPVS_REQUIRE(workspace_bytes >= froxel_ws(n_boxes) && workspace, NPVS_ERR_WORKSPACE,
+                 "npvs_froxelize: workspace too small");
+    cudaStream_t st = as_stream(stream);
+    size_t nbytes = (size_t)g.B * g.D * g.H * (g.W / 32) * sizeof(uint32_t);
+    if (cudaMemsetAsync(occ_bits, 0, nbytes, st) != cudaSuccess) return check_launch("npvs_froxelize memset");
+    if (n_boxes == 0) return NPVS_OK;
+    const int F = n_boxes * 6;
+    const int nchunk = ceil_div(F, kScanChunk);
+    Arena ar(workspace, workspace_bytes);
+    FaceRec* faces = ar.take<FaceRec>(F);
+    int* counts = ar.take<int>(F);
+    long long* offs = ar.take<long long>(F);
+    int* csum = ar.take<int>(nchunk + 1);
+    int* coff = ar.take<int>(nchunk + 1);
+    long long* total = ar.take<long long>(1);
+    face_setup_kernel<<<ceil_div(F, 256), 256, 0, st>>>(boxes, box_offsets, n_boxes, cams, g, faces, counts);
+    NPVS_TRY(check_launch("face_setup_kernel"));
+    chunk_scan_kernel<<<nchunk, kScanChunk, 0, st>>>(counts, offs, F, csum);
+    NPVS_TRY(check_launch("chunk_scan_kernel"));
+    NPVS_TRY(scan_block_counts(csum, coff, nchunk, csum + nchunk, -1, nullptr, st));
+    chunk_add_kernel<<<nchunk, kScanChunk, 0, st>>>(offs, F, coff, counts, total);
+    NPVS_TRY(check_launch("chunk_add_kernel"));
+    froxel_items_kernel<<<kNumSMs * 8, 256, 0, st>>>(faces, offs, F, total, cams, g, s, occ_bits);
+    return check_launch("froxel_items_kernel");
+}

@@ -1,0 +1,321 @@
+"""Per-frame NeuralPVS inference on one GPU through the npvs C ABI.
+
+V = g_d^-1(f_theta(g_d(G))) thresholded at tau and masked by G (Sec. 3.1-3.3), with G the
+froxelized scene of the viewcell's enclosing frustum (Sec. 3.2). All device buffers are
+allocated once per (workload, batch, dtype) with capacity-bounded sizes; every step is a kernel
+of libnpvs.so enqueued on the current stream, with row counts kept on the device, so a frame can
+be replayed as a CUDA graph.
+"""
+from __future__ import annotations
+
+import contextlib
+import dataclasses
+from typing import Dict, List, Optional, Sequence
+
+import torch
+
+from . import _lib as L
+from . import ops
+
+TORCH_DT = {L.F32: torch.float32, L.BF16: torch.bfloat16, L.F64: torch.float64}
+KIND = {"subm3": L.CONV_SUBM3, "down2": L.CONV_DOWN2, "up2": L.CONV_UP2, "head1": L.CONV_HEAD1}
+
+
+@dataclasses.dataclass
+class SparseLevel:
+    dims: L.Dims
+    capacity: int
+    coords: torch.Tensor     # [cap][4] int32
+    n_rows: torch.Tensor     # [1] int32
+    table: torch.Tensor      # [B*Z*Y*X] int32
+    nbr: torch.Tensor        # [cap][27] int32
+    down: Optional[torch.Tensor] = None   # [cap_next][8] child rows of each parent (next level)
+    up: Optional[torch.Tensor] = None     # [cap][1] parent*8 + tap
+
+    @staticmethod
+    def alloc(X, Y, Z, B, cap, device):
+        n_sites = X * Y * Z * B
+        i32 = dict(dtype=torch.int32, device=device)
+        return SparseLevel(L.Dims(X, Y, Z, B), cap, torch.zeros(cap, 4, **i32), torch.zeros(1, **i32),
+                           torch.empty(n_sites, **i32), torch.empty(cap, 27, **i32))
+
+
+def _timing_event():
+    # "external" events stay queryable when recorded inside a CUDA graph capture
+    try:
+        return torch.cuda.Event(enable_timing=True, external=True)
+    except TypeError:
+        return torch.cuda.Event(enable_timing=True)
+
+
+class StageTimer:
+    """Records a CUDA event pair around each named stage on the current stream."""
+
+    def __init__(self):
+        self.events = []
+
+    @contextlib.contextmanager
+    def __call__(self, name):
+        s = _timing_event()
+        e = _timing_event()
+        s.record()
+        yield
+        e.record()
+        self.events.append((name, s, e))
+
+    def totals(self) -> Dict[str, float]:
+        out: Dict[str, float] = {}
+        for name, s, e in self.events:
+            out[name] = out.get(name, 0.0) + s.elapsed_time(e)
+        return out
+
+
+_null = contextlib.nullcontext()
+
+
+class Net:
+    """Network weights on the device: FP32 master [taps][cin][cout], biases, and per dtype the
+    operand the kernels read (packed BF16 tiles, or the FP32/FP64 tensors themselves)."""
+
+    def __init__(self, layers, weights: Sequence, biases: Sequence, device="cuda"):
+        self.layers = list(layers)
+        self.w32 = [torch.as_tensor(w, dtype=torch.float32).contiguous().to(device) for w in weights]
+        self.b32 = [torch.as_tensor(b, dtype=torch.float32).contiguous().to(device) for b in biases]
+        self.device = device
+        self._packed: Optional[List[torch.Tensor]] = None
+        self._w64: Optional[List[torch.Tensor]] = None
+
+    def packed(self) -> List[torch.Tensor]:
+        if self._packed is None:
+            self._packed = []
+            for l, w in zip(self.layers, self.w32):
+                nb = ops.npvs_packed_weight_bytes(KIND[l.kind], l.cin, l.cout)
+                buf = torch.empty(nb, dtype=torch.uint8, device=self.device)
+                ops.npvs_pack_weights(KIND[l.kind], l.cin, l.cout, w, buf)
+                self._packed.append(buf)
+        return self._packed
+
+    def repack(self):
+        self._packed = None
+        self._w64 = None
+
+    def operands(self, dtype):
+        if dtype == L.BF16:
+            return self.packed()
+        if dtype == L.F64:
+            if self._w64 is None:
+                self._w64 = [w.double() for w in self.w32]
+            return self._w64
+        return self.w32
+
+
+class FramePipeline:
+    """Buffers and launch sequence of one frame (batch of viewcells) for a workload."""
+
+    def __init__(self, wl, net: Net, batch: int = 1, dtype: int = L.BF16, tau: float = 0.5,
+                 device="cuda", capacity_frac: float = 1.0):
+        self.wl, self.net, self.B, self.dtype, self.tau = wl, net, batch, dtype, tau
+        self.device = device
+        d = wl.d
+        self.grid = L.Grid(wl.W, wl.H, wl.D, batch)
+        self.n_levels = 1 + sum(1 for l in net.layers if l.kind == "down2")
+        i32 = dict(dtype=torch.int32, device=device)
+        self.occ = torch.empty(batch * wl.D * wl.H * (wl.W // 32), **i32)
+        self.pvs = torch.empty_like(self.occ)
+        self.status = torch.zeros(1, **i32)
+        self.levels: List[SparseLevel] = []
+        X, Y, Z = wl.W // d, wl.H // d, wl.D // d
+        for li in range(self.n_levels):
+            sites = X * Y * Z * batch
+            cap = max(1, int(sites * capacity_frac))
+            self.levels.append(SparseLevel.alloc(X, Y, Z, batch, cap, device))
+            X, Y, Z = X // 2, Y // 2, Z // 2
+        for li in range(self.n_levels - 1):
+            a, b = self.levels[li], self.levels[li + 1]
+            b_down = torch.empty(b.capacity, 8, **i32)
+            a.down = b_down
+            a.up = torch.empty(a.capacity, 1, **i32)
+        act_dt = TORCH_DT[dtype]
+        cap0 = self.levels[0].capacity
+        self.feats = torch.zeros(cap0, wl.feat_ch, dtype=act_dt, device=device)
+        self.acts: Dict[str, torch.Tensor] = {}
+        lv_of = self._level_of_layers()
+        last = net.layers[-1].name
+        for l in net.layers:
+            cap = self.levels[lv_of[l.name]].capacity
+            # the last layer's logits are FP32 on every path but FP64
+            dt = torch.float32 if (l.name == last and dtype != L.F64) else act_dt
+            self.acts[l.name] = torch.zeros(cap, l.cout, dtype=dt, device=device)
+        self.logits = self.acts[net.layers[-1].name]
+        self.probs = torch.zeros(cap0, d ** 3, dtype=torch.float32, device=device)
+        self.ws = ops.Workspace(device)
+        self.timer: Optional[StageTimer] = None
+        self._build_descs()
+
+    def _t(self, name):
+        return self.timer(name) if self.timer is not None else _null
+
+    def _level_of_layers(self):
+        lv, out = 0, {}
+        for l in self.net.layers:
+            if l.kind == "down2":
+                lv += 1
+            elif l.kind == "up2":
+                lv -= 1
+            out[l.name] = lv
+        return out
+
+    # ------------------------------------------------------------------------------------------
+    def froxelize(self, boxes, box_offsets, cams_dev):
+        with self._t("froxelize"):
+            ops.npvs_froxelize(boxes, box_offsets, cams_dev, self.grid, self.wl.supersample, self.occ, ws=self.ws)
+
+    def interleave(self):
+        lv0 = self.levels[0]
+        with self._t("interleave"):
+            ops.npvs_interleave(self.occ, self.grid, self.wl.d, self.wl.in_ch, self.dtype, lv0.capacity,
+                                lv0.coords, self.feats, lv0.n_rows, table=lv0.table, status=self.status, ws=self.ws)
+
+    def rulebooks(self):
+        with self._t("rulebooks"):
+            for li, lv in enumerate(self.levels):
+                ops.npvs_build_rulebook(L.RB_SUBM3, lv, None, lv.nbr, status=self.status, ws=self.ws)
+                if li + 1 < self.n_levels:
+                    nxt = self.levels[li + 1]
+                    ops.npvs_build_rulebook(L.RB_DOWN2, lv, nxt, lv.down, lv.up, status=self.status, ws=self.ws)
+
+    def _build_descs(self):
+        """Descriptors of every layer (fixed buffers), the shared convolution workspace sized for the
+        largest product-form tile set, and the skip input of each decoder up-conv."""
+        lv_of = self._level_of_layers()
+        self.descs, self.skip_of = [], {}
+        for i, l in enumerate(self.net.layers):
+            li = lv_of[l.name]
+            lv = self.levels[li]
+            last = i == len(self.net.layers) - 1
+            common = dict(out_f32=last, status=self.status)
+            if l.kind == "subm3":
+                d = ops.conv_desc(L.CONV_SUBM3, self.dtype, l.cin, l.cout, l.relu, lv.nbr, lv.n_rows, lv.capacity,
+                                  n_in=lv.n_rows, cap_in=lv.capacity, **common)
+            elif l.kind == "down2":
+                prev = self.levels[li - 1]
+                d = ops.conv_desc(L.CONV_DOWN2, self.dtype, l.cin, l.cout, l.relu, prev.down, lv.n_rows, lv.capacity,
+                                  n_in=prev.n_rows, cap_in=prev.capacity, **common)
+            elif l.kind == "up2":
+                nxt = self.levels[li + 1]
+                d = ops.conv_desc(L.CONV_UP2, self.dtype, l.cin, l.cout, l.relu, lv.up, lv.n_rows, lv.capacity,
+                                  map2=lv.down, n_in=nxt.n_rows, cap_in=nxt.capacity, **common)
+                self.skip_of[i] = self.acts[f"enc{li}b"]
+            else:
+                d = ops.conv_desc(L.CONV_HEAD1, self.dtype, l.cin, l.cout, l.relu, None, lv.n_rows, lv.capacity,
+                                  n_in=lv.n_rows, cap_in=lv.capacity, **common)
+            self.descs.append(d)
+        self.conv_ws = None
+        if self.dtype == L.BF16:
+            nbytes = max(ops.npvs_conv_workspace_bytes(d) for d in self.descs)
+            self.conv_ws = ops.conv_workspace(nbytes, self.device)
+            for d in self.descs:
+                d.workspace = self.conv_ws.data_ptr()
+                d.workspace_bytes = self.conv_ws.numel()
+
+    def network(self):
+        W = self.net.operands(self.dtype)
+        a = self.feats
+        for i, l in enumerate(self.net.layers):
+            y = self.acts[l.name]
+            with self._t("conv:" + l.name):
+                ops.npvs_sparse_conv_fwd(self.descs[i], a, W[i], self.net.b32[i], self.skip_of.get(i), y)
+            a = y
+        return a
+
+    # ---- autotuning ------------------------------------------------------------------------------
+    CANDIDATES = {
+        "subm3": [dict(tune_form=2), dict(tune_form=1, tune_gather_warps=8),
+                  dict(tune_form=1, tune_gather_warps=8, tune_max_split=1), dict(tune_form=1, tune_gather_warps=4)],
+        "down2": [dict(tune_form=2), dict(tune_form=1, tune_gather_warps=8),
+                  dict(tune_form=1, tune_gather_warps=8, tune_max_split=1)],
+        "up2": [dict(tune_form=2), dict(tune_form=1)],
+        "head1": [dict()],
+    }
+
+    def autotune(self, boxes, box_offsets, cams_dev, reps: int = 10):
+        """Times the candidate configurations of every BF16 layer on this frame (each as a CUDA
+        graph of `reps` launches) and keeps the fastest in the layer's descriptor. The best choice
+        depends on the active-site counts, so tune on a representative frame. Returns
+        {layer: (config, microseconds)}."""
+        if self.dtype != L.BF16:
+            return {}
+        self.run(boxes, box_offsets, cams_dev, want_probs=False)
+        torch.cuda.synchronize()
+        W = self.net.operands(self.dtype)
+        chosen = {}
+        x = self.feats
+        for i, l in enumerate(self.net.layers):
+            y = self.acts[l.name]
+            best = None
+            for cfg in self.CANDIDATES[l.kind]:
+                d = L.ConvDesc.from_buffer_copy(self.descs[i])
+                for k, v in cfg.items():
+                    setattr(d, k, v)
+                args = (d, x, W[i], self.net.b32[i], self.skip_of.get(i), y)
+                ops.npvs_sparse_conv_fwd(*args)
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g):
+                    for _ in range(reps):
+                        ops.npvs_sparse_conv_fwd(*args)
+                g.replay()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                g.replay()
+                e1.record()
+                torch.cuda.synchronize()
+                us = e0.elapsed_time(e1) * 1000.0 / reps
+                if best is None or us < best[1]:
+                    best = (cfg, us)
+            for k, v in best[0].items():
+                setattr(self.descs[i], k, v)
+            chosen[l.name] = best
+            x = y
+        self.run(boxes, box_offsets, cams_dev, want_probs=False)   # outputs with the chosen configs
+        torch.cuda.synchronize()
+        return chosen
+
+    def deinterleave(self, want_probs=True):
+        lv0 = self.levels[0]
+        with self._t("deinterleave"):
+            ops.npvs_deinterleave(self.logits, lv0.table, lv0.n_rows, self.grid, self.wl.d, self.tau, self.occ,
+                                  self.pvs, probs_out=self.probs if want_probs else None, capacity=lv0.capacity)
+
+    def run(self, boxes, box_offsets, cams_dev, want_probs=True):
+        self.froxelize(boxes, box_offsets, cams_dev)
+        self.interleave()
+        self.rulebooks()
+        self.network()
+        self.deinterleave(want_probs)
+
+    # ---- CUDA graph of one frame ------------------------------------------------------------
+    def capture(self, boxes, box_offsets, cams_dev, want_probs=False, timer: Optional[StageTimer] = None):
+        """Captures one frame into a CUDA graph over fixed input buffers (boxes, box_offsets,
+        cams_dev); refill those buffers and call graph.replay() per frame. With `timer`, the stage
+        events are captured too and hold the stage times of the latest replay."""
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self.run(boxes, box_offsets, cams_dev, want_probs)   # warm-up outside capture
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        self.timer = timer
+        try:
+            with torch.cuda.graph(g):
+                self.run(boxes, box_offsets, cams_dev, want_probs)
+        finally:
+            self.timer = None
+        return g
+
+    def frame_from_host(self, graph, cam_buf, cam_host, pvs_host):
+        """One frame through a captured graph with host buffers: upload the camera (pinned host
+        npvs_camera bytes), replay, download the PVS bits into pinned host memory (async)."""
+        cam_buf.copy_(cam_host, non_blocking=True)
+        graph.replay()
+        pvs_host.copy_(self.pvs, non_blocking=True)

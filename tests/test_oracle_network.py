@@ -122,3 +122,25 @@ def test_gradients_match_central_differences(which):
                 g = float(P.grad.view(-1)[idx])
                 # central-difference rounding error ~ eps * L / h
                 assert abs(g - fd) <= 1e-5 * max(abs(g), abs(fd)) + 1e-8 * abs(float(L.detach())), (layers[li].name, g, fd)
+
+
+def test_rulebook_oracle_by_brute_force():
+    """nbr[n][k] = m exactly when coords[m] - coords[n] is offset k (all pairs); parents equal
+    the unique floor(p/2) set computed independently; down/up maps invert each other."""
+    from oracle import rulebook as RB
+    rng = np.random.default_rng(4)
+    lv, _ = random_level(rng, (2, 4, 6, 6), 0.3)
+    c = lv.coords.numpy()
+    nbr = RB.neighbour_map(c)
+    exp = np.full_like(nbr, -1)
+    for n in range(len(c)):
+        for m in range(len(c)):
+            dlt = c[m] - c[n]
+            if dlt[0] == 0 and np.all(np.abs(dlt[1:]) <= 1):
+                exp[n, ((dlt[1] + 1) * 3 + dlt[2] + 1) * 3 + dlt[3] + 1] = m
+    np.testing.assert_array_equal(nbr, exp)
+    parents, down, up = RB.parent_level(c)
+    np.testing.assert_array_equal(parents, lv.parent().coords.numpy())
+    for n in range(len(c)):
+        assert down[up[n] // 8, up[n] % 8] == n
+    assert (down >= 0).sum() == len(c)
