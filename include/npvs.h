@@ -214,6 +214,24 @@ npvs_status npvs_interleave(const uint32_t* occ_bits, npvs_grid grid, int32_t d,
                             int32_t* n_active, int32_t* table, int32_t* status, void* workspace,
                             size_t workspace_bytes, void* stream);
 
+/* npvs_interleave for callers that cannot allocate device memory (the paper has no counterpart;
+ * this is an interface convenience). Same arguments and results as npvs_interleave, without the
+ * workspace: the scratch lives in a fixed 128 KiB array inside the library's device memory, which
+ * every GPU that loads the library keeps until the process exits. Meant for callers that must not
+ * allocate or free device memory, e.g. an engine that reserves its whole GPU heap at start-up, or code
+ * on a frame's critical path where cudaMalloc / cudaFree (which may synchronise the device) is not
+ * allowed. It allocates nothing itself.
+ *  - Limit: B * (W/d) * (H/d) * (D/d) <= 4,194,304 coarse sites; larger grids return
+ *    NPVS_ERR_UNSUPPORTED with a message (use npvs_interleave and a workspace).
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ *    device current; make that first call before any stream capture on the device.
+ *  - All calls on a device share the one array and it keeps the last call's contents; no part of it
+ *    needs to start at zero (each call rewrites what it reads), but calls that overlap on the GPU (e.g.
+ *    from two streams at once) race on it and must be serialised by the caller. */
+npvs_status npvs_interleave_noalloc(const uint32_t* occ_bits, npvs_grid grid, int32_t d, int32_t in_ch,
+                                    int32_t feat_dtype, int32_t capacity, int32_t* coords, void* feats,
+                                    int32_t* n_active, int32_t* table, int32_t* status, void* stream);
+
 /* Sec. 3.3 g_d^-1 with the Sec. 3.1 threshold and the Sec. 3.2 mask: for every froxel, p =
  * sigmoid(logit) of its site's channel (0 for inactive sites) in binary32 (CUDA expf);
  * pvs bit = (p >= tau) AND mask bit. logits: device float [cap][d^3]; table: level-0 table;

@@ -68,6 +68,7 @@ SIGNATURES = {
     "npvs_froxelize": (I32, [P, P, I32, P, Grid, I32, P, P, SZ, P]),
     "npvs_interleave_workspace_bytes": (SZ, [Grid, I32]),
     "npvs_interleave": (I32, [P, Grid, I32, I32, I32, I32, P, P, P, P, P, P, SZ, P]),
+    "npvs_interleave_noalloc": (I32, [P, Grid, I32, I32, I32, I32, P, P, P, P, P, P]),
     "npvs_deinterleave": (I32, [P, P, P, Grid, I32, ctypes.c_float, P, P, P, I32, P]),
     "npvs_rulebook_workspace_bytes": (SZ, [Dims]),
     "npvs_build_rulebook": (I32, [I32, ctypes.POINTER(Level), ctypes.POINTER(Level), P, P, P, P, SZ, P]),

@@ -233,3 +233,87 @@ extern "C" npvs_status npvs_deinterleave(const float* logits, const int32_t* tab
     }
     return NPVS_OK;
 }
+
+// ---- interleave for callers that cannot allocate ----------------------------------------------
+//
+// npvs_interleave needs a small scratch area (per-CTA counts and their prefix sums) that the caller
+// normally passes in. Some callers cannot hand out device memory at all: a renderer or game engine
+// that reserves its whole GPU heap at start-up and forbids allocations during a frame, or code that
+// runs where calling cudaMalloc is not permitted (inside a frame's time budget, or from a thread
+// that must not synchronise the device, which cudaMalloc/cudaFree may do). For them
+// npvs_interleave_noalloc keeps that scratch in a fixed array that lives in the library's own
+// device memory for as long as the library is loaded.
+#include <mutex>
+
+namespace {
+constexpr long long kNoAllocMaxSites = 1ll << 22;  // 4,194,304 coarse sites per call (all batches)
+constexpr int kNoAllocMaxCtas = (int)(kNoAllocMaxSites / npvs::kSitesPerCta);
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+int* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+}  // namespace
+
+// counts [kNoAllocMaxCtas + 1] then offsets [kNoAllocMaxCtas + 1] (128 KiB per device)
+static __device__ __align__(256) int npvs_interleave_scratch[2 * (kNoAllocMaxCtas + 1)];
+
+extern "C" npvs_status npvs_interleave_noalloc(const uint32_t* occ_bits, npvs_grid g, int32_t d, int32_t in_ch,
+                                               int32_t feat_dtype, int32_t capacity, int32_t* coords, void* feats,
+                                               int32_t* n_active, int32_t* table, int32_t* status, void* stream) {
+    NPVS_REQUIRE(occ_bits && coords && feats && n_active, NPVS_ERR_INVALID_ARG,
+                 "npvs_interleave_noalloc: NULL pointer");
+    NPVS_REQUIRE(valid_d(d), NPVS_ERR_UNSUPPORTED, "npvs_interleave_noalloc: d must divide 32");
+    NPVS_REQUIRE(g.W > 0 && g.H > 0 && g.D > 0 && g.B > 0 && g.W % 32 == 0 && g.W % d == 0 &&
+                     g.H % d == 0 && g.D % d == 0,
+                 NPVS_ERR_UNSUPPORTED, "npvs_interleave_noalloc: grid must be a multiple of d (and W of 32)");
+    NPVS_REQUIRE(in_ch == 1 || in_ch == 2, NPVS_ERR_UNSUPPORTED, "npvs_interleave_noalloc: in_ch must be 1 or 2");
+    NPVS_REQUIRE(feat_dtype == NPVS_F32 || feat_dtype == NPVS_BF16 || feat_dtype == NPVS_F64,
+                 NPVS_ERR_UNSUPPORTED, "npvs_interleave_noalloc: bad feat_dtype");
+    NPVS_REQUIRE(capacity >= 0, NPVS_ERR_INVALID_ARG, "npvs_interleave_noalloc: capacity < 0");
+    const long long n_sites = (long long)g.B * (g.W / d) * (g.H / d) * (g.D / d);
+    if (n_sites > kNoAllocMaxSites) {
+        set_error("npvs_interleave_noalloc: %lld coarse sites exceed the fixed scratch limit of %lld "
+                  "(use npvs_interleave with a workspace)",
+                  n_sites, kNoAllocMaxSites);
+        return NPVS_ERR_UNSUPPORTED;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+        set_error("npvs_interleave_noalloc: no usable current device");
+        return NPVS_ERR_CUDA;
+    }
+    int* scratch;
+    {
+        // the device address of the array, looked up once per device (with that device current)
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (g_noalloc_ptr[dev] == nullptr) {
+            void* ptr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&ptr, npvs_interleave_scratch);
+            if (e != cudaSuccess || ptr == nullptr) {
+                set_error("npvs_interleave_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+                return NPVS_ERR_CUDA;
+            }
+            g_noalloc_ptr[dev] = static_cast<int*>(ptr);
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    cudaStream_t st = as_stream(stream);
+    ILParams p;
+    p.bits = occ_bits;
+    p.g = g;
+    p.d = d;
+    p.in_ch = in_ch;
+    p.dtype = feat_dtype;
+    p.cap = capacity;
+    p.Xc = g.W / d;
+    p.Yc = g.H / d;
+    p.Zc = g.D / d;
+    p.n_sites = n_sites;
+    const int nb = ceil_div(p.n_sites, kSitesPerCta);
+    int* counts = scratch;                      // fully rewritten by every call before it is read
+    int* offs = scratch + kNoAllocMaxCtas + 1;  // likewise
+    il_count_kernel<<<nb, kSitesPerCta, 0, st>>>(p, counts);
+    NPVS_TRY(check_launch("il_count_kernel"));
+    NPVS_TRY(scan_block_counts(counts, offs, nb, n_active, capacity, status, st));
+    il_write_kernel<<<nb, kSitesPerCta, 0, st>>>(p, offs, coords, feats, table, status);
+    return check_launch("il_write_kernel");
+}

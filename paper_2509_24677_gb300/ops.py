@@ -122,6 +122,16 @@ def npvs_interleave(occ_bits, g: L.Grid, d: int, in_ch: int, feat_dtype: int, ca
           "npvs_interleave")
 
 
+def npvs_interleave_noalloc(occ_bits, g: L.Grid, d: int, in_ch: int, feat_dtype: int, capacity: int, coords,
+                            feats, n_active, table=None, status=None, stream=None):
+    """npvs_interleave without a workspace argument, for callers that cannot allocate device memory:
+    the library keeps the scratch in a fixed device array (limit and sharing rules in npvs.h)."""
+    _need_cuda(occ_bits, coords, feats, n_active, table, status)
+    check(_lib().npvs_interleave_noalloc(_p(occ_bits), g, d, in_ch, feat_dtype, capacity, _p(coords), _p(feats),
+                                         _p(n_active), _p(table), _p(status), _s(stream)),
+          "npvs_interleave_noalloc")
+
+
 def npvs_deinterleave(logits, table, n_active, g: L.Grid, d: int, tau: float, mask_bits, pvs_bits,
                       probs_out=None, capacity: int = 0, stream=None):
     _need_cuda(logits, table, n_active, mask_bits, pvs_bits, probs_out)
