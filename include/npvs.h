@@ -106,7 +106,7 @@ typedef struct {
     int32_t* table;   /* device [B*Z*Y*X] */
 } npvs_level;
 
-typedef enum { NPVS_RB_SUBM3 = 0, NPVS_RB_DOWN2 = 1 } npvs_rulebook_kind;
+typedef enum { NPVS_RB_SUBM3 = 0, NPVS_RB_DOWN2 = 1, NPVS_RB_SUBM3_TABLE = 2 } npvs_rulebook_kind;
 
 typedef enum {
     NPVS_CONV_SUBM3 = 0, /* submanifold 3x3x3: output set = input set */
@@ -248,6 +248,8 @@ size_t npvs_rulebook_workspace_bytes(npvs_dims dims);
 /* SUBM3 (out_level, map2 unused): fills in->table from in->coords (-1 elsewhere) and writes the
  * neighbour map map [in->capacity][27]: entry k of row n is the row of site coords[n] + offset_k
  * or -1 (absent or outside the grid).
+ * SUBM3_TABLE: the same neighbour map, with in->table already filled for every site of the level
+ * (as npvs_interleave's table output and a DOWN2 rulebook's out->table are).
  * DOWN2: from in->table builds the parent level: out->coords / out->n_rows / out->table for the
  * sites {floor(p/2)} in linear order (out->dims must be in->dims halved; all even), map
  * [out->capacity][8] = rows of each parent's children (tap (cz*2+cy)*2+cx, -1 if absent), and

@@ -22,6 +22,7 @@ void set_error(const char* fmt, ...) {
 // One CTA of 1024 threads scans n block counts in chunks of 1024.
 __global__ void scan_block_counts_kernel(const int* in, int* out, int n, int* total_out, int cap,
                                          int32_t* status) {
+    pdl_begin();
     __shared__ int sw[33];
     int carry = 0;
     for (int base = 0; base < n; base += blockDim.x) {
@@ -44,7 +45,7 @@ __global__ void scan_block_counts_kernel(const int* in, int* out, int n, int* to
 
 npvs_status scan_block_counts(const int* in, int* out, int n, int* total_out, int cap,
                               int32_t* status, cudaStream_t st) {
-    scan_block_counts_kernel<<<1, 1024, 0, st>>>(in, out, n, total_out, cap, status);
+    launch_k(scan_block_counts_kernel, 1, 1024, 0, st, in, out, n, total_out, cap, status);
     return check_launch("scan_block_counts");
 }
 

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <utility>
 #include <cstdarg>
 #include <cstdio>
 
@@ -47,6 +48,27 @@ inline npvs_status check_launch(const char* what) {
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Every kernel of the library is launched with programmatic stream serialisation: the next kernel
+// on the stream may be launched and scheduled while this one finishes. Each kernel therefore
+// starts with pdl_begin(): griddepcontrol.wait (returns once every earlier kernel on the stream has
+// completed and its writes are visible; a no-op without the attribute), then
+// griddepcontrol.launch_dependents (lets the following kernel start its own launch).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                            Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 constexpr int kNumSMs = 152;
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
@@ -72,6 +94,11 @@ struct Arena {
 };
 
 // ---- device helpers -------------------------------------------------------------------------
+
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 __device__ __forceinline__ void raise_status(int32_t* status, npvs_status s) {
     if (status) atomicOr(status, 1 << (int)s);

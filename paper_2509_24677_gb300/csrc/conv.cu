@@ -19,6 +19,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) conv_simt_kernel(npvs_conv_desc dsc, const T* __restrict__ x,
                                                         const T* __restrict__ w, const float* __restrict__ bias,
                                                         const T* __restrict__ skip, T* __restrict__ y) {
+    pdl_begin();
     __shared__ T sA[BK][BM + 1];
     __shared__ T sB[BK][BN];
     __shared__ int sRow[BM];
@@ -103,10 +104,10 @@ extern "C" npvs_status npvs_sparse_conv_fwd(const npvs_conv_desc* dsc, const voi
     if (dsc->dtype == NPVS_BF16) return conv_tc_fwd(*dsc, x, w, bias, skip, y, st);
     dim3 grid(ceil_div(dsc->cap_out, BM), ceil_div(dsc->cout, BN));
     if (dsc->dtype == NPVS_F32) {
-        conv_simt_kernel<float><<<grid, 256, 0, st>>>(*dsc, (const float*)x, (const float*)w, bias, (const float*)skip,
+        launch_k(conv_simt_kernel<float>, grid, 256, 0, st, *dsc, (const float*)x, (const float*)w, bias, (const float*)skip,
                                                       (float*)y);
     } else if (dsc->dtype == NPVS_F64) {
-        conv_simt_kernel<double><<<grid, 256, 0, st>>>(*dsc, (const double*)x, (const double*)w, bias,
+        launch_k(conv_simt_kernel<double>, grid, 256, 0, st, *dsc, (const double*)x, (const double*)w, bias,
                                                        (const double*)skip, (double*)y);
     } else {
         return fail(NPVS_ERR_UNSUPPORTED, "npvs_sparse_conv_fwd: unknown dtype");

@@ -258,6 +258,7 @@ __device__ __forceinline__ void store16(const TcParams& p, int n, int ng, const 
 template <int LAG, int PW>
 __global__ void __launch_bounds__(threads_for(PW), 1)
     conv_tc_kernel(const TcParams p, const __grid_constant__ CUtensorMap tmap) {
+    pdl_begin();
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int S = p.stages;
@@ -621,6 +622,7 @@ __global__ void __launch_bounds__(256) conv_reduce_kernel(const float* __restric
                                                           const int32_t* __restrict__ n_out_p, int cap_out, int cout,
                                                           const float* __restrict__ bias, int relu,
                                                           const __nv_bfloat16* __restrict__ skip, OutT* __restrict__ y) {
+    pdl_begin();
     const int n_out = min(*n_out_p, cap_out);
     const int G = cout >> 2;
     const long long total = (long long)n_out * G;
@@ -682,6 +684,7 @@ __global__ void __launch_bounds__(256) conv_reduce_kernel(const float* __restric
 // have n = j * cout + o and k = ci; the direct forms have n = o and k = t * cin + ci.
 __global__ void pack_weights_kernel(int kind, int cin, int cout, TcShape sh, const float* __restrict__ w,
                                     __nv_bfloat16* __restrict__ out) {
+    pdl_begin();
     const size_t total = (size_t)sh.KB * sh.Npad * sh.BKE;
     const int nchunk = sh.BKE / 8;
     const bool colblocks = sh.J > 1;
@@ -743,7 +746,7 @@ npvs_status launch_tc(const TcParams& p, const CUtensorMap& tm, int grid, size_t
         cudaFuncSetAttribute(conv_tc_kernel<LAG, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
         attr_set = true;
     }
-    conv_tc_kernel<LAG, PW><<<grid, threads_for(PW), smem, st>>>(p, tm);
+    launch_k(conv_tc_kernel<LAG, PW>, grid, threads_for(PW), smem, st, p, tm);
     return check_launch("conv_tc_kernel");
 }
 
@@ -924,10 +927,10 @@ npvs_status conv_tc_fwd(const npvs_conv_desc& d, const void* x, const void* w, c
         const long long work = (long long)d.cap_out * (d.cout / 4);
         const int grid = (int)std::max<long long>(1, std::min<long long>(ceil_div(work, 256), kNumSMs * 8));
         if (d.out_f32)
-            conv_reduce_kernel<float><<<grid, 256, 0, st>>>(T, sh.Ntot, d.map, taps, d.n_out, d.cap_out, d.cout, bias,
+            launch_k(conv_reduce_kernel<float>, grid, 256, 0, st, T, sh.Ntot, d.map, taps, d.n_out, d.cap_out, d.cout, bias,
                                                             d.relu, (const __nv_bfloat16*)skip, (float*)y);
         else
-            conv_reduce_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(T, sh.Ntot, d.map, taps, d.n_out, d.cap_out, d.cout,
+            launch_k(conv_reduce_kernel<__nv_bfloat16>, grid, 256, 0, st, T, sh.Ntot, d.map, taps, d.n_out, d.cap_out, d.cout,
                                                                     bias, d.relu, (const __nv_bfloat16*)skip,
                                                                     (__nv_bfloat16*)y);
         return check_launch("conv_reduce_kernel");
@@ -974,7 +977,7 @@ extern "C" npvs_status npvs_pack_weights(int32_t kind, int32_t cin, int32_t cout
         TcShape sh = tc_shape(kind, cin, cout, f);
         const size_t total = (size_t)sh.KB * sh.Npad * sh.BKE;
         const int grid = (int)std::min<size_t>((total + 255) / 256, (size_t)kNumSMs * 16);
-        pack_weights_kernel<<<grid, 256, 0, as_stream(stream)>>>(kind, cin, cout, sh, w, (__nv_bfloat16*)out);
+        launch_k(pack_weights_kernel, grid, 256, 0, as_stream(stream), kind, cin, cout, sh, w, (__nv_bfloat16*)out);
         NPVS_TRY(check_launch("pack_weights_kernel"));
         out += packed_image_bytes(kind, cin, cout, f);
     }

@@ -31,6 +31,7 @@ __device__ __forceinline__ int batch_of_box(const int32_t* off, int B, int j) {
 __global__ void face_setup_kernel(const float* __restrict__ boxes, const int32_t* __restrict__ box_off,
                                   int n_boxes, const npvs_camera* __restrict__ cams, npvs_grid g,
                                   FaceRec* __restrict__ faces, int* __restrict__ counts) {
+    pdl_begin();
     int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= n_boxes * 6) return;
     int j = f / 6, fl = f % 6, axis = fl >> 1, side = fl & 1;
@@ -112,6 +113,7 @@ __global__ void face_setup_kernel(const float* __restrict__ boxes, const int32_t
 // Per-chunk exclusive scan of counts into 64-bit offsets; chunk sums for the second level.
 __global__ void chunk_scan_kernel(const int* __restrict__ counts, long long* __restrict__ offs, int n,
                                   int* __restrict__ chunk_sum) {
+    pdl_begin();
     __shared__ int sw[33];
     int i = blockIdx.x * kScanChunk + threadIdx.x;
     int v = i < n ? counts[i] : 0;
@@ -123,6 +125,7 @@ __global__ void chunk_scan_kernel(const int* __restrict__ counts, long long* __r
 
 __global__ void chunk_add_kernel(long long* __restrict__ offs, int n, const int* __restrict__ chunk_off,
                                  const int* __restrict__ counts, long long* __restrict__ total) {
+    pdl_begin();
     int i = blockIdx.x * kScanChunk + threadIdx.x;
     if (i < n) {
         long long o = offs[i] + chunk_off[blockIdx.x];
@@ -140,10 +143,15 @@ __device__ __forceinline__ int slice_of(const float* __restrict__ z, int D, floa
     return lo;
 }
 
+// SS: the supersampling factor as a compile-time constant (0: runtime value s, up to 16)
+template <int SS>
 __global__ void __launch_bounds__(256) froxel_items_kernel(
     const FaceRec* __restrict__ faces, const long long* __restrict__ offs, int n_faces,
-    const long long* __restrict__ total_p, const npvs_camera* __restrict__ cams, npvs_grid g, int s,
+    const long long* __restrict__ total_p, const npvs_camera* __restrict__ cams, npvs_grid g, int s_rt,
     uint32_t* __restrict__ bits) {
+    pdl_begin();
+    constexpr int CAP = SS ? SS : 16;
+    const int s = SS ? SS : s_rt;
     const long long total = *total_p;
     const int sW = s * g.W, sH = s * g.H, WW = g.W >> 5;
     const float fsW = (float)sW, fsH = (float)sH;
@@ -164,34 +172,50 @@ __global__ void __launch_bounds__(256) froxel_items_kernel(
         const float r_ax = c.right[ax], r1 = c.right[j1], r2 = c.right[j2];
         const float u_ax = c.up[ax], u1 = c.up[j1], u2 = c.up[j2];
         const float tanh_ = c.tan_half;
-        const float z0 = c.slices[0], zD = c.slices[g.D];
+        const float* z = c.slices;
+        const float z0 = z[0], zD = z[g.D];
         const float num = __fsub_rn(fr.P, o_ax);
         size_t word_base = (((size_t)fr.b * g.D) * g.H + y) * WW + (x >> 5);
         const uint32_t bit = 1u << (x & 31);
+        // ray direction parts that depend on the sub-column a only: f_i + (n_x tan) r_i, each
+        // operation rounded as in the per-ray definition
+        float ca_ax[CAP], ca_1[CAP], ca_2[CAP];
+#pragma unroll
+        for (int i = 0; i < CAP; ++i) {
+            if (i >= s) break;
+            const float nx = __fdiv_rn((float)(2 * (x * s + i) + 1 - sW), fsW);
+            const float sx = __fmul_rn(nx, tanh_);
+            ca_ax[i] = __fadd_rn(f_ax, __fmul_rn(sx, r_ax));
+            ca_1[i] = __fadd_rn(f1, __fmul_rn(sx, r1));
+            ca_2[i] = __fadd_rn(f2, __fmul_rn(sx, r2));
+        }
         int last_k = -1;
+        float zlo = 0.f, zhi = -1.f;  // slice interval of last_k
         for (int bb = y * s; bb < y * s + s; ++bb) {
-            float ny = __fdiv_rn((float)(2 * bb + 1 - sH), fsH);
-            float sy = __fmul_rn(ny, tanh_);
-            for (int a = x * s; a < x * s + s; ++a) {
-                float nx = __fdiv_rn((float)(2 * a + 1 - sW), fsW);
-                float sx = __fmul_rn(nx, tanh_);
-                float d_ax = __fadd_rn(__fadd_rn(f_ax, __fmul_rn(sx, r_ax)), __fmul_rn(sy, u_ax));
+            const float ny = __fdiv_rn((float)(2 * bb + 1 - sH), fsH);
+            const float sy = __fmul_rn(ny, tanh_);
+            const float su_ax = __fmul_rn(sy, u_ax), su_1 = __fmul_rn(sy, u1), su_2 = __fmul_rn(sy, u2);
+#pragma unroll
+            for (int i = 0; i < CAP; ++i) {
+                if (i >= s) break;
+                const float d_ax = __fadd_rn(ca_ax[i], su_ax);
                 if (d_ax == 0.0f) continue;
-                float t = __fdiv_rn(num, d_ax);
+                const float t = __fdiv_rn(num, d_ax);
                 if (!(t >= z0 && t < zD)) continue;
-                float d1 = __fadd_rn(__fadd_rn(f1, __fmul_rn(sx, r1)), __fmul_rn(sy, u1));
-                float h1 = __fadd_rn(o1, __fmul_rn(t, d1));
+                const float h1 = __fadd_rn(o1, __fmul_rn(t, __fadd_rn(ca_1[i], su_1)));
                 if (!(h1 >= fr.lo1 && h1 <= fr.hi1)) continue;
-                float d2 = __fadd_rn(__fadd_rn(f2, __fmul_rn(sx, r2)), __fmul_rn(sy, u2));
-                float h2 = __fadd_rn(o2, __fmul_rn(t, d2));
+                const float h2 = __fadd_rn(o2, __fmul_rn(t, __fadd_rn(ca_2[i], su_2)));
                 if (!(h2 >= fr.lo2 && h2 <= fr.hi2)) continue;
-                int k = slice_of(c.slices, g.D, t);
-                if (k != last_k) {
+                if (!(t >= zlo && t < zhi)) {
+                    const int k = slice_of(z, g.D, t);
                     atomicOr(bits + word_base + (size_t)k * g.H * WW, bit);
                     last_k = k;
+                    zlo = z[k];
+                    zhi = z[k + 1];
                 }
             }
         }
+        (void)last_k;
     }
 }
 
@@ -218,8 +242,8 @@ extern "C" npvs_status npvs_froxelize(const float* boxes, const int32_t* box_off
     NPVS_REQUIRE(g.W > 0 && g.H > 0 && g.D > 0 && g.B > 0 && g.W % 32 == 0, NPVS_ERR_UNSUPPORTED,
                  "npvs_froxelize: need W % 32 == 0 and positive sizes");
     NPVS_REQUIRE(g.D <= NPVS_MAX_SLICES, NPVS_ERR_UNSUPPORTED, "npvs_froxelize: D > NPVS_MAX_SLICES");
-    NPVS_REQUIRE(s >= 1 && (long long)s * g.W <= 65536 && (long long)s * g.H <= 65536,
-                 NPVS_ERR_UNSUPPORTED, "npvs_froxelize: supersampled size out of range");
+    NPVS_REQUIRE(s >= 1 && s <= 16 && (long long)s * g.W <= 65536 && (long long)s * g.H <= 65536,
+                 NPVS_ERR_UNSUPPORTED, "npvs_froxelize: supersampling must be 1..16 and s*W, s*H <= 65536");
     NPVS_REQUIRE(workspace_bytes >= froxel_ws(n_boxes) && workspace, NPVS_ERR_WORKSPACE,
                  "npvs_froxelize: workspace too small");
     cudaStream_t st = as_stream(stream);
@@ -235,13 +259,19 @@ extern "C" npvs_status npvs_froxelize(const float* boxes, const int32_t* box_off
     int* csum = ar.take<int>(nchunk + 1);
     int* coff = ar.take<int>(nchunk + 1);
     long long* total = ar.take<long long>(1);
-    face_setup_kernel<<<ceil_div(F, 256), 256, 0, st>>>(boxes, box_offsets, n_boxes, cams, g, faces, counts);
+    launch_k(face_setup_kernel, ceil_div(F, 256), 256, 0, st, boxes, box_offsets, n_boxes, cams, g, faces, counts);
     NPVS_TRY(check_launch("face_setup_kernel"));
-    chunk_scan_kernel<<<nchunk, kScanChunk, 0, st>>>(counts, offs, F, csum);
+    launch_k(chunk_scan_kernel, nchunk, kScanChunk, 0, st, counts, offs, F, csum);
     NPVS_TRY(check_launch("chunk_scan_kernel"));
     NPVS_TRY(scan_block_counts(csum, coff, nchunk, csum + nchunk, -1, nullptr, st));
-    chunk_add_kernel<<<nchunk, kScanChunk, 0, st>>>(offs, F, coff, counts, total);
+    launch_k(chunk_add_kernel, nchunk, kScanChunk, 0, st, offs, F, coff, counts, total);
     NPVS_TRY(check_launch("chunk_add_kernel"));
-    froxel_items_kernel<<<kNumSMs * 8, 256, 0, st>>>(faces, offs, F, total, cams, g, s, occ_bits);
+    switch (s) {
+        case 1: launch_k(froxel_items_kernel<1>, kNumSMs * 8, 256, 0, st, faces, offs, F, total, cams, g, s, occ_bits); break;
+        case 2: launch_k(froxel_items_kernel<2>, kNumSMs * 8, 256, 0, st, faces, offs, F, total, cams, g, s, occ_bits); break;
+        case 4: launch_k(froxel_items_kernel<4>, kNumSMs * 8, 256, 0, st, faces, offs, F, total, cams, g, s, occ_bits); break;
+        case 8: launch_k(froxel_items_kernel<8>, kNumSMs * 8, 256, 0, st, faces, offs, F, total, cams, g, s, occ_bits); break;
+        default: launch_k(froxel_items_kernel<0>, kNumSMs * 8, 256, 0, st, faces, offs, F, total, cams, g, s, occ_bits);
+    }
     return check_launch("froxel_items_kernel");
 }

@@ -42,6 +42,7 @@ __device__ __forceinline__ bool site_active(const ILParams& p, long long site, i
 }
 
 __global__ void __launch_bounds__(kSitesPerCta) il_count_kernel(ILParams p, int* __restrict__ counts) {
+    pdl_begin();
     long long site = (long long)blockIdx.x * kSitesPerCta + threadIdx.x;
     int b, Z, Y, X;
     int f = site < p.n_sites ? (int)site_active(p, site, b, Z, Y, X) : 0;
@@ -49,22 +50,34 @@ __global__ void __launch_bounds__(kSitesPerCta) il_count_kernel(ILParams p, int*
     if (threadIdx.x == 0) counts[blockIdx.x] = c;
 }
 
-// value of interleaved channel ch of site (b, Z, Y, X)
-__device__ __forceinline__ float il_value(const ILParams& p, int b, int Z, int Y, int X, int ch) {
-    const int d = p.d, d3 = d * d * d;
-    int c = ch / d3, r = ch - c * d3;
-    int dz = r / (d * d), dy = (r / d) % d, dx = r % d;
-    int x = d * X + dx, y = d * Y + dy, k = d * Z + dz;
-    const int WW = p.g.W >> 5;
-    uint32_t w = p.bits[(((size_t)b * p.g.D + k) * p.g.H + y) * WW + (x >> 5)];
-    bool occ = (w >> (x & 31)) & 1u;
-    if (c == 0) return occ ? 1.0f : 0.0f;
-    return occ ? __fdiv_rn((float)(2 * k + 1), (float)(2 * p.g.D)) : 0.0f;
+// Store n (4 or 8, or 1) consecutive channel values of one feature row.
+__device__ __forceinline__ void store_vals(void* feats, int dtype, size_t off, const float* v, int n) {
+    if (dtype == NPVS_BF16) {
+        __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(feats) + off;
+        __align__(16) __nv_bfloat16 h[8];
+        for (int q = 0; q < n; ++q) h[q] = __float2bfloat16_rn(v[q]);
+        if (n == 8) *reinterpret_cast<uint4*>(out) = *reinterpret_cast<uint4*>(h);
+        else if (n == 4) *reinterpret_cast<uint2*>(out) = *reinterpret_cast<uint2*>(h);
+        else for (int q = 0; q < n; ++q) out[q] = h[q];
+    } else if (dtype == NPVS_F32) {
+        float* out = reinterpret_cast<float*>(feats) + off;
+        if (n >= 4) {
+            for (int q = 0; q < n; q += 4) *reinterpret_cast<float4*>(out + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+        } else {
+            for (int q = 0; q < n; ++q) out[q] = v[q];
+        }
+    } else {
+        double* out = reinterpret_cast<double*>(feats) + off;
+        for (int q = 0; q < n; ++q) out[q] = (double)v[q];
+    }
 }
 
+// DD: the interleave factor as a compile-time constant (0: runtime p.d)
+template <int DD>
 __global__ void __launch_bounds__(kSitesPerCta) il_write_kernel(ILParams p, const int* __restrict__ block_off,
                                                                 int32_t* __restrict__ coords, void* __restrict__ feats,
                                                                 int32_t* __restrict__ table, int32_t* status) {
+    pdl_begin();
     __shared__ int sw[33];
     __shared__ int4 s_site[kSitesPerCta];
     __shared__ int s_rank[kSitesPerCta];
@@ -86,31 +99,36 @@ __global__ void __launch_bounds__(kSitesPerCta) il_write_kernel(ILParams p, cons
         s_rank[loc] = rank;
     }
     __syncthreads();
-    const int C = p.in_ch * p.d * p.d * p.d;
-    const int vec = (C % 8 == 0) ? 8 : 1;
-    const int chunks = C / vec;
-    for (int e = threadIdx.x; e < nloc * chunks; e += kSitesPerCta) {
-        int i = e / chunks, ch0 = (e - i * chunks) * vec;
-        int r = s_rank[i];
+    // one thread per (active site, dz): the d x d occupancy bits of that slab (d words), written as
+    // d^2 occupancy values and, with in_ch = 2, d^2 depth values (one quotient per slab)
+    const int d = DD ? DD : p.d, d2 = d * d, d3 = d2 * d, C = p.in_ch * d3, WW = p.g.W >> 5;
+    const int grp = d2 >= 8 ? 8 : d2;  // values per vector store
+    for (int e = threadIdx.x; e < nloc * d; e += kSitesPerCta) {
+        const int i = e / d, dz = e - i * d;
+        const int r = s_rank[i];
         if (r >= p.cap) continue;
-        int4 s = s_site[i];
-        size_t off = (size_t)r * C + ch0;
-        if (p.dtype == NPVS_BF16) {
-            __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(feats) + off;
-            if (vec == 8) {
-                __align__(16) __nv_bfloat16 v[8];
+        const int4 st = s_site[i];
+        const int k = d * st.y + dz, x0 = d * st.w;
+        const float dep = __fdiv_rn((float)(2 * k + 1), (float)(2 * p.g.D));
+        const uint32_t* wrow = p.bits + (((size_t)st.x * p.g.D + k) * p.g.H + (size_t)d * st.z) * WW + (x0 >> 5);
+        const size_t base = (size_t)r * C + (size_t)dz * d2;
+        float vo[8], vd[8];
+        int nv = 0, j0 = 0;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) v[q] = __float2bfloat16_rn(il_value(p, s.x, s.y, s.z, s.w, ch0 + q));
-                *reinterpret_cast<uint4*>(out) = *reinterpret_cast<uint4*>(v);
-            } else {
-                out[0] = __float2bfloat16_rn(il_value(p, s.x, s.y, s.z, s.w, ch0));
+        for (int dy = 0; dy < (DD ? DD : d); ++dy) {
+            const uint32_t wbits = wrow[(size_t)dy * WW] >> (x0 & 31);
+#pragma unroll
+            for (int dx = 0; dx < (DD ? DD : d); ++dx) {
+                const bool occ = (wbits >> dx) & 1u;
+                vo[nv] = occ ? 1.0f : 0.0f;
+                vd[nv] = occ ? dep : 0.0f;
+                if (++nv == grp) {
+                    store_vals(feats, p.dtype, base + j0, vo, grp);
+                    if (p.in_ch == 2) store_vals(feats, p.dtype, base + d3 + j0, vd, grp);
+                    j0 += grp;
+                    nv = 0;
+                }
             }
-        } else if (p.dtype == NPVS_F32) {
-            float* out = reinterpret_cast<float*>(feats) + off;
-            for (int q = 0; q < vec; ++q) out[q] = il_value(p, s.x, s.y, s.z, s.w, ch0 + q);
-        } else {
-            double* out = reinterpret_cast<double*>(feats) + off;
-            for (int q = 0; q < vec; ++q) out[q] = (double)il_value(p, s.x, s.y, s.z, s.w, ch0 + q);
         }
     }
 }
@@ -120,6 +138,7 @@ __global__ void __launch_bounds__(kSitesPerCta) il_write_kernel(ILParams p, cons
 __global__ void deinterleave_kernel(const float* __restrict__ logits, const int32_t* __restrict__ table,
                                     const int32_t* __restrict__ n_active, npvs_grid g, int d, float tau,
                                     const uint32_t* __restrict__ mask_bits, uint32_t* __restrict__ pvs) {
+    pdl_begin();
     const int WW = g.W >> 5;
     const long long n_words = (long long)g.B * g.D * g.H * WW;
     const int n = *n_active;
@@ -155,6 +174,7 @@ __global__ void deinterleave_kernel(const float* __restrict__ logits, const int3
 
 __global__ void sigmoid_rows_kernel(const float* __restrict__ logits, const int32_t* __restrict__ n_active,
                                     int d3, float* __restrict__ probs) {
+    pdl_begin();
     const long long n = (long long)(*n_active) * d3;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
@@ -167,6 +187,16 @@ __global__ void sigmoid_rows_kernel(const float* __restrict__ logits, const int3
 using namespace npvs;
 
 static bool valid_d(int d) { return d == 1 || d == 2 || d == 4 || d == 8 || d == 16 || d == 32; }
+
+static void launch_il_write(const ILParams& p, int nb, const int* offs, int32_t* coords, void* feats, int32_t* table,
+                            int32_t* status, cudaStream_t st) {
+    switch (p.d) {
+        case 2: launch_k(il_write_kernel<2>, nb, kSitesPerCta, 0, st, p, offs, coords, feats, table, status); break;
+        case 4: launch_k(il_write_kernel<4>, nb, kSitesPerCta, 0, st, p, offs, coords, feats, table, status); break;
+        case 8: launch_k(il_write_kernel<8>, nb, kSitesPerCta, 0, st, p, offs, coords, feats, table, status); break;
+        default: launch_k(il_write_kernel<0>, nb, kSitesPerCta, 0, st, p, offs, coords, feats, table, status);
+    }
+}
 
 extern "C" size_t npvs_interleave_workspace_bytes(npvs_grid g, int32_t d) {
     if (!valid_d(d) || d <= 0) return 0;
@@ -206,10 +236,10 @@ extern "C" npvs_status npvs_interleave(const uint32_t* occ_bits, npvs_grid g, in
     Arena ar(workspace, workspace_bytes);
     int* counts = ar.take<int>(nb + 1);
     int* offs = ar.take<int>(nb + 1);
-    il_count_kernel<<<nb, kSitesPerCta, 0, st>>>(p, counts);
+    launch_k(il_count_kernel, nb, kSitesPerCta, 0, st, p, counts);
     NPVS_TRY(check_launch("il_count_kernel"));
     NPVS_TRY(scan_block_counts(counts, offs, nb, n_active, capacity, status, st));
-    il_write_kernel<<<nb, kSitesPerCta, 0, st>>>(p, offs, coords, feats, table, status);
+    launch_il_write(p, nb, offs, coords, feats, table, status, st);
     return check_launch("il_write_kernel");
 }
 
@@ -223,12 +253,12 @@ extern "C" npvs_status npvs_deinterleave(const float* logits, const int32_t* tab
     cudaStream_t st = as_stream(stream);
     long long words = (long long)g.B * g.D * g.H * (g.W / 32);
     int blocks = (int)std::min<long long>(ceil_div(words, 256), kNumSMs * 16);
-    deinterleave_kernel<<<blocks, 256, 0, st>>>(logits, table, n_active, g, d, tau, mask_bits, pvs_bits);
+    launch_k(deinterleave_kernel, blocks, 256, 0, st, logits, table, n_active, g, d, tau, mask_bits, pvs_bits);
     NPVS_TRY(check_launch("deinterleave_kernel"));
     if (probs_out) {
         int d3 = d * d * d;
         int pb = (int)std::min<long long>(ceil_div((long long)capacity * d3, 256), kNumSMs * 16);
-        if (pb > 0) sigmoid_rows_kernel<<<pb, 256, 0, st>>>(logits, n_active, d3, probs_out);
+        if (pb > 0) launch_k(sigmoid_rows_kernel, pb, 256, 0, st, logits, n_active, d3, probs_out);
         NPVS_TRY(check_launch("sigmoid_rows_kernel"));
     }
     return NPVS_OK;
@@ -311,9 +341,9 @@ extern "C" npvs_status npvs_interleave_noalloc(const uint32_t* occ_bits, npvs_gr
     const int nb = ceil_div(p.n_sites, kSitesPerCta);
     int* counts = scratch;                      // fully rewritten by every call before it is read
     int* offs = scratch + kNoAllocMaxCtas + 1;  // likewise
-    il_count_kernel<<<nb, kSitesPerCta, 0, st>>>(p, counts);
+    launch_k(il_count_kernel, nb, kSitesPerCta, 0, st, p, counts);
     NPVS_TRY(check_launch("il_count_kernel"));
     NPVS_TRY(scan_block_counts(counts, offs, nb, n_active, capacity, status, st));
-    il_write_kernel<<<nb, kSitesPerCta, 0, st>>>(p, offs, coords, feats, table, status);
+    launch_il_write(p, nb, offs, coords, feats, table, status, st);
     return check_launch("il_write_kernel");
 }

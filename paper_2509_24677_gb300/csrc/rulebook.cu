@@ -14,6 +14,7 @@ constexpr int kCta = 256;
 
 __global__ void table_insert_kernel(const int32_t* __restrict__ coords, const int32_t* __restrict__ n_rows,
                                     int cap, npvs_dims d, int32_t* __restrict__ table) {
+    pdl_begin();
     const int n = min(*n_rows, cap);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int4 c = reinterpret_cast<const int4*>(coords)[i];
@@ -23,6 +24,7 @@ __global__ void table_insert_kernel(const int32_t* __restrict__ coords, const in
 
 __global__ void subm3_nbr_kernel(const int32_t* __restrict__ coords, const int32_t* __restrict__ n_rows, int cap,
                                  npvs_dims d, const int32_t* __restrict__ table, int32_t* __restrict__ nbr) {
+    pdl_begin();
     const long long n = (long long)min(*n_rows, cap) * 27;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (long long)gridDim.x * blockDim.x) {
@@ -57,6 +59,7 @@ __device__ __forceinline__ int child_row(const DownParams& p, int b, int Z, int 
 }
 
 __global__ void __launch_bounds__(kCta) down_count_kernel(DownParams p, int* __restrict__ counts) {
+    pdl_begin();
     long long s = (long long)blockIdx.x * kCta + threadIdx.x;
     int f = 0;
     if (s < p.n_sites) {
@@ -71,6 +74,7 @@ __global__ void __launch_bounds__(kCta) down_count_kernel(DownParams p, int* __r
 __global__ void __launch_bounds__(kCta) down_write_kernel(DownParams p, const int* __restrict__ block_off,
                                                           int32_t* __restrict__ coords, int32_t* __restrict__ table,
                                                           int32_t* __restrict__ down, int32_t* status) {
+    pdl_begin();
     __shared__ int sw[33];
     long long s = (long long)blockIdx.x * kCta + threadIdx.x;
     int b = 0, Z = 0, Y = 0, X = 0;
@@ -102,6 +106,7 @@ __global__ void __launch_bounds__(kCta) down_write_kernel(DownParams p, const in
 
 __global__ void up_map_kernel(const int32_t* __restrict__ fine_coords, const int32_t* __restrict__ n_fine, int cap,
                               npvs_dims cd, const int32_t* __restrict__ coarse_table, int32_t* __restrict__ up) {
+    pdl_begin();
     const int n = min(*n_fine, cap);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int4 c = reinterpret_cast<const int4*>(fine_coords)[i];
@@ -131,13 +136,16 @@ extern "C" npvs_status npvs_build_rulebook(int32_t kind, const npvs_level* in, c
     const npvs_dims fd = in->dims;
     NPVS_REQUIRE(fd.X > 0 && fd.Y > 0 && fd.Z > 0 && fd.B > 0, NPVS_ERR_INVALID_ARG, "npvs_build_rulebook: bad dims");
     cudaStream_t st = as_stream(stream);
-    if (kind == NPVS_RB_SUBM3) {
+    if (kind == NPVS_RB_SUBM3 || kind == NPVS_RB_SUBM3_TABLE) {
         NPVS_REQUIRE(in->coords && in->n_rows, NPVS_ERR_INVALID_ARG, "npvs_build_rulebook: level without coords");
-        size_t tb = (size_t)fd.B * fd.X * fd.Y * fd.Z * sizeof(int32_t);
-        if (cudaMemsetAsync(in->table, 0xFF, tb, st) != cudaSuccess) return check_launch("rulebook memset");
-        table_insert_kernel<<<grid_for(in->capacity), kCta, 0, st>>>(in->coords, in->n_rows, in->capacity, fd, in->table);
-        NPVS_TRY(check_launch("table_insert_kernel"));
-        subm3_nbr_kernel<<<grid_for((long long)in->capacity * 27), kCta, 0, st>>>(in->coords, in->n_rows, in->capacity,
+        if (kind == NPVS_RB_SUBM3) {
+            size_t tb = (size_t)fd.B * fd.X * fd.Y * fd.Z * sizeof(int32_t);
+            if (cudaMemsetAsync(in->table, 0xFF, tb, st) != cudaSuccess) return check_launch("rulebook memset");
+            launch_k(table_insert_kernel, grid_for(in->capacity), kCta, 0, st, in->coords, in->n_rows, in->capacity,
+                     fd, in->table);
+            NPVS_TRY(check_launch("table_insert_kernel"));
+        }
+        launch_k(subm3_nbr_kernel, grid_for((long long)in->capacity * 27), kCta, 0, st, in->coords, in->n_rows, in->capacity,
                                                                                  fd, in->table, map);
         return check_launch("subm3_nbr_kernel");
     }
@@ -159,11 +167,11 @@ extern "C" npvs_status npvs_build_rulebook(int32_t kind, const npvs_level* in, c
     Arena ar(workspace, workspace_bytes);
     int* counts = ar.take<int>(nb + 1);
     int* offs = ar.take<int>(nb + 1);
-    down_count_kernel<<<nb, kCta, 0, st>>>(p, counts);
+    launch_k(down_count_kernel, nb, kCta, 0, st, p, counts);
     NPVS_TRY(check_launch("down_count_kernel"));
     NPVS_TRY(scan_block_counts(counts, offs, nb, out->n_rows, out->capacity, status, st));
-    down_write_kernel<<<nb, kCta, 0, st>>>(p, offs, out->coords, out->table, map, status);
+    launch_k(down_write_kernel, nb, kCta, 0, st, p, offs, out->coords, out->table, map, status);
     NPVS_TRY(check_launch("down_write_kernel"));
-    up_map_kernel<<<grid_for(in->capacity), kCta, 0, st>>>(in->coords, in->n_rows, in->capacity, cd, out->table, map2);
+    launch_k(up_map_kernel, grid_for(in->capacity), kCta, 0, st, in->coords, in->n_rows, in->capacity, cd, out->table, map2);
     return check_launch("up_map_kernel");
 }

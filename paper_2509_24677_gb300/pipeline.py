@@ -179,7 +179,9 @@ class FramePipeline:
     def rulebooks(self):
         with self._t("rulebooks"):
             for li, lv in enumerate(self.levels):
-                ops.npvs_build_rulebook(L.RB_SUBM3, lv, None, lv.nbr, status=self.status, ws=self.ws)
+                # every level's table is already written (level 0 by the interleave, the others by
+                # the down rulebook), so only the neighbour map is built
+                ops.npvs_build_rulebook(L.RB_SUBM3_TABLE, lv, None, lv.nbr, status=self.status, ws=self.ws)
                 if li + 1 < self.n_levels:
                     nxt = self.levels[li + 1]
                     ops.npvs_build_rulebook(L.RB_DOWN2, lv, nxt, lv.down, lv.up, status=self.status, ws=self.ws)

@@ -231,19 +231,20 @@ def make_levels(occ_coarse, n_levels):
     return lvs, c0
 
 
-def build_rulebooks(lvs):
+def build_rulebooks(lvs, prebuilt=False):
     L, ops, _ = lib()
     for li, lv in enumerate(lvs):
-        ops.npvs_build_rulebook(L.RB_SUBM3, lv, None, lv.nbr)
+        ops.npvs_build_rulebook(L.RB_SUBM3_TABLE if (prebuilt and li > 0) else L.RB_SUBM3, lv, None, lv.nbr)
         if li + 1 < len(lvs):
             ops.npvs_build_rulebook(L.RB_DOWN2, lv, lvs[li + 1], lv.down, lv.up)
 
 
-def test_rulebooks_bit_exact():
+@pytest.mark.parametrize("prebuilt", [False, True])
+def test_rulebooks_bit_exact(prebuilt):
     rng = np.random.default_rng(3)
     occ = rng.random((2, 8, 12, 16)) < 0.15
     lvs, c0 = make_levels(occ, 3)
-    build_rulebooks(lvs)
+    build_rulebooks(lvs, prebuilt)
     torch.cuda.synchronize()
     coords = c0
     for li in range(3):
