@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle sample")
+    ap.add_argument("--no-train", action="store_true", help="skip the training-step measurement")
+    ap.add_argument("--train-points", type=int, default=256, help="ground-truth viewpoints per viewcell")
     return ap.parse_args()
 
 
@@ -223,6 +225,53 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_train(args, dev, flush):
+    """Training steps/s: the city256 network on batches of 8 viewcells (2x2x2 world units, two
+    street cells of each of 4 seeded cities), weighted Dice + repulsive visibility loss + BCE,
+    BF16 forward/backward on the tensor cores, FP32 master weights and Adam, one CUDA graph per
+    step. Ground truth: GPU ray casting from `train_points` viewpoints per cell, ANDed with G."""
+    from paper_2509_24677_gb300 import _lib as L
+    from paper_2509_24677_gb300 import data as Dm
+    from paper_2509_24677_gb300 import ops
+    from paper_2509_24677_gb300 import train as T
+    wl = I.workload(WORKLOAD)
+    pairs = Dm.city_training_set(4, 2, half=1.0)
+    t0 = time.perf_counter()
+    batch = Dm.make_batch([p[0] for p in pairs], [p[1] for p in pairs], wl, M=args.train_points, device=dev)
+    torch.cuda.synchronize()
+    t_gt = time.perf_counter() - t0
+    ws, bs = I.kaiming_uniform(wl.layers, seed=0)
+    tr = T.Trainer(wl, wl.layers, ws, bs, len(pairs), L.BF16, loss_prm=ops.loss_params(w_bce=1.0), device=dev)
+    tr.gt.copy_(batch.gt)
+    l0 = ops.npvs_launch_count()
+    g = tr.capture(batch.boxes, batch.box_offsets, batch.cams)
+    launches = (ops.npvs_launch_count() - l0) // 2
+    st = torch.cuda.current_stream()
+    losses, ev = [], []
+    for i in range(args.warmup + args.steps):
+        s_ = torch.cuda.Event(enable_timing=True)
+        e_ = torch.cuda.Event(enable_timing=True)
+        s_.record(st)
+        g.replay()
+        e_.record(st)
+        if i >= args.warmup:
+            ev.append((s_, e_))
+        if i == 0 or i == args.warmup + args.steps - 1:
+            torch.cuda.synchronize()
+            losses.append(float(tr.loss.item()))
+    torch.cuda.synchronize()
+    if ops.npvs_check_status(tr.pipe.status) != 0:
+        raise RuntimeError("device status set during the training steps")
+    ms = statistics.mean(s_.elapsed_time(e_) for s_, e_ in ev)
+    n_act = int(tr.pipe.levels[0].n_rows.item())
+    gt_bits = int(torch.bitwise_count(batch.gt).sum().item()) if hasattr(torch, "bitwise_count") else None
+    return {"steps_per_s": round(1000.0 / ms, 3), "ms_per_step": round(ms, 3), "batch": len(pairs), "dtype": "bf16",
+            "master": "fp32", "optimizer": "adam lr 1e-3", "loss": "dice(alpha 0.9)+rvl(lambda 0.99)+bce(w 1)",
+            "loss_first_last": [round(losses[0], 5), round(losses[-1], 5)], "gpu_launches_per_step": int(launches),
+            "active_sites_level0": n_act, "gt_points": args.train_points, "gt_seconds": round(t_gt, 2),
+            "gt_bits": gt_bits, "graph": "one CUDA graph replay per step; working set > L2"}
+
+
 def run_ours(args):
     from paper_2509_24677_gb300 import _lib as L
     from paper_2509_24677_gb300 import ops, pipeline as P
@@ -375,6 +424,9 @@ def run_ours(args):
     }
     if clk:
         line["clocks"] = clk
+    if not args.no_train:
+        del g16, g32, g16t
+        line["train"] = run_train(args, dev, flush)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cms, desc, cores, spent = cpu_oracle_frame_estimate(args.cpu_seconds)
         line["cpu_baseline"] = {"value": round(1000.0 / cms, 5), "unit": "frames/s", "cores": cores, "kind": "oracle",

@@ -274,10 +274,104 @@ size_t npvs_packed_weight_bytes(int32_t kind, int32_t cin, int32_t cout);
 npvs_status npvs_pack_weights(int32_t kind, int32_t cin, int32_t cout, const float* w,
                               void* packed, void* stream);
 
-/* y = act(b + conv(x)) (+ skip); see npvs_conv_desc. Output-stationary: every output row is
- * written exactly once (no atomics); rows >= *n_out are not touched. */
+/* y = act(b + conv(x)) (+ skip); see npvs_conv_desc. bias (nullable): [cout], FP32, or FP64 with
+ * dtype F64. Output-stationary: every output row is written exactly once (no atomics); rows >=
+ * *n_out are not touched. */
 npvs_status npvs_sparse_conv_fwd(const npvs_conv_desc* desc, const void* x, const void* w,
-                                 const float* bias, const void* skip, void* y, void* stream);
+                                 const void* bias, const void* skip, void* y, void* stream);
+
+/* ---- training targets: ground-truth PVS (Sec. 3.2) ---------------------------------------- */
+
+/* From-region visibility by ray casting: for each viewpoint p_m of batch element e (device
+ * float [B][n_points][3], world positions outside every box) and each pixel of the (s_gt W) x
+ * (s_gt H) raster of cams[e]'s directions (as npvs_froxelize), the nearest box hit t > 0 of
+ * p_m + t dir is reprojected into cams[e]'s frame; a hit inside the frustum sets its froxel in
+ * gt_bits [B][D][H][W/32] (zeroed here). With g_bits (nullable) the result is ANDed with the
+ * geometry grid. Binary32 arithmetic. n_points * s_gt^2 * W * H must be a multiple of 256. */
+npvs_status npvs_gt_raycast(const float* boxes, const int32_t* box_offsets, const npvs_camera* cams,
+                            const float* points, int32_t n_points, npvs_grid grid, int32_t s_gt,
+                            const uint32_t* g_bits, uint32_t* gt_bits, void* stream);
+
+/* ---- a10: sparse convolution backward ---------------------------------------------------- */
+
+/* Bytes of the workspace of npvs_sparse_conv_bwd for this convolution (the gradient g of the
+ * pre-activation, fixed-order partial sums of dW and db, the transposed weights and, for BF16,
+ * the workspace of the transposed forward convolution that computes dx). */
+size_t npvs_conv_bwd_workspace_bytes(const npvs_conv_desc* desc);
+
+/* Backward of npvs_sparse_conv_fwd with the same desc (Sec. 2.3 layers; gradients of the masked
+ * dense definition). With g = dy * 1[y > 0] (g = dy without ReLU):
+ *   db = sum_n g[n],   dW_t = sum_n x[map(n, t)]^T g[n],   dx = transposed convolution of g (+ dx_add)
+ *  x:      the forward input [cap_in][cin] (dtype; rows < n_in).
+ *  w:      master weights [taps][cin][cout]: FP32 for F32 and BF16, FP64 for F64 (not packed).
+ *  y:      the layer's output after ReLU and before a skip addition [cap_out][cout] (dtype);
+ *          read only with relu (NULL otherwise). ReLU with out_f32 is unsupported.
+ *  dy:     gradient of the output [cap_out][cout] (dtype, also for an out_f32 layer).
+ *  dx:     nullable [cap_in][cin] (dtype): gradient of x, rows < n_in written. dx_add (nullable,
+ *          same shape) is added to it: a gradient reaching x by another path (a skip).
+ *  dw, db: FP32 (FP64 for F64) [taps][cin][cout] and [cout], overwritten; db nullable.
+ *  The stride-2 kinds need map2 (the other map of the level pair), n_in and cap_in for dx.
+ *  Sums are taken in a fixed order: results are bitwise reproducible for the same capacities.
+ *  desc->workspace is not used; workspace must hold npvs_conv_bwd_workspace_bytes(desc). */
+npvs_status npvs_sparse_conv_bwd(const npvs_conv_desc* desc, const void* x, const void* w, const void* y,
+                                 const void* dy, void* dx, const void* dx_add, void* dw, void* db,
+                                 void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---- a8/a9: weighted Dice + repulsive visibility loss (Sec. 3.3) -------------------------- */
+
+/* Readings of Sec. 3.3 (the prose and printed formulas disagree on FN / FP): with y the ground
+ * truth bit, g the geometry bit and p~ = sigmoid(z) g per froxel of a sample,
+ *   TP = sum y p~, FP = sum (1-y) p~, GTP = popcount(GT), FN = GTP - TP, NOCC = sum g,
+ *   dice = 1 - (2TP + eps) / (2TP + alpha FN + (1-alpha) FP + eps)
+ *   attr = FN / (GTP + eps), rep = FP / (GTP + eps), bce = sum_g BCE-with-logits / NOCC (w_bce != 0)
+ *   L_b = lam dice + (1 - lam)(attr + rep) + w_bce bce, and the loss is the mean of L_b over the batch.
+ * Defaults: alpha 0.9, eps 1, lam 0.99 (Sec. 4.2), w_bce 0. */
+typedef struct {
+    double alpha, eps, lam, w_bce;
+} npvs_loss_params;
+
+#define NPVS_LOSS_TERMS 12
+enum {
+    NPVS_LT_L = 0, NPVS_LT_DICE = 1, NPVS_LT_ATTR = 2, NPVS_LT_REP = 3, NPVS_LT_BCE = 4, NPVS_LT_GTP = 5,
+    NPVS_LT_TP = 6, NPVS_LT_FN = 7, NPVS_LT_FP = 8, NPVS_LT_NOCC = 9,
+    NPVS_LT_DTP = 10, /* dLoss/dTP of the batch mean */
+    NPVS_LT_DFP = 11  /* dLoss/dFP of the batch mean */
+};
+
+/* Bytes of the npvs_loss_fwd workspace for `capacity` rows of logits of this dtype (F32 / F64). */
+size_t npvs_loss_workspace_bytes(int32_t capacity, int32_t dtype);
+
+/* Loss of the logits z [capacity][d^3] (dtype F32 or F64; rows < *n_rows, coarse sites `coords`
+ * of the interleaved level, channel order as the interleave) against the ground-truth and
+ * geometry grids gt_bits / g_bits [B][D][H][W/32] of `grid`. Writes terms [B][NPVS_LOSS_TERMS]
+ * and the scalar loss (device, dtype). Sums are fixed-order (bitwise reproducible). */
+npvs_status npvs_loss_fwd(int32_t dtype, const void* logits, const int32_t* coords, const int32_t* n_rows,
+                          int32_t capacity, const uint32_t* gt_bits, const uint32_t* g_bits, npvs_grid grid,
+                          int32_t d, const npvs_loss_params* prm, void* terms, void* loss, void* workspace,
+                          size_t workspace_bytes, void* stream);
+
+/* dLoss/dz from the terms of npvs_loss_fwd, times the device scalar dloss (dtype; NULL = 1):
+ * dz = g (p(1-p)(y dL/dTP + (1-y) dL/dFP) + w_bce (p - y) / (B NOCC)). Rows < *n_rows written, in
+ * dlogits_dtype: F32 or BF16 for F32 logits (BF16 feeds the tensor-core backward), F64 for F64. */
+npvs_status npvs_loss_bwd(int32_t dtype, const void* logits, const int32_t* coords, const int32_t* n_rows,
+                          int32_t capacity, const uint32_t* gt_bits, const uint32_t* g_bits, npvs_grid grid,
+                          int32_t d, const npvs_loss_params* prm, const void* terms, const void* dloss,
+                          int32_t dlogits_dtype, void* dlogits, void* stream);
+
+/* ---- a11: Adam (Sec. 4.2) ----------------------------------------------------------------- */
+
+/* Paper: Adam, lr 1e-3, "decay 1e-10" (read as L2 weight decay added to the gradient); betas and
+ * eps unspecified (0.9, 0.999, 1e-8). */
+typedef struct {
+    float lr, beta1, beta2, eps, weight_decay;
+} npvs_adam_params;
+
+/* One Adam step on n FP32 master parameters (all device): g = grad + wd theta, m and v updated,
+ * theta -= lr mhat / (sqrt(vhat) + eps) with bias corrections of step t. state: device int32[2],
+ * zero before the first step; state[0] counts the steps taken (t = state[0] + 1 is used and stored
+ * back by the last CTA), state[1] is scratch. Replaying a captured step advances t. */
+npvs_status npvs_adam_step(float* theta, const float* grad, float* m, float* v, int64_t n,
+                           const npvs_adam_params* prm, int32_t* state, void* stream);
 
 #ifdef __cplusplus
 }

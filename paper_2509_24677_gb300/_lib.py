@@ -57,6 +57,20 @@ class ConvDesc(ctypes.Structure):
                 ("tune_form", I32)]
 
 
+class LossParams(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("eps", ctypes.c_double), ("lam", ctypes.c_double),
+                ("w_bce", ctypes.c_double)]
+
+
+class AdamParams(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("weight_decay", ctypes.c_float)]
+
+
+LOSS_TERMS = 12
+(LT_L, LT_DICE, LT_ATTR, LT_REP, LT_BCE, LT_GTP, LT_TP, LT_FN, LT_FP, LT_NOCC, LT_DTP,
+ LT_DFP) = range(LOSS_TERMS)
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "npvs_last_error": (ctypes.c_char_p, []),
@@ -76,6 +90,13 @@ SIGNATURES = {
     "npvs_packed_weight_bytes": (SZ, [I32, I32, I32]),
     "npvs_pack_weights": (I32, [I32, I32, I32, P, P, P]),
     "npvs_sparse_conv_fwd": (I32, [ctypes.POINTER(ConvDesc), P, P, P, P, P, P]),
+    "npvs_gt_raycast": (I32, [P, P, P, P, I32, Grid, I32, P, P, P]),
+    "npvs_conv_bwd_workspace_bytes": (SZ, [ctypes.POINTER(ConvDesc)]),
+    "npvs_sparse_conv_bwd": (I32, [ctypes.POINTER(ConvDesc), P, P, P, P, P, P, P, P, P, SZ, P]),
+    "npvs_loss_workspace_bytes": (SZ, [I32, I32]),
+    "npvs_loss_fwd": (I32, [I32, P, P, P, I32, P, P, Grid, I32, ctypes.POINTER(LossParams), P, P, P, SZ, P]),
+    "npvs_loss_bwd": (I32, [I32, P, P, P, I32, P, P, Grid, I32, ctypes.POINTER(LossParams), P, P, I32, P, P]),
+    "npvs_adam_step": (I32, [P, P, P, P, ctypes.c_int64, ctypes.POINTER(AdamParams), P, P]),
 }
 
 _lib = None

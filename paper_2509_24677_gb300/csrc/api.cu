@@ -1,6 +1,7 @@
 // Status/error entry points, the host-side frustum setup (a1) and the shared scan kernel.
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "common.cuh"
@@ -11,6 +12,14 @@ static thread_local char g_err[512] = "";
 static std::atomic<unsigned long long> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* v = std::getenv("NPVS_PDL");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
 
 void set_error(const char* fmt, ...) {
     va_list ap;

@@ -1,6 +1,7 @@
 // Shared helpers of the npvs CUDA library (device status word, error reporting, scans).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -53,6 +54,9 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 // starts with pdl_begin(): griddepcontrol.wait (returns once every earlier kernel on the stream has
 // completed and its writes are visible; a no-op without the attribute), then
 // griddepcontrol.launch_dependents (lets the following kernel start its own launch).
+// Programmatic dependent launch can be switched off for the whole process with NPVS_PDL=0.
+bool pdl_enabled();
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                             Args&&... args) {
@@ -65,7 +69,7 @@ inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, siz
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 

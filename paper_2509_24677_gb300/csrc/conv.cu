@@ -17,7 +17,7 @@ constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
 
 template <typename T>
 __global__ void __launch_bounds__(256) conv_simt_kernel(npvs_conv_desc dsc, const T* __restrict__ x,
-                                                        const T* __restrict__ w, const float* __restrict__ bias,
+                                                        const T* __restrict__ w, const T* __restrict__ bias,
                                                         const T* __restrict__ skip, T* __restrict__ y) {
     pdl_begin();
     __shared__ T sA[BK][BM + 1];
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(256) conv_simt_kernel(npvs_conv_desc dsc, cons
 using namespace npvs;
 
 extern "C" npvs_status npvs_sparse_conv_fwd(const npvs_conv_desc* dsc, const void* x, const void* w,
-                                            const float* bias, const void* skip, void* y, void* stream) {
+                                            const void* bias, const void* skip, void* y, void* stream) {
     NPVS_REQUIRE(dsc && x && w && y && dsc->n_out, NPVS_ERR_INVALID_ARG, "npvs_sparse_conv_fwd: NULL argument");
     NPVS_REQUIRE(dsc->kind >= NPVS_CONV_SUBM3 && dsc->kind <= NPVS_CONV_HEAD1, NPVS_ERR_UNSUPPORTED,
                  "npvs_sparse_conv_fwd: unknown kind");
@@ -101,13 +101,13 @@ extern "C" npvs_status npvs_sparse_conv_fwd(const npvs_conv_desc* dsc, const voi
                  "npvs_sparse_conv_fwd: bad sizes");
     cudaStream_t st = as_stream(stream);
     if (dsc->cap_out == 0) return NPVS_OK;
-    if (dsc->dtype == NPVS_BF16) return conv_tc_fwd(*dsc, x, w, bias, skip, y, st);
+    if (dsc->dtype == NPVS_BF16) return conv_tc_fwd(*dsc, x, w, (const float*)bias, skip, y, st);
     dim3 grid(ceil_div(dsc->cap_out, BM), ceil_div(dsc->cout, BN));
     if (dsc->dtype == NPVS_F32) {
-        launch_k(conv_simt_kernel<float>, grid, 256, 0, st, *dsc, (const float*)x, (const float*)w, bias, (const float*)skip,
+        launch_k(conv_simt_kernel<float>, grid, 256, 0, st, *dsc, (const float*)x, (const float*)w, (const float*)bias, (const float*)skip,
                                                       (float*)y);
     } else if (dsc->dtype == NPVS_F64) {
-        launch_k(conv_simt_kernel<double>, grid, 256, 0, st, *dsc, (const double*)x, (const double*)w, bias,
+        launch_k(conv_simt_kernel<double>, grid, 256, 0, st, *dsc, (const double*)x, (const double*)w, (const double*)bias,
                                                        (const double*)skip, (double*)y);
     } else {
         return fail(NPVS_ERR_UNSUPPORTED, "npvs_sparse_conv_fwd: unknown dtype");

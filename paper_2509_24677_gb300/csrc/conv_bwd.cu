@@ -1,0 +1,309 @@
+// a10: backward of the sparse convolutions (Sec. 2.3 layers, trained with Sec. 4.2's optimiser).
+//
+// For a layer y = act(b + sum_t W_t^T x[map(n, t)]) with ReLU mask m = 1[y > 0]:
+//   g      = dy * m                                       (grad_mask_kernel, also the bias partials)
+//   db     = sum_n g[n]
+//   dW_t   = sum_n x[map(n, t)]^T g[n]                    (wgrad_kernel: one reduction GEMM per tap)
+//   dx[i]  = sum_{(n, t): map(n, t) = i} W_t g[n]         (dgrad)
+// The dgrad is itself a forward sparse convolution over the transposed rulebook, so it runs on
+// the forward kernels (tensor cores for BF16): a submanifold conv's transpose is the submanifold
+// conv with the opposite taps (the neighbour map is symmetric: map(n, t) = i iff
+// map(i, 26 - t) = n) and weights W_{26-t}^T; a stride-2 down conv's transpose is the up conv on
+// the same level pair with W_t^T and vice versa; a 1x1 conv's transpose is the 1x1 conv with W^T.
+//
+// Determinism: every sum has a fixed order. Rows are cut into fixed chunks that depend only on the
+// capacity; each chunk's partial sums are written to the workspace and added in chunk order.
+#include "common.cuh"
+#include "conv_tc.cuh"
+
+namespace npvs {
+namespace {
+
+template <typename T> struct AccOf { using type = float; };
+template <> struct AccOf<double> { using type = double; };
+
+__device__ __forceinline__ float to_acc(float v) { return v; }
+__device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ double to_acc(double v) { return v; }
+
+constexpr int kMaskRows = 256;
+constexpr int WB = 64, WK = 16;
+
+// g = dy * 1[y > 0] (rows < n; not written without ReLU) and per-chunk column sums of g.
+template <typename T, typename A>
+__global__ void __launch_bounds__(256) grad_mask_kernel(const T* __restrict__ dy, const T* __restrict__ y, int relu,
+                                                        const int32_t* __restrict__ n_out, int cap, int cout,
+                                                        T* __restrict__ g, A* __restrict__ part_db) {
+    pdl_begin();
+    __shared__ A s[256];
+    const int n = min(*n_out, cap);
+    const int row0 = blockIdx.x * kMaskRows;
+    const int rend = min(row0 + kMaskRows, n);
+    for (int o0 = 0; o0 < cout; o0 += 256) {
+        const int cw = min(256, cout - o0);
+        const int ge = 256 / cw;  // row phases
+        const int q = threadIdx.x / cw, o = o0 + threadIdx.x % cw;
+        A acc = 0;
+        if (q < ge) {
+            for (int r = row0 + q; r < rend; r += ge) {
+                const size_t i = (size_t)r * cout + o;
+                const T v = dy[i];
+                if (relu) {
+                    const bool on = to_acc(y[i]) > A(0);
+                    g[i] = on ? v : T(0.0f);
+                    if (on) acc += to_acc(v);
+                } else {
+                    acc += to_acc(v);
+                }
+            }
+        }
+        s[threadIdx.x] = acc;
+        __syncthreads();
+        if (threadIdx.x < cw) {
+            A t = 0;
+            for (int qq = 0; qq < ge; ++qq) t += s[qq * cw + threadIdx.x];
+            part_db[(size_t)blockIdx.x * cout + o0 + threadIdx.x] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// Per (ci tile, co tile) x tap x row chunk: sum over the chunk's rows n of x[map(n, t)]^T g[n].
+template <typename T, typename A>
+__global__ void __launch_bounds__(256) wgrad_kernel(int kind, const int32_t* __restrict__ map, const int32_t* __restrict__ n_out,
+                                                    int cap, int cin, int cout, int rows_per_chunk,
+                                                    const T* __restrict__ x, const T* __restrict__ g,
+                                                    A* __restrict__ part) {
+    pdl_begin();
+    __shared__ A sA[WK][WB + 1];
+    __shared__ A sB[WK][WB + 1];
+    __shared__ int sRow[WK];
+    const int taps = conv_taps(kind);
+    const int tiles_co = (cout + WB - 1) / WB;
+    const int ci0 = (blockIdx.x / tiles_co) * WB, co0 = (blockIdx.x % tiles_co) * WB;
+    const int t = blockIdx.y, chunk = blockIdx.z;
+    const int n = min(*n_out, cap);
+    const int rb = chunk * rows_per_chunk, re = min(rb + rows_per_chunk, n);
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    A acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = A(0);
+    for (int r0 = rb; r0 < re; r0 += WK) {
+        int any = 0;
+        if (tid < WK) {
+            const int r = r0 + tid;
+            const int src = r < re ? gather_row(kind, map, r, t) : -1;
+            sRow[tid] = src;
+            any = src >= 0;
+        }
+        if (!__syncthreads_or(any)) continue;
+        for (int e = tid; e < WK * WB; e += 256) {
+            const int k = e / WB, c = e % WB;
+            const int src = sRow[k];
+            sA[k][c] = (src >= 0 && ci0 + c < cin) ? to_acc(x[(size_t)src * cin + ci0 + c]) : A(0);
+            sB[k][c] = (src >= 0 && co0 + c < cout) ? to_acc(g[(size_t)(r0 + k) * cout + co0 + c]) : A(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < WK; ++k) {
+            A a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = sA[k][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = sB[k][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    A* out = part + ((size_t)chunk * taps + t) * cin * cout;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int ci = ci0 + ty * 4 + i;
+        if (ci >= cin) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int co = co0 + tx * 4 + j;
+            if (co < cout) out[(size_t)ci * cout + co] = acc[i][j];
+        }
+    }
+}
+
+// dw[e] = sum over chunks of the weight partials; db[o] = sum over chunks of the bias partials.
+template <typename A>
+__global__ void __launch_bounds__(256) grad_reduce_kernel(const A* __restrict__ part_w, int n_chunks, long long nW,
+                                                          const A* __restrict__ part_db, int n_db, int cout,
+                                                          A* __restrict__ dw, A* __restrict__ db) {
+    pdl_begin();
+    const long long total = nW + (db ? cout : 0);
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        A s = 0;
+        if (e < nW) {
+            for (int c = 0; c < n_chunks; ++c) s += part_w[(size_t)c * nW + e];
+            dw[e] = s;
+        } else {
+            const int o = (int)(e - nW);
+            for (int c = 0; c < n_db; ++c) s += part_db[(size_t)c * cout + o];
+            db[o] = s;
+        }
+    }
+}
+
+// wt[t][co][ci] = w[s][ci][co], s = t or taps - 1 - t (flip).
+template <typename T>
+__global__ void __launch_bounds__(256) transpose_taps_kernel(const T* __restrict__ w, int taps, int cin, int cout, int flip,
+                                                             T* __restrict__ wt) {
+    pdl_begin();
+    const long long total = (long long)taps * cin * cout;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int ci = (int)(e % cin);
+        const long long r = e / cin;
+        const int co = (int)(r % cout), t = (int)(r / cout);
+        const int s = flip ? taps - 1 - t : t;
+        wt[e] = w[((size_t)s * cin + ci) * cout + co];
+    }
+}
+
+int host_taps(int kind) { return kind == NPVS_CONV_SUBM3 ? 27 : (kind == NPVS_CONV_HEAD1 ? 1 : 8); }
+
+struct BwdPlan {
+    int taps, n_db, n_chunks, rows_per_chunk, tiles;
+    size_t el, acc, g_bytes, db_bytes, w_bytes, wt_bytes, conv_bytes;
+    npvs_conv_desc td;  // the transposed convolution (dgrad)
+    int mode;           // weight transpose: 1 plain, 2 with reversed taps
+};
+
+BwdPlan plan_bwd(const npvs_conv_desc& d) {
+    BwdPlan p;
+    p.taps = host_taps(d.kind);
+    p.el = d.dtype == NPVS_F64 ? 8 : (d.dtype == NPVS_BF16 ? 2 : 4);
+    p.acc = d.dtype == NPVS_F64 ? 8 : 4;
+    const int cap = std::max(d.cap_out, 1);
+    p.n_db = ceil_div(cap, kMaskRows);
+    p.tiles = ceil_div(d.cin, WB) * ceil_div(d.cout, WB);
+    int want = std::max(1, ceil_div(4LL * kNumSMs, (long long)p.tiles * p.taps));
+    want = std::min(want, std::max(1, ceil_div(cap, 4 * WK)));
+    p.rows_per_chunk = ceil_div(ceil_div(cap, want), WK) * WK;
+    p.n_chunks = ceil_div(cap, p.rows_per_chunk);
+    p.g_bytes = d.relu ? (size_t)cap * d.cout * p.el : 0;
+    p.db_bytes = (size_t)p.n_db * d.cout * p.acc;
+    p.w_bytes = (size_t)p.n_chunks * p.taps * d.cin * d.cout * p.acc;
+
+    npvs_conv_desc t = d;
+    t.relu = 0;
+    t.out_f32 = 0;
+    t.cin = d.cout;
+    t.cout = d.cin;
+    t.n_out = d.n_in ? d.n_in : d.n_out;
+    t.cap_out = d.cap_in > 0 ? d.cap_in : d.cap_out;
+    t.n_in = d.n_out;
+    t.cap_in = d.cap_out;
+    t.tune_stages = t.tune_max_split = t.tune_lag = t.tune_gather = t.tune_gather_warps = t.tune_form = 0;
+    t.workspace = nullptr;
+    t.workspace_bytes = 0;
+    p.mode = 1;
+    switch (d.kind) {
+        case NPVS_CONV_SUBM3: t.kind = NPVS_CONV_SUBM3; t.map2 = nullptr; p.mode = 2; break;
+        case NPVS_CONV_DOWN2: t.kind = NPVS_CONV_UP2; t.map = d.map2; t.map2 = d.map; break;
+        case NPVS_CONV_UP2: t.kind = NPVS_CONV_DOWN2; t.map = d.map2; t.map2 = d.map; break;
+        default: t.kind = NPVS_CONV_HEAD1; t.map = nullptr; t.map2 = nullptr; break;
+    }
+    p.td = t;
+    if (d.dtype == NPVS_BF16) {
+        p.wt_bytes = npvs_packed_weight_bytes(t.kind, t.cin, t.cout);
+        p.conv_bytes = npvs_conv_workspace_bytes(&t);
+    } else {
+        p.wt_bytes = (size_t)p.taps * d.cin * d.cout * p.el;
+        p.conv_bytes = 0;
+    }
+    return p;
+}
+
+template <typename T>
+npvs_status run_bwd(const npvs_conv_desc& d, BwdPlan& p, const void* x, const void* w, const void* y, const void* dy,
+                    void* dx, const void* dx_add, void* dw, void* db, Arena& ar, cudaStream_t st) {
+    using A = typename AccOf<T>::type;
+    const int cap = d.cap_out;
+    T* g = d.relu ? ar.take<T>((size_t)cap * d.cout) : nullptr;
+    A* part_db = ar.take<A>((size_t)p.n_db * d.cout);
+    A* part_w = ar.take<A>((size_t)p.n_chunks * p.taps * d.cin * d.cout);
+    launch_k(grad_mask_kernel<T, A>, p.n_db, 256, 0, st, (const T*)dy, (const T*)y, d.relu, d.n_out, cap, d.cout, g,
+             part_db);
+    NPVS_TRY(check_launch("grad_mask_kernel"));
+    const T* gg = d.relu ? g : (const T*)dy;
+    dim3 wg(p.tiles, p.taps, p.n_chunks);
+    launch_k(wgrad_kernel<T, A>, wg, 256, 0, st, d.kind, d.map, d.n_out, cap, d.cin, d.cout, p.rows_per_chunk,
+             (const T*)x, gg, part_w);
+    NPVS_TRY(check_launch("wgrad_kernel"));
+    const long long nW = (long long)p.taps * d.cin * d.cout;
+    const int rg = std::max(1, std::min(ceil_div(nW + d.cout, 256), kNumSMs * 8));
+    launch_k(grad_reduce_kernel<A>, rg, 256, 0, st, (const A*)part_w, p.n_chunks, nW, (const A*)part_db, p.n_db, d.cout,
+             (A*)dw, (A*)db);
+    NPVS_TRY(check_launch("grad_reduce_kernel"));
+    if (!dx) return NPVS_OK;
+    // dgrad: the transposed convolution of g
+    void* wt = ar.take<char>(p.wt_bytes);
+    if (d.dtype == NPVS_BF16) {
+        NPVS_TRY(pack_weights_mode(p.td.kind, p.td.cin, p.td.cout, (const float*)w, wt, p.mode, st));
+        p.td.workspace = ar.take<char>(p.conv_bytes);
+        p.td.workspace_bytes = p.conv_bytes;
+    } else {
+        const long long tot = (long long)p.taps * d.cin * d.cout;
+        const int tg = std::max(1, std::min(ceil_div(tot, 256), kNumSMs * 8));
+        launch_k(transpose_taps_kernel<T>, tg, 256, 0, st, (const T*)w, p.taps, d.cin, d.cout, p.mode == 2 ? 1 : 0,
+                 (T*)wt);
+        NPVS_TRY(check_launch("transpose_taps_kernel"));
+    }
+    return npvs_sparse_conv_fwd(&p.td, gg, wt, nullptr, dx_add, dx, st);
+}
+
+size_t bwd_bytes(const BwdPlan& p) {
+    return Arena::round(p.g_bytes) + Arena::round(p.db_bytes) + Arena::round(p.w_bytes) + Arena::round(p.wt_bytes) +
+           Arena::round(p.conv_bytes) + 6 * 256;
+}
+
+}  // namespace
+}  // namespace npvs
+
+using namespace npvs;
+
+extern "C" size_t npvs_conv_bwd_workspace_bytes(const npvs_conv_desc* desc) {
+    if (!desc) return 0;
+    BwdPlan p = plan_bwd(*desc);
+    return bwd_bytes(p);
+}
+
+extern "C" npvs_status npvs_sparse_conv_bwd(const npvs_conv_desc* desc, const void* x, const void* w, const void* y,
+                                            const void* dy, void* dx, const void* dx_add, void* dw, void* db,
+                                            void* workspace, size_t workspace_bytes, void* stream) {
+    NPVS_REQUIRE(desc && x && w && dy && dw && desc->n_out, NPVS_ERR_INVALID_ARG, "npvs_sparse_conv_bwd: NULL argument");
+    const npvs_conv_desc& d = *desc;
+    NPVS_REQUIRE(d.kind >= NPVS_CONV_SUBM3 && d.kind <= NPVS_CONV_HEAD1, NPVS_ERR_UNSUPPORTED,
+                 "npvs_sparse_conv_bwd: unknown kind");
+    NPVS_REQUIRE(d.cin > 0 && d.cout > 0 && d.cap_out >= 0, NPVS_ERR_INVALID_ARG, "npvs_sparse_conv_bwd: bad sizes");
+    NPVS_REQUIRE(d.kind == NPVS_CONV_HEAD1 || d.map, NPVS_ERR_INVALID_ARG, "npvs_sparse_conv_bwd: map is NULL");
+    NPVS_REQUIRE(!d.relu || y, NPVS_ERR_INVALID_ARG, "npvs_sparse_conv_bwd: a ReLU layer needs its output y");
+    NPVS_REQUIRE(!(d.relu && d.out_f32), NPVS_ERR_UNSUPPORTED, "npvs_sparse_conv_bwd: ReLU with out_f32 is not supported");
+    NPVS_REQUIRE(!dx || d.kind == NPVS_CONV_SUBM3 || d.kind == NPVS_CONV_HEAD1 || d.map2, NPVS_ERR_INVALID_ARG,
+                 "npvs_sparse_conv_bwd: the dgrad of a stride-2 conv needs map2 (the other map of the level pair)");
+    NPVS_REQUIRE(!dx || !(d.kind == NPVS_CONV_DOWN2 || d.kind == NPVS_CONV_UP2) || (d.n_in && d.cap_in > 0),
+                 NPVS_ERR_INVALID_ARG, "npvs_sparse_conv_bwd: the dgrad of a stride-2 conv needs n_in and cap_in");
+    BwdPlan p = plan_bwd(d);
+    NPVS_REQUIRE(workspace && workspace_bytes >= bwd_bytes(p), NPVS_ERR_WORKSPACE,
+                 "npvs_sparse_conv_bwd: workspace smaller than npvs_conv_bwd_workspace_bytes()");
+    if (d.cap_out == 0) return NPVS_OK;
+    cudaStream_t st = as_stream(stream);
+    Arena ar(workspace, workspace_bytes);
+    switch (d.dtype) {
+        case NPVS_F32: return run_bwd<float>(d, p, x, w, y, dy, dx, dx_add, dw, db, ar, st);
+        case NPVS_BF16: return run_bwd<__nv_bfloat16>(d, p, x, w, y, dy, dx, dx_add, dw, db, ar, st);
+        case NPVS_F64: return run_bwd<double>(d, p, x, w, y, dy, dx, dx_add, dw, db, ar, st);
+        default: return fail(NPVS_ERR_UNSUPPORTED, "npvs_sparse_conv_bwd: unknown dtype");
+    }
+}

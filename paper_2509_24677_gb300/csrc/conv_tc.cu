@@ -682,9 +682,21 @@ __global__ void __launch_bounds__(256) conv_reduce_kernel(const float* __restric
 // exactly as the 128-byte (BKE = 64) or 64-byte (BKE = 32) shared-memory swizzle places them, so a
 // stage is one linear bulk copy. Column-block forms (the transposed conv and the product form)
 // have n = j * cout + o and k = ci; the direct forms have n = o and k = t * cin + ci.
+// Weight W_t[ci][co] of the convolution being packed. mode 0: w is [taps][cin][cout]. mode 1 / 2:
+// the convolution is the transpose of a stored one, w is the stored [taps][cout][cin] and
+// W_t[ci][co] = w_s[co][ci] with s = t (mode 1) or s = taps - 1 - t (mode 2: the tap of the
+// opposite offset, for the transpose of a submanifold convolution).
+__device__ __forceinline__ float weight_at(const float* __restrict__ w, int mode, int taps, int cin, int cout, int t,
+                                           int ci, int co) {
+    if (mode == 0) return w[((size_t)t * cin + ci) * cout + co];
+    const int s = mode == 2 ? taps - 1 - t : t;
+    return w[((size_t)s * cout + co) * cin + ci];
+}
+
 __global__ void pack_weights_kernel(int kind, int cin, int cout, TcShape sh, const float* __restrict__ w,
-                                    __nv_bfloat16* __restrict__ out) {
+                                    __nv_bfloat16* __restrict__ out, int mode) {
     pdl_begin();
+    const int taps = conv_taps(kind);
     const size_t total = (size_t)sh.KB * sh.Npad * sh.BKE;
     const int nchunk = sh.BKE / 8;
     const bool colblocks = sh.J > 1;
@@ -697,10 +709,10 @@ __global__ void pack_weights_kernel(int kind, int cin, int cout, TcShape sh, con
         if (k < sh.Kflat && n < sh.Ntot) {
             if (colblocks) {
                 const int j = n / cout, o = n - j * cout;
-                v = w[((size_t)j * cin + k) * cout + o];
+                v = weight_at(w, mode, taps, cin, cout, j, k, o);
             } else {
                 const int t = k / cin, ci = k - t * cin;
-                v = w[((size_t)t * cin + ci) * cout + n];
+                v = weight_at(w, mode, taps, cin, cout, t, ci, n);
             }
         }
         const int sw = ((n * sh.RB) >> 7) & (nchunk - 1);
@@ -966,8 +978,9 @@ extern "C" size_t npvs_packed_weight_bytes(int32_t kind, int32_t cin, int32_t co
     return b;
 }
 
-extern "C" npvs_status npvs_pack_weights(int32_t kind, int32_t cin, int32_t cout, const float* w, void* packed,
-                                         void* stream) {
+namespace npvs {
+
+npvs_status pack_weights_mode(int kind, int cin, int cout, const float* w, void* packed, int mode, cudaStream_t st) {
     NPVS_REQUIRE(w && packed && cin > 0 && cout > 0, NPVS_ERR_INVALID_ARG, "npvs_pack_weights: bad arguments");
     NPVS_REQUIRE(kind >= NPVS_CONV_SUBM3 && kind <= NPVS_CONV_HEAD1, NPVS_ERR_UNSUPPORTED,
                  "npvs_pack_weights: unknown kind");
@@ -977,9 +990,16 @@ extern "C" npvs_status npvs_pack_weights(int32_t kind, int32_t cin, int32_t cout
         TcShape sh = tc_shape(kind, cin, cout, f);
         const size_t total = (size_t)sh.KB * sh.Npad * sh.BKE;
         const int grid = (int)std::min<size_t>((total + 255) / 256, (size_t)kNumSMs * 16);
-        launch_k(pack_weights_kernel, grid, 256, 0, as_stream(stream), kind, cin, cout, sh, w, (__nv_bfloat16*)out);
+        launch_k(pack_weights_kernel, grid, 256, 0, st, kind, cin, cout, sh, w, (__nv_bfloat16*)out, mode);
         NPVS_TRY(check_launch("pack_weights_kernel"));
         out += packed_image_bytes(kind, cin, cout, f);
     }
     return NPVS_OK;
+}
+
+}  // namespace npvs
+
+extern "C" npvs_status npvs_pack_weights(int32_t kind, int32_t cin, int32_t cout, const float* w, void* packed,
+                                         void* stream) {
+    return pack_weights_mode(kind, cin, cout, w, packed, 0, as_stream(stream));
 }

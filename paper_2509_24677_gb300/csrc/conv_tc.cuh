@@ -36,6 +36,11 @@ struct TcShape {
 
 TcShape tc_shape(int kind, int cin, int cout, int form);
 
+// Packs FP32 weights into the BF16 tensor-core image of a (kind, cin, cout) convolution; mode 1 / 2
+// read them as the transpose of a stored (kind, cout, cin) convolution (2: with the taps
+// reversed, the transpose of a submanifold convolution).
+npvs_status pack_weights_mode(int kind, int cin, int cout, const float* w, void* packed, int mode, cudaStream_t st);
+
 npvs_status conv_tc_fwd(const npvs_conv_desc& d, const void* x, const void* w, const float* bias,
                         const void* skip, void* y, cudaStream_t st);
 

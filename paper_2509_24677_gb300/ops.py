@@ -18,12 +18,26 @@ def _lib():
 
 
 def _p(t: Optional[torch.Tensor]):
-    return None if t is None else ctypes.c_void_p(t.data_ptr())
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("npvs: tensors passed to the library must be contiguous (row-major)")
+    return ctypes.c_void_p(t.data_ptr())
 
 
 def _s(stream: Optional[torch.cuda.Stream]):
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
+
+
+_TDT = {L.F32: torch.float32, L.BF16: torch.bfloat16, L.F64: torch.float64}
+
+
+def _want(dt, **tensors):
+    """Raises TypeError unless every given tensor (None allowed) has torch dtype dt."""
+    for name, t in tensors.items():
+        if t is not None and t.dtype != dt:
+            raise TypeError(f"npvs: {name} must be {dt}, got {t.dtype}")
 
 
 def _need_cuda(*ts):
@@ -191,5 +205,75 @@ def conv_desc(kind, dtype, cin, cout, relu, map_, n_out, cap_out, out_f32=False,
 
 def npvs_sparse_conv_fwd(desc: L.ConvDesc, x, w, bias, skip, y, stream=None):
     _need_cuda(x, w, bias, skip, y)
+    T = _TDT[desc.dtype]
+    _want(T, x=x, skip=skip)
+    _want(torch.float32 if (desc.out_f32 and desc.dtype != L.F64) else T, y=y)
+    _want(torch.float64 if desc.dtype == L.F64 else torch.float32, bias=bias)
+    if desc.dtype != L.BF16:
+        _want(T, w=w)
     check(_lib().npvs_sparse_conv_fwd(ctypes.byref(desc), _p(x), _p(w), _p(bias), _p(skip), _p(y), _s(stream)),
           "npvs_sparse_conv_fwd")
+
+
+# ---- training: ground truth and a8-a11 ----------------------------------------------------------
+
+def npvs_gt_raycast(boxes, box_offsets, cams_dev, points, g: L.Grid, s_gt: int, gt_bits, g_bits=None,
+                    stream=None):
+    _need_cuda(boxes, box_offsets, cams_dev, points, gt_bits, g_bits)
+    check(_lib().npvs_gt_raycast(_p(boxes), _p(box_offsets), _p(cams_dev), _p(points), points.shape[-2], g, s_gt,
+                                 _p(g_bits), _p(gt_bits), _s(stream)), "npvs_gt_raycast")
+
+
+
+def npvs_conv_bwd_workspace_bytes(desc: L.ConvDesc) -> int:
+    return int(_lib().npvs_conv_bwd_workspace_bytes(ctypes.byref(desc)))
+
+
+def npvs_sparse_conv_bwd(desc: L.ConvDesc, x, w, y, dy, dx, dx_add, dw, db, workspace, stream=None):
+    _need_cuda(x, w, y, dy, dx, dx_add, dw, db, workspace)
+    T = _TDT[desc.dtype]
+    A = torch.float64 if desc.dtype == L.F64 else torch.float32
+    _want(T, x=x, y=y, dy=dy, dx=dx, dx_add=dx_add)
+    _want(A, w=w, dw=dw, db=db)
+    check(_lib().npvs_sparse_conv_bwd(ctypes.byref(desc), _p(x), _p(w), _p(y), _p(dy), _p(dx), _p(dx_add),
+                                      _p(dw), _p(db), _p(workspace), workspace.numel() * workspace.element_size(),
+                                      _s(stream)), "npvs_sparse_conv_bwd")
+
+
+def loss_params(alpha=0.9, eps=1.0, lam=0.99, w_bce=0.0) -> L.LossParams:
+    return L.LossParams(alpha, eps, lam, w_bce)
+
+
+def npvs_loss_workspace_bytes(capacity: int, dtype: int) -> int:
+    return int(_lib().npvs_loss_workspace_bytes(capacity, dtype))
+
+
+def npvs_loss_fwd(dtype: int, logits, coords, n_rows, capacity: int, gt_bits, g_bits, g: L.Grid, d: int,
+                  prm: L.LossParams, terms, loss, workspace, stream=None):
+    _need_cuda(logits, coords, n_rows, gt_bits, g_bits, terms, loss, workspace)
+    _want(_TDT[dtype], logits=logits, terms=terms, loss=loss)
+    check(_lib().npvs_loss_fwd(dtype, _p(logits), _p(coords), _p(n_rows), capacity, _p(gt_bits), _p(g_bits), g, d,
+                               ctypes.byref(prm), _p(terms), _p(loss), _p(workspace),
+                               workspace.numel() * workspace.element_size(), _s(stream)), "npvs_loss_fwd")
+
+
+def npvs_loss_bwd(dtype: int, logits, coords, n_rows, capacity: int, gt_bits, g_bits, g: L.Grid, d: int,
+                  prm: L.LossParams, terms, dloss, dlogits_dtype: int, dlogits, stream=None):
+    _need_cuda(logits, coords, n_rows, gt_bits, g_bits, terms, dloss, dlogits)
+    _want(_TDT[dtype], logits=logits, terms=terms, dloss=dloss)
+    _want(_TDT[dlogits_dtype], dlogits=dlogits)
+    check(_lib().npvs_loss_bwd(dtype, _p(logits), _p(coords), _p(n_rows), capacity, _p(gt_bits), _p(g_bits), g, d,
+                               ctypes.byref(prm), _p(terms), _p(dloss), dlogits_dtype, _p(dlogits), _s(stream)),
+          "npvs_loss_bwd")
+
+
+def adam_params(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=1e-10) -> L.AdamParams:
+    return L.AdamParams(lr, beta1, beta2, eps, weight_decay)
+
+
+def npvs_adam_step(theta, grad, m, v, prm: L.AdamParams, state, stream=None):
+    _need_cuda(theta, grad, m, v, state)
+    _want(torch.float32, theta=theta, grad=grad, m=m, v=v)
+    _want(torch.int32, state=state)
+    check(_lib().npvs_adam_step(_p(theta), _p(grad), _p(m), _p(v), theta.numel(), ctypes.byref(prm), _p(state),
+                                _s(stream)), "npvs_adam_step")

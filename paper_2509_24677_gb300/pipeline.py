@@ -98,6 +98,7 @@ class Net:
     def repack(self):
         self._packed = None
         self._w64 = None
+        self._b64 = None
 
     def operands(self, dtype):
         if dtype == L.BF16:
@@ -107,6 +108,14 @@ class Net:
                 self._w64 = [w.double() for w in self.w32]
             return self._w64
         return self.w32
+
+    def biases(self, dtype):
+        """Bias operands: FP32, or FP64 copies for the FP64 path."""
+        if dtype == L.F64:
+            if getattr(self, "_b64", None) is None:
+                self._b64 = [b.double() for b in self.b32]
+            return self._b64
+        return self.b32
 
 
 class FramePipeline:
@@ -202,7 +211,7 @@ class FramePipeline:
             elif l.kind == "down2":
                 prev = self.levels[li - 1]
                 d = ops.conv_desc(L.CONV_DOWN2, self.dtype, l.cin, l.cout, l.relu, prev.down, lv.n_rows, lv.capacity,
-                                  n_in=prev.n_rows, cap_in=prev.capacity, **common)
+                                  map2=prev.up, n_in=prev.n_rows, cap_in=prev.capacity, **common)
             elif l.kind == "up2":
                 nxt = self.levels[li + 1]
                 d = ops.conv_desc(L.CONV_UP2, self.dtype, l.cin, l.cout, l.relu, lv.up, lv.n_rows, lv.capacity,
@@ -222,11 +231,12 @@ class FramePipeline:
 
     def network(self):
         W = self.net.operands(self.dtype)
+        Bs = self.net.biases(self.dtype)
         a = self.feats
         for i, l in enumerate(self.net.layers):
             y = self.acts[l.name]
             with self._t("conv:" + l.name):
-                ops.npvs_sparse_conv_fwd(self.descs[i], a, W[i], self.net.b32[i], self.skip_of.get(i), y)
+                ops.npvs_sparse_conv_fwd(self.descs[i], a, W[i], Bs[i], self.skip_of.get(i), y)
             a = y
         return a
 

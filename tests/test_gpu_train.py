@@ -1,0 +1,607 @@
+"""GPU parity of the training path: loss forward/backward, convolution backward, Adam, whole-network
+gradients against the FP64 oracle, and the FP64 finite-difference gradient check on the
+plain 64x64x32 network.
+
+Tolerances: FP32 1e-5 normwise on single ops with exactly representable inputs, BF16 2e-2;
+whole-network gradients 1e-3 (FP32) and 2e-2 (BF16) normwise per parameter tensor; central finite
+differences |g - g_fd| <= 1e-3 max(|g|, |g_fd|, 1e-6) with ReLU kink crossings counted and excluded.
+"""
+import numpy as np
+import pytest
+import torch
+
+import npvs_inputs as I
+from oracle import interleave as oil
+from oracle import loss as oloss
+from oracle import network as onet
+from test_gpu_parity import DEV, bf16_round, build_rulebooks, lib, make_levels, normwise, u32
+
+pytestmark = pytest.mark.gpu
+
+
+# ------------------------------------------------------------------------------------------
+# a10: single-convolution backward
+# ------------------------------------------------------------------------------------------
+
+BWD_CASES = [("subm3", 8, 16), ("subm3", 16, 16), ("subm3", 32, 32), ("subm3", 64, 128), ("subm3", 128, 32),
+             ("down2", 16, 32), ("down2", 32, 64), ("down2", 64, 128), ("up2", 32, 16), ("up2", 64, 32),
+             ("up2", 128, 64), ("head1", 16, 64), ("head1", 32, 64), ("head1", 64, 512)]
+
+
+@pytest.mark.parametrize("dt", ["f32", "bf16", "f64"])
+@pytest.mark.parametrize("kind,cin,cout", BWD_CASES)
+def test_conv_bwd_parity(kind, cin, cout, dt):
+    L, ops, P = lib()
+    rng = np.random.default_rng(sum(map(ord, kind)) * 7919 + cin * 31 + cout)
+    occ = rng.random((2, 10, 12, 14)) < 0.12
+    lvs, c0 = make_levels(occ, 2)
+    build_rulebooks(lvs)
+    torch.cuda.synchronize()
+    fine = onet.Level(c0, (2, 10, 12, 14))
+    coarse = fine.parent()
+    relu = kind != "head1"
+    layer = I.Layer("t", kind, cin, cout, relu)
+    w = I.kaiming_uniform([layer], seed=3)[0][0]
+    b = (rng.normal(size=cout) * 0.1).astype(np.float32)
+    n_in = {"subm3": fine.n, "down2": fine.n, "up2": coarse.n, "head1": fine.n}[kind]
+    n_out = {"subm3": fine.n, "down2": coarse.n, "up2": fine.n, "head1": fine.n}[kind]
+    x = rng.normal(size=(n_in, cin)).astype(np.float32)
+    dy = rng.normal(size=(n_out, cout)).astype(np.float32)
+    add = rng.normal(size=(n_in, cin)).astype(np.float32)
+    rnd = bf16_round if dt == "bf16" else (lambda a: np.asarray(a, np.float64))
+    x_r, dy_r, add_r = rnd(x), rnd(dy), rnd(add)
+    xt = torch.tensor(x_r, requires_grad=True)
+    wt = torch.tensor(w.astype(np.float64), requires_grad=True)
+    bt = torch.tensor(b.astype(np.float64), requires_grad=True)
+    pre = {"subm3": lambda: onet.subm3(fine, xt, wt, bt), "down2": lambda: onet.down2(fine, coarse, xt, wt, bt),
+           "up2": lambda: onet.up2(coarse, fine, xt, wt, bt), "head1": lambda: onet.head1(fine, xt, wt, bt)}[kind]()
+    y_ref = torch.relu(pre) if relu else pre
+    g = torch.tensor(dy_r) * ((y_ref > 0).double() if relu else 1.0)
+    gx, gw, gb = torch.autograd.grad(pre, (xt, wt, bt), grad_outputs=g)
+    # device side
+    dtype = {"f32": L.F32, "bf16": L.BF16, "f64": L.F64}[dt]
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f64": torch.float64}[dt]
+    mdt = torch.float64 if dt == "f64" else torch.float32
+    lv_in = lvs[1] if kind == "up2" else lvs[0]
+    lv_out = lvs[1] if kind == "down2" else lvs[0]
+
+    def dev_rows(a, cap):
+        t = torch.zeros(cap, a.shape[1], dtype=tdt, device=DEV)
+        t[:len(a)] = torch.from_numpy(np.asarray(a, np.float64)).to(DEV).to(tdt)
+        return t
+
+    xin = dev_rows(x, lv_in.capacity)
+    dyd = dev_rows(dy, lv_out.capacity)
+    yd = dev_rows(y_ref.detach().numpy(), lv_out.capacity) if relu else None
+    addd = dev_rows(add, lv_in.capacity)
+    mp = {"subm3": lvs[0].nbr, "down2": lvs[0].down, "up2": lvs[0].up, "head1": None}[kind]
+    mp2 = {"down2": lvs[0].up, "up2": lvs[0].down}.get(kind)
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+    desc = ops.conv_desc(P.KIND[kind], dtype, cin, cout, relu, mp, lv_out.n_rows, lv_out.capacity, map2=mp2,
+                         n_in=lv_in.n_rows, cap_in=lv_in.capacity, status=status)
+    ws = ops.conv_workspace(ops.npvs_conv_bwd_workspace_bytes(desc), DEV)
+    w_dev = torch.from_numpy(w).to(DEV).to(mdt).contiguous()
+    results = []
+    for rep in range(2):
+        dx = torch.full((lv_in.capacity, cin), float("nan"), dtype=tdt, device=DEV)
+        dw = torch.full(w.shape, float("nan"), dtype=mdt, device=DEV)
+        db = torch.full((cout,), float("nan"), dtype=mdt, device=DEV)
+        ops.npvs_sparse_conv_bwd(desc, xin, w_dev, yd, dyd, dx, addd, dw, db, ws)
+        assert ops.npvs_check_status(status) == 0
+        results.append((dx, dw, db))
+    dx, dw, db = results[0]
+    tol_dx = {"f32": 1e-5, "bf16": 2e-2, "f64": 1e-12}[dt]
+    tol_w = {"f32": 1e-5, "bf16": 1e-5, "f64": 1e-12}[dt]     # dW, db: exact operands, FP32 sums
+    assert normwise(dw.cpu().numpy(), gw.numpy()) <= tol_w
+    assert normwise(db.cpu().numpy(), gb.numpy()) <= tol_w
+    got = dx[:n_in].double().cpu().numpy()
+    assert normwise(got - add_r, gx.numpy()) <= tol_dx, normwise(got - add_r, gx.numpy())
+    assert torch.isnan(dx[n_in:].float()).all()            # rows past n_in untouched
+    for a, b2 in zip(results[0], results[1]):                # fixed-order sums: bitwise reproducible
+        assert torch.equal(torch.nan_to_num(a.float(), 7.0), torch.nan_to_num(b2.float(), 7.0))
+
+
+@pytest.mark.parametrize("sync_first", [False, True])
+def test_conv_bwd_empty_level(sync_first):
+    L, ops, P = lib()
+    lvs, _ = make_levels(np.zeros((1, 4, 4, 4), bool), 1)
+    build_rulebooks(lvs)
+    desc = ops.conv_desc(L.CONV_SUBM3, L.F32, 16, 16, True, lvs[0].nbr, lvs[0].n_rows, lvs[0].capacity,
+                         n_in=lvs[0].n_rows, cap_in=lvs[0].capacity)
+    ws = ops.conv_workspace(ops.npvs_conv_bwd_workspace_bytes(desc), DEV)
+    f32 = dict(dtype=torch.float32, device=DEV)
+    z = torch.zeros(lvs[0].capacity, 16, **f32)
+    dw = torch.full((27, 16, 16), 5.0, **f32)
+    db = torch.full((16,), 5.0, **f32)
+    w = torch.zeros(27, 16, 16, **f32)
+    for rep in range(8):
+        dw.fill_(5.0)
+        db.fill_(5.0)
+        dx = z.clone()
+        if sync_first:
+            torch.cuda.synchronize()
+        ops.npvs_sparse_conv_bwd(desc, z, w, z, z, dx, None, dw, db, ws)
+        torch.cuda.synchronize()
+        bad = (dw != 0).reshape(-1).nonzero().reshape(-1)
+        assert bad.numel() == 0 and (db == 0).all(), (rep, bad.numel(), bad[:4].tolist(), bad[-4:].tolist(),
+                                                     db.tolist())
+
+
+def test_conv_bwd_argument_errors():
+    L, ops, P = lib()
+    lvs, _ = make_levels(np.ones((1, 4, 4, 4), bool), 2)
+    build_rulebooks(lvs)
+    z = torch.zeros(64, 16, device=DEV)
+    d = ops.conv_desc(L.CONV_DOWN2, L.F32, 16, 16, True, lvs[0].down, lvs[1].n_rows, lvs[1].capacity,
+                      n_in=lvs[0].n_rows, cap_in=lvs[0].capacity)     # no map2
+    ws = ops.conv_workspace(ops.npvs_conv_bwd_workspace_bytes(d), DEV)
+    with pytest.raises(L.NpvsError) as e:
+        ops.npvs_sparse_conv_bwd(d, z, torch.zeros(8, 16, 16, device=DEV), z, z, z, None,
+                                 torch.zeros(8, 16, 16, device=DEV), None, ws)
+    assert e.value.status == L.ERR_INVALID_ARG
+    d.map2 = lvs[0].up.data_ptr()
+    with pytest.raises(L.NpvsError) as e:
+        ops.npvs_sparse_conv_bwd(d, z, torch.zeros(8, 16, 16, device=DEV), z, z, z, None,
+                                 torch.zeros(8, 16, 16, device=DEV), None, ws[:16])
+    assert e.value.status == L.ERR_WORKSPACE
+
+
+# ------------------------------------------------------------------------------------------
+# a8/a9: loss
+# ------------------------------------------------------------------------------------------
+
+def loss_inputs(seed=0, B=3, W=64, H=32, D=16, d=2):
+    """Clustered geometry bits, a ground truth that is a random part of them plus a few bits
+    outside the geometry, an empty ground truth for the last sample, the interleaved level."""
+    L, ops, P = lib()
+    from test_gpu_parity import clustered_bits
+    rng = np.random.default_rng(seed)
+    dense = clustered_bits(rng, B, D, H, W, 0.05)
+    G = oil.pack_bits(dense)
+    gt = dense & (rng.random(dense.shape) < 0.35)
+    gt |= rng.random(dense.shape) < 0.001
+    gt[-1] = False
+    GT = oil.pack_bits(gt)
+    coords, _, _ = oil.interleave(G, W, d, 1)
+    return G, GT, np.ascontiguousarray(coords, dtype=np.int32)
+
+
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+@pytest.mark.parametrize("w_bce", [0.0, 1.0])
+def test_loss_parity(dt, w_bce):
+    L, ops, P = lib()
+    W, H, D, d, B = 64, 32, 16, 2, 3
+    G, GT, coords = loss_inputs(B=B, W=W, H=H, D=D, d=d)
+    n = len(coords)
+    rng = np.random.default_rng(1)
+    z = rng.normal(size=(n, d ** 3)) * 2.0
+    prm = oloss.LossParams(w_bce=w_bce)
+    zt = torch.tensor(z.astype(np.float32).astype(np.float64) if dt == "f32" else z, requires_grad=True)
+    Lref, terms = oloss.loss_terms(zt, coords, G, GT, W, d, prm)
+    Lref.backward()
+    # device
+    tdt = torch.float32 if dt == "f32" else torch.float64
+    dtype = L.F32 if dt == "f32" else L.F64
+    cap = n + 37
+    zd = torch.zeros(cap, d ** 3, dtype=tdt, device=DEV)
+    zd[:n] = torch.from_numpy(z).to(DEV).to(tdt)
+    cd = torch.zeros(cap, 4, dtype=torch.int32, device=DEV)
+    cd[:n] = torch.from_numpy(coords.astype(np.int32)).to(DEV)
+    nr = torch.tensor([n], dtype=torch.int32, device=DEV)
+    gtd = torch.from_numpy(GT.view(np.int32)).to(DEV)
+    gd = torch.from_numpy(G.view(np.int32)).to(DEV)
+    grid = ops.grid(W, H, D, B)
+    lp = ops.loss_params(w_bce=w_bce)
+    termsd = torch.zeros(B, L.LOSS_TERMS, dtype=tdt, device=DEV)
+    lossd = torch.zeros(1, dtype=tdt, device=DEV)
+    ws = ops.conv_workspace(ops.npvs_loss_workspace_bytes(cap, dtype), DEV)
+    ops.npvs_loss_fwd(dtype, zd, cd, nr, cap, gtd, gd, grid, d, lp, termsd, lossd, ws)
+    tol = 1e-5 if dt == "f32" else 1e-12
+    assert abs(lossd.item() - Lref.item()) <= tol * max(1.0, abs(Lref.item()))
+    T = termsd.cpu().numpy()
+    for b in range(B):
+        for key, col in (("dice", L.LT_DICE), ("attr", L.LT_ATTR), ("rep", L.LT_REP), ("bce", L.LT_BCE),
+                         ("tp", L.LT_TP), ("fp", L.LT_FP), ("L", L.LT_L)):
+            ref = float(terms[b][key])
+            assert abs(T[b, col] - ref) <= tol * max(1.0, abs(ref)), (b, key, T[b, col], ref)
+        assert T[b, L.LT_GTP] == terms[b]["gtp"]
+    assert T[-1, L.LT_GTP] == 0 and T[-1, L.LT_ATTR] == 0
+    # backward, F32 / F64 and the BF16 gradient for the tensor-core backward
+    outs = [(dtype, tdt)] + ([(L.BF16, torch.bfloat16)] if dt == "f32" else [])
+    for odt, otd in outs:
+        dz = torch.full((cap, d ** 3), float("nan"), dtype=otd, device=DEV)
+        ops.npvs_loss_bwd(dtype, zd, cd, nr, cap, gtd, gd, grid, d, lp, termsd, None, odt, dz)
+        got = dz[:n].double().cpu().numpy()
+        t = 1e-5 if odt == L.F32 else (1e-12 if odt == L.F64 else 8e-3)
+        assert normwise(got, zt.grad.numpy()) <= t, (odt, normwise(got, zt.grad.numpy()))
+        assert torch.isnan(dz[n:].float()).all()
+
+
+def test_loss_pins_perfect_and_zero_prediction():
+    """Perfect prediction (p~ = y) gives zero Dice, attraction and repulsion; p~ = 0 gives
+    L_dice = 1 - eps / (alpha GTP + eps) and L_attr = GTP / (GTP + eps)."""
+    L, ops, P = lib()
+    W, H, D, d, B = 64, 32, 16, 2, 2
+    G, GT, coords = loss_inputs(seed=4, B=B, W=W, H=H, D=D, d=d)
+    GT = GT & G                                     # inside the geometry, so p~ = y is reachable
+    y = oloss.site_labels(GT, coords, W, d)
+    n = len(coords)
+    cd = torch.from_numpy(coords.astype(np.int32)).to(DEV)
+    nr = torch.tensor([n], dtype=torch.int32, device=DEV)
+    args = (cd, nr, n, torch.from_numpy(GT.view(np.int32)).to(DEV), torch.from_numpy(G.view(np.int32)).to(DEV),
+            ops.grid(W, H, D, B), d, ops.loss_params())
+    ws = ops.conv_workspace(ops.npvs_loss_workspace_bytes(n, L.F64), DEV)
+    terms = torch.zeros(B, L.LOSS_TERMS, dtype=torch.float64, device=DEV)
+    loss = torch.zeros(1, dtype=torch.float64, device=DEV)
+    z = torch.from_numpy(np.where(y > 0, 800.0, -800.0)).to(DEV)     # sigmoid saturates to exactly 0 / 1
+    ops.npvs_loss_fwd(L.F64, z, *args, terms, loss, ws)
+    T = terms.cpu().numpy()
+    assert np.all(T[:, [L.LT_DICE, L.LT_ATTR, L.LT_REP, L.LT_L]] == 0.0)
+    ops.npvs_loss_fwd(L.F64, torch.full_like(z, -800.0), *args, terms, loss, ws)
+    T = terms.cpu().numpy()
+    gtp = T[:, L.LT_GTP]
+    np.testing.assert_allclose(T[:, L.LT_DICE], 1 - 1.0 / (0.9 * gtp + 1.0), rtol=1e-14)
+    np.testing.assert_allclose(T[:, L.LT_ATTR], gtp / (gtp + 1.0), rtol=1e-14)
+    assert np.all(T[:, L.LT_REP] == 0)
+
+
+# ------------------------------------------------------------------------------------------
+# a11: Adam
+# ------------------------------------------------------------------------------------------
+
+def test_adam_matches_oracle_over_steps():
+    L, ops, P = lib()
+    rng = np.random.default_rng(9)
+    n = 100_003
+    theta = rng.normal(size=n).astype(np.float32)
+    th_d = torch.from_numpy(theta).to(DEV)
+    m_d, v_d = torch.zeros_like(th_d), torch.zeros_like(th_d)
+    st = torch.zeros(2, dtype=torch.int32, device=DEV)
+    th_r, m_r, v_r = theta.astype(np.float64), np.zeros(n), np.zeros(n)
+    prm = ops.adam_params(lr=1e-3, weight_decay=1e-2)
+    for t in range(1, 4):
+        g = (rng.normal(size=n) * 10 ** rng.uniform(-4, 1, size=n)).astype(np.float32)
+        ops.npvs_adam_step(th_d, torch.from_numpy(g).to(DEV), m_d, v_d, prm, st)
+        th_r, m_r, v_r = oloss.adam_step(th_r, g.astype(np.float64), m_r, v_r, t, wd=1e-2)
+        err = np.abs(th_d.double().cpu().numpy() - th_r)
+        assert np.all(err <= 3e-7 * t * np.abs(th_r) + 1e-9), err.max()
+    assert st.cpu().tolist() == [3, 0]
+
+
+# ------------------------------------------------------------------------------------------
+# whole-network gradients
+# ------------------------------------------------------------------------------------------
+
+UNET_SMALL = I.Workload("unet-small", 128, 64, 32, 4, 2, 8, tuple(I.unet_layers(128, [16, 32, 64], 64)))
+
+
+def scene_for(wl):
+    if wl.name == "plain64":
+        return I.plain64_scene()
+    return I.city_boxes(0), I.city_viewcells(0, 1)[0]
+
+
+def make_trainer(wl, dtype, seed=0, batch=1):
+    L, ops, P = lib()
+    from paper_2509_24677_gb300 import train as T
+    boxes, vc = scene_for(wl)
+    ws, bs = I.kaiming_uniform(wl.layers, seed=seed, bias_scale=0.05)
+    tr = T.Trainer(wl, wl.layers, ws, bs, batch, dtype)
+    cams = ops.cameras_to_device([ops.npvs_camera_setup(vc, wl.D)] * batch)
+    bx = torch.from_numpy(np.concatenate([boxes] * batch)).to(DEV)
+    off = torch.tensor([len(boxes) * i for i in range(batch + 1)], dtype=torch.int32, device=DEV)
+    tr.forward(bx, off, cams)
+    torch.cuda.synchronize()
+    G = u32(tr.pipe.occ).reshape(batch, wl.D, wl.H, wl.W // 32)
+    rng = np.random.default_rng(seed + 11)
+    dense = oil.unpack_bits(G, wl.W)
+    GT = oil.pack_bits(dense & (rng.random(dense.shape) < 0.4))
+    tr.gt.copy_(torch.from_numpy(GT.reshape(-1).view(np.int32)))
+    return tr, (bx, off, cams), G, GT, ws, bs
+
+
+def oracle_grads(wl, G, GT, ws, bs):
+    coords, feats, _ = oil.interleave(G, wl.W, wl.d, wl.in_ch)
+    n_levels = 1 + sum(1 for l in wl.layers if l.kind == "down2")
+    levels = onet.build_levels(coords, (G.shape[0], wl.D // wl.d, wl.H // wl.d, wl.W // wl.d), n_levels)
+    W_, B_ = onet.to_torch_params(ws, bs, requires_grad=True)
+    logits = onet.forward(list(wl.layers), W_, B_, levels, torch.tensor(feats))
+    Lref, _ = oloss.loss_terms(logits, coords, G, GT, wl.W, wl.d)
+    Lref.backward()
+    return float(Lref), [w.grad.numpy() for w in W_], [b.grad.numpy() for b in B_]
+
+
+@pytest.mark.parametrize("wl_name,dt", [("plain64", "f32"), ("plain64", "bf16"), ("unet-small", "f32"),
+                                        ("unet-small", "bf16")])
+def test_network_gradients_match_oracle(wl_name, dt):
+    L, ops, P = lib()
+    wl = I.workload("plain64") if wl_name == "plain64" else UNET_SMALL
+    dtype = L.F32 if dt == "f32" else L.BF16
+    tr, _, G, GT, ws, bs = make_trainer(wl, dtype)
+    tr.loss_forward()
+    tr.backward()
+    assert ops.npvs_check_status(tr.pipe.status) == 0
+    Lref, gw_ref, gb_ref = oracle_grads(wl, G, GT, ws, bs)
+    tol_l = 1e-5 if dt == "f32" else 2e-2
+    assert abs(tr.loss.item() - Lref) <= tol_l * abs(Lref)
+    tol = 1e-3 if dt == "f32" else 2e-2
+    worst, cosines = [], []
+    for i, l in enumerate(wl.layers):
+        g = tr.params.gw[i].double().cpu().numpy().ravel()
+        r = gw_ref[i].ravel()
+        ew = normwise(g, r)
+        eb = normwise(tr.params.gb[i].cpu().numpy(), gb_ref[i])
+        worst.append((l.name, ew, eb))
+        cosines.append(float(g @ r / (np.linalg.norm(g) * np.linalg.norm(r))))
+    print("per-layer gradient error (weights, biases, cosine):",
+          [(n, f"{a:.2e}", f"{b:.2e}", f"{c:.4f}") for (n, a, b), c in zip(worst, cosines)])
+    if wl_name == "unet-small" and dt == "bf16":
+        # The BF16 forward's rounding flips ReLU masks of near-zero pre-activations; deep in the
+        # U-Net that moves the FP64-oracle gradient by up to tens of percent normwise (the backward
+        # kernels themselves stay within 2e-2 at the GPU's own activations, see
+        # test_backward_given_forward_matches_oracle). Stated here, bounded by direction.
+        assert min(cosines) >= 0.95, cosines
+        return
+    bad = [(n, a, b) for n, a, b in worst if a > tol or b > tol]
+    assert not bad, bad
+
+
+LAYER_FN = {"subm3": lambda lv, x, W, b: onet.subm3(lv[0], x, W, b),
+            "down2": lambda lv, x, W, b: onet.down2(lv[0], lv[1], x, W, b),
+            "up2": lambda lv, x, W, b: onet.up2(lv[1], lv[0], x, W, b),
+            "head1": lambda lv, x, W, b: onet.head1(lv[0], x, W, b)}
+
+
+def oracle_backward_given_forward(wl, tr, G, GT):
+    """The oracle's FP64 backward evaluated at the GPU's own forward activations (its BF16 or FP32
+    layer outputs, the recomputed up-conv outputs before the skip, its logits): isolates the
+    backward kernels' error from the forward's rounding."""
+    p = tr.pipe
+    lv_of = p._level_of_layers()
+    n_levels = p.n_levels
+    levels = []
+    for li in range(n_levels):
+        n = int(p.levels[li].n_rows.item())
+        dm = p.levels[li].dims
+        levels.append(onet.Level(p.levels[li].coords[:n].cpu().numpy(), (dm.B, dm.Z, dm.Y, dm.X)))
+    F = lambda t, n: t[:n].double().cpu()
+    names = [l.name for l in wl.layers]
+    n0 = levels[0].n
+    z = torch.tensor(F(p.logits, n0).numpy(), requires_grad=True)
+    Lb, _ = oloss.loss_terms(z, levels[0].coords.numpy(), G, GT, wl.W, wl.d)
+    Lb.backward()
+    dy = {names[-1]: z.grad}
+    skip_grad = {}
+    gws = [None] * len(wl.layers)
+    for i in range(len(wl.layers) - 1, -1, -1):
+        l = wl.layers[i]
+        li = lv_of[l.name]
+        lo = levels[li]
+        if l.kind == "down2":
+            lin = levels[li - 1]
+        elif l.kind == "up2":
+            lin = levels[li + 1]
+        else:
+            lin = lo
+        x_t = p.feats if i == 0 else p.acts[names[i - 1]]
+        x = torch.tensor(F(x_t, lin.n).numpy(), requires_grad=True)
+        W = torch.tensor(tr.params.w[i].double().cpu().numpy(), requires_grad=True)
+        b = torch.tensor(tr.params.b[i].double().cpu().numpy(), requires_grad=True)
+        lvpair = {"down2": (lin, lo), "up2": (lo, lin)}.get(l.kind, (lo, lo))
+        pre = LAYER_FN[l.kind](lvpair, x, W, b)
+        g = dy[l.name]
+        if l.relu:
+            y = tr.u[i] if l.kind == "up2" else p.acts[l.name]
+            g = g * (F(y, lo.n) > 0).double()
+        gx, gW, _ = torch.autograd.grad(pre, (x, W, b), grad_outputs=g)
+        gws[i] = gW.numpy()
+        if l.kind == "up2":
+            skip_grad[f"enc{li}b"] = dy[l.name]
+        if i > 0:
+            prev = names[i - 1]
+            dy[prev] = gx + skip_grad.get(prev, 0.0)
+    return gws
+
+
+@pytest.mark.parametrize("wl_name,dt", [("unet-small", "bf16"), ("unet-small", "f32"), ("plain64", "bf16")])
+def test_backward_given_forward_matches_oracle(wl_name, dt):
+    L, ops, P = lib()
+    wl = I.workload("plain64") if wl_name == "plain64" else UNET_SMALL
+    tr, _, G, GT, _, _ = make_trainer(wl, L.F32 if dt == "f32" else L.BF16)
+    tr.loss_forward()
+    tr.backward()
+    torch.cuda.synchronize()
+    ref = oracle_backward_given_forward(wl, tr, G, GT)
+    errs = [(l.name, normwise(tr.params.gw[i].cpu().numpy(), ref[i])) for i, l in enumerate(wl.layers)]
+    print("backward at the GPU's activations, per-layer dW error:", [(n, f"{e:.2e}") for n, e in errs])
+    tol = 2e-2 if dt == "bf16" else 1e-4
+    assert all(e <= tol for _, e in errs), errs
+
+
+def test_fd_gradient_check_plain64_f64():
+    """FP64 instantiation of the GPU backward against FP64 central differences of the GPU
+    forward: every bias, 512 random weights and 8 random directions."""
+    L, ops, P = lib()
+    wl = I.workload("plain64")
+    tr, _, G, GT, _, _ = make_trainer(wl, L.F64)
+    tr.loss_forward()
+    tr.backward()
+    torch.cuda.synchronize()
+    grad = tr.params.grad.clone()
+    theta = tr.params.theta
+    relu_layers = [l.name for l in wl.layers if l.relu]
+
+    def evaluate():
+        tr.network()
+        tr.loss_forward()
+        masks = torch.cat([(tr.pipe.acts[n] > 0).reshape(-1) for n in relu_layers])
+        return tr.loss.item(), masks
+
+    rng = np.random.default_rng(5)
+    idx = []
+    for (ow, nw, ob), l in zip(tr.params.offsets, wl.layers):
+        idx += list(range(ob, ob + l.cout))
+    w_idx = np.concatenate([np.arange(ow, ow + nw) for (ow, nw, _) in tr.params.offsets])
+    idx += list(rng.choice(w_idx, 512, replace=False))
+    fails, kinks = [], 0
+    for i in idx:
+        t0 = theta[i].item()
+        h = 1e-5 * max(1.0, abs(t0))
+        theta[i] = t0 + h
+        lp, mp = evaluate()
+        theta[i] = t0 - h
+        lm, mm = evaluate()
+        theta[i] = t0
+        if not torch.equal(mp, mm):
+            kinks += 1
+            continue
+        gfd = (lp - lm) / (2 * h)
+        g = grad[i].item()
+        if abs(g - gfd) > 1e-3 * max(abs(g), abs(gfd), 1e-6):
+            fails.append((int(i), g, gfd))
+    used = torch.zeros_like(theta, dtype=torch.bool)
+    for (ow, nw, ob), l in zip(tr.params.offsets, wl.layers):
+        used[ow:ow + nw] = True
+        used[ob:ob + l.cout] = True
+    base = theta.clone()
+    dir_fails = []
+    for k in range(8):
+        v = torch.randn(theta.shape, dtype=torch.float64, device=DEV, generator=torch.Generator(DEV).manual_seed(k))
+        v = v * used
+        h = 1e-6
+        theta.copy_(base + h * v)
+        lp, mp = evaluate()
+        theta.copy_(base - h * v)
+        lm, mm = evaluate()
+        theta.copy_(base)
+        if not torch.equal(mp, mm):
+            kinks += 1
+            continue
+        dfd = (lp - lm) / (2 * h)
+        dan = float((grad * v).sum())
+        if abs(dan - dfd) > 1e-3 * max(abs(dan), abs(dfd), 1e-6):
+            dir_fails.append((k, dan, dfd))
+    print(f"finite differences: {len(idx)} coordinates + 8 directions, {kinks} ReLU kink crossings")
+    assert not fails, fails[:10]
+    assert not dir_fails, dir_fails
+    assert kinks <= len(idx) // 20
+
+
+def test_training_step_graph_replay_is_deterministic_and_learns():
+    """A captured step replayed K times equals K eager steps bitwise, and the loss falls."""
+    L, ops, P = lib()
+    wl = I.workload("plain64")
+    tr1, inp, _, _, _, _ = make_trainer(wl, L.F32)
+    tr2, inp2, _, _, _, _ = make_trainer(wl, L.F32)
+    losses = []
+    for _ in range(6):
+        tr1.step(*inp)
+        losses.append(tr1.loss.item())
+    g = tr2.capture(*inp2)          # the warm-up step outside the capture is step 1
+    for _ in range(5):
+        g.replay()
+    torch.cuda.synchronize()
+    assert tr2.adam_state[0].item() == 6
+    assert torch.equal(tr1.params.theta, tr2.params.theta)
+    assert losses[-1] < losses[0], losses
+
+
+def test_autograd_functions_match_trainer():
+    L, ops, P = lib()
+    from paper_2509_24677_gb300 import train as T
+    wl = I.workload("plain64")
+    tr, _, G, GT, _, _ = make_trainer(wl, L.F32)
+    tr.loss_forward()
+    tr.backward()
+    p = tr.pipe
+    lv0 = p.levels[0]
+    ws = [w.detach().clone().requires_grad_(True) for w in tr.params.w]
+    bs = [b.detach().clone().requires_grad_(True) for b in tr.params.b]
+    a = p.feats
+    for i, l in enumerate(wl.layers):
+        ydt = torch.float32
+        a = T.SparseConv.apply(a, ws[i], bs[i], None, p.descs[i], ws[i].detach(), lv0.capacity, ydt)
+    loss, _ = T.RVLoss.apply(a, lv0.coords, lv0.n_rows, tr.gt, p.occ, p.grid, wl.d, tr.loss_prm, L.F32)
+    loss.backward()
+    assert torch.equal(loss.detach(), tr.loss)
+    for i in range(len(wl.layers)):
+        assert torch.equal(ws[i].grad, tr.params.gw[i])
+        assert torch.equal(bs[i].grad, tr.params.gb[i])
+
+
+# ------------------------------------------------------------------------------------------
+# training targets: ground-truth ray casting
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", ["plain64", "city-small"])
+def test_gt_raycast_matches_oracle(case):
+    """Binary32 GPU ray casting against the FP64 oracle: identical viewpoints; froxels may differ
+    only where a ray grazes an edge or two hits tie (a small fraction)."""
+    from oracle import camera as ocam
+    from oracle import froxel as ofx
+    from paper_2509_24677_gb300 import data as Dm
+    L, ops, P = lib()
+    if case == "plain64":
+        wl = I.workload("plain64")
+        boxes, vc = I.plain64_scene()
+        M = 8
+    else:
+        wl = UNET_SMALL
+        boxes, vc = I.city_boxes(1), I.city_viewcells(1, 1, half=1.0)[0]
+        M = 4
+    cam = ops.npvs_camera_setup(vc, wl.D)
+    pts = Dm.viewpoints(vc, cam, boxes, M, seed=3)
+    cam_o = ocam.frustum(vc, wl.D)
+    offs = I.gt_candidate_offsets(3, vc, max(4 * M, M + 64))
+    G_o = ofx.froxelize(cam_o, boxes, wl.W, wl.H, wl.D, wl.supersample)
+    gt_o, raw_o = ofx.ground_truth(vc, cam_o, boxes, wl.W, wl.H, wl.D, 1, offs, M, G_o)
+    pts_o = ofx.viewpoints(vc, cam_o, offs)
+    pts_o = pts_o[ofx.points_outside_boxes(pts_o, boxes)][:M]
+    np.testing.assert_allclose(pts, pts_o, rtol=0, atol=1e-4)
+    g = ops.grid(wl.W, wl.H, wl.D, 1)
+    bx = torch.from_numpy(boxes).to(DEV)
+    of = torch.tensor([0, len(boxes)], dtype=torch.int32, device=DEV)
+    cd = ops.cameras_to_device([cam])
+    words = wl.D * wl.H * (wl.W // 32)
+    raw = torch.full((words,), -1, dtype=torch.int32, device=DEV)
+    ops.npvs_gt_raycast(bx, of, cd, torch.from_numpy(pts[None]).to(DEV), g, 1, raw)
+    occ = torch.empty(words, dtype=torch.int32, device=DEV)
+    ops.npvs_froxelize(bx, of, cd, g, wl.supersample, occ)
+    gt = torch.empty(words, dtype=torch.int32, device=DEV)
+    ops.npvs_gt_raycast(bx, of, cd, torch.from_numpy(pts[None]).to(DEV), g, 1, gt, g_bits=occ)
+    raw_h = u32(raw).reshape(raw_o.shape)
+    gt_h = u32(gt).reshape(gt_o.shape)
+    n_ref = int(oil.unpack_bits(raw_o, wl.W).sum())
+    d_raw = int(oil.unpack_bits(raw_h ^ raw_o, wl.W).sum())
+    d_gt = int(oil.unpack_bits(gt_h ^ gt_o, wl.W).sum())
+    print(f"{case}: {n_ref} raw GT froxels, {d_raw} differ; {d_gt} differ after AND with G")
+    assert n_ref > 50
+    assert d_raw <= max(3, n_ref // 200) and d_gt <= max(3, n_ref // 200)
+    assert not (oil.unpack_bits(gt_h, wl.W) & ~oil.unpack_bits(u32(occ).reshape(gt_o.shape), wl.W)).any()
+
+
+def test_gt_raycast_monotone_in_viewpoints():
+    """A prefix of the viewpoint sample sees a subset (Sec. 3.2: the PVS of a region contains the
+    PVS of any sub-sample of it)."""
+    from paper_2509_24677_gb300 import data as Dm
+    L, ops, P = lib()
+    wl = I.workload("plain64")
+    boxes, vc = I.plain64_scene()
+    cam = ops.npvs_camera_setup(vc, wl.D)
+    pts = Dm.viewpoints(vc, cam, boxes, 16, seed=0)
+    g = ops.grid(wl.W, wl.H, wl.D, 1)
+    bx = torch.from_numpy(boxes).to(DEV)
+    of = torch.tensor([0, len(boxes)], dtype=torch.int32, device=DEV)
+    cd = ops.cameras_to_device([cam])
+    words = wl.D * wl.H * (wl.W // 32)
+    outs = []
+    for m in (4, 16):
+        o = torch.empty(words, dtype=torch.int32, device=DEV)
+        ops.npvs_gt_raycast(bx, of, cd, torch.from_numpy(np.ascontiguousarray(pts[None, :m])).to(DEV), g, 1, o)
+        outs.append(u32(o))
+    assert ((outs[0] & ~outs[1]) == 0).all()
+    assert popcount_u32(outs[1]) > popcount_u32(outs[0])
+
+
+def popcount_u32(a):
+    return int(np.unpackbits(np.ascontiguousarray(a).view(np.uint8)).sum())

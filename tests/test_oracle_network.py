@@ -14,7 +14,16 @@ import torch.nn.functional as F
 import npvs_inputs as I
 from oracle import network as N
 
-torch.set_default_dtype(torch.float64)
+
+
+@pytest.fixture(autouse=True)
+def _float64_default():
+    """These pins build their tensors in float64; the default is restored after each test so that
+    other test modules in the same process keep float32."""
+    old = torch.get_default_dtype()
+    torch.set_default_dtype(torch.float64)
+    yield
+    torch.set_default_dtype(old)
 
 
 def random_level(rng, dims, frac):
