@@ -11,8 +11,8 @@
 // map(i, 26 - t) = n) and weights W_{26-t}^T; a stride-2 down conv's transpose is the up conv on
 // the same level pair with W_t^T and vice versa; a 1x1 conv's transpose is the 1x1 conv with W^T.
 //
-// Determinism: every sum has a fixed order. Rows are cut into fixed chunks that depend only on the
-// capacity; each chunk's partial sums are written to the workspace and added in chunk order.
+// Determinism: every sum has a fixed order. Rows are cut into a fixed number of chunks of the device
+// row count; each chunk's partial sums are written to the workspace and added in chunk order.
 #include "common.cuh"
 #include "conv_tc.cuh"
 
@@ -27,9 +27,10 @@ __device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162flo
 __device__ __forceinline__ double to_acc(double v) { return v; }
 
 constexpr int kMaskRows = 256;
-constexpr int WB = 64, WK = 16;
+constexpr int WK = 32;  // rows per shared-memory stage of the weight-gradient kernel
 
-// g = dy * 1[y > 0] (rows < n; not written without ReLU) and per-chunk column sums of g.
+// g = dy * 1[y > 0] (rows < n; not written without ReLU) and per-chunk column sums of g. The rows
+// are cut into gridDim.x equal chunks of the device row count.
 template <typename T, typename A>
 __global__ void __launch_bounds__(256) grad_mask_kernel(const T* __restrict__ dy, const T* __restrict__ y, int relu,
                                                         const int32_t* __restrict__ n_out, int cap, int cout,
@@ -37,8 +38,9 @@ __global__ void __launch_bounds__(256) grad_mask_kernel(const T* __restrict__ dy
     pdl_begin();
     __shared__ A s[256];
     const int n = min(*n_out, cap);
-    const int row0 = blockIdx.x * kMaskRows;
-    const int rend = min(row0 + kMaskRows, n);
+    const int rpc = (n + gridDim.x - 1) / gridDim.x;
+    const int row0 = min((int)blockIdx.x * rpc, n);
+    const int rend = min(row0 + rpc, n);
     for (int o0 = 0; o0 < cout; o0 += 256) {
         const int cw = min(256, cout - o0);
         const int ge = 256 / cw;  // row phases
@@ -69,65 +71,75 @@ __global__ void __launch_bounds__(256) grad_mask_kernel(const T* __restrict__ dy
 }
 
 // Per (ci tile, co tile) x tap x row chunk: sum over the chunk's rows n of x[map(n, t)]^T g[n].
-template <typename T, typename A>
+// The chunk's rows are cut from the device row count (n_chunks equal chunks), so the work spreads
+// over every chunk whatever the occupancy. Rows are visited in windows of 256: the rows whose
+// neighbour through tap t exists are compacted in order (ballot + block scan), then consumed 16 at a
+// time from shared memory into a TT x TT register tile per thread (tile TILE = 16 TT channels).
+template <typename T, typename A, int TT>
 __global__ void __launch_bounds__(256) wgrad_kernel(int kind, const int32_t* __restrict__ map, const int32_t* __restrict__ n_out,
-                                                    int cap, int cin, int cout, int rows_per_chunk,
+                                                    int cap, int cin, int cout, int n_chunks,
                                                     const T* __restrict__ x, const T* __restrict__ g,
                                                     A* __restrict__ part) {
     pdl_begin();
-    __shared__ A sA[WK][WB + 1];
-    __shared__ A sB[WK][WB + 1];
-    __shared__ int sRow[WK];
+    constexpr int TILE = 16 * TT;
+    __shared__ A sA[WK][TILE + 1];
+    __shared__ A sB[WK][TILE + 1];
+    __shared__ int sRow[256], sSrc[256];
+    __shared__ int sw[33];
     const int taps = conv_taps(kind);
-    const int tiles_co = (cout + WB - 1) / WB;
-    const int ci0 = (blockIdx.x / tiles_co) * WB, co0 = (blockIdx.x % tiles_co) * WB;
+    const int tiles_co = (cout + TILE - 1) / TILE;
+    const int ci0 = (blockIdx.x / tiles_co) * TILE, co0 = (blockIdx.x % tiles_co) * TILE;
     const int t = blockIdx.y, chunk = blockIdx.z;
     const int n = min(*n_out, cap);
-    const int rb = chunk * rows_per_chunk, re = min(rb + rows_per_chunk, n);
+    const int rpc = (n + n_chunks - 1) / n_chunks;
+    const int rb = min(chunk * rpc, n), re = min(rb + rpc, n);
     const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-    A acc[4][4];
+    A acc[TT][TT];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TT; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = A(0);
-    for (int r0 = rb; r0 < re; r0 += WK) {
-        int any = 0;
-        if (tid < WK) {
-            const int r = r0 + tid;
-            const int src = r < re ? gather_row(kind, map, r, t) : -1;
-            sRow[tid] = src;
-            any = src >= 0;
-        }
-        if (!__syncthreads_or(any)) continue;
-        for (int e = tid; e < WK * WB; e += 256) {
-            const int k = e / WB, c = e % WB;
-            const int src = sRow[k];
-            sA[k][c] = (src >= 0 && ci0 + c < cin) ? to_acc(x[(size_t)src * cin + ci0 + c]) : A(0);
-            sB[k][c] = (src >= 0 && co0 + c < cout) ? to_acc(g[(size_t)(r0 + k) * cout + co0 + c]) : A(0);
+        for (int j = 0; j < TT; ++j) acc[i][j] = A(0);
+    for (int w0 = rb; w0 < re; w0 += 256) {
+        const int r = w0 + tid;
+        const int src = r < re ? gather_row(kind, map, r, t) : -1;
+        int nv;
+        const int pos = block_exclusive_scan(src >= 0 ? 1 : 0, sw, &nv);
+        if (src >= 0) {
+            sRow[pos] = r;
+            sSrc[pos] = src;
         }
         __syncthreads();
+        for (int k0 = 0; k0 < nv; k0 += WK) {
+            for (int e = tid; e < WK * TILE; e += 256) {
+                const int k = e / TILE, c = e % TILE;
+                const bool ok = k0 + k < nv;
+                sA[k][c] = (ok && ci0 + c < cin) ? to_acc(x[(size_t)sSrc[k0 + k] * cin + ci0 + c]) : A(0);
+                sB[k][c] = (ok && co0 + c < cout) ? to_acc(g[(size_t)sRow[k0 + k] * cout + co0 + c]) : A(0);
+            }
+            __syncthreads();
 #pragma unroll
-        for (int k = 0; k < WK; ++k) {
-            A a[4], b[4];
+            for (int k = 0; k < WK; ++k) {
+                A a[TT], b[TT];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = sA[k][ty * 4 + i];
+                for (int i = 0; i < TT; ++i) a[i] = sA[k][ty * TT + i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = sB[k][tx * 4 + j];
+                for (int j = 0; j < TT; ++j) b[j] = sB[k][tx * TT + j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < TT; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                    for (int j = 0; j < TT; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
     A* out = part + ((size_t)chunk * taps + t) * cin * cout;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int ci = ci0 + ty * 4 + i;
+    for (int i = 0; i < TT; ++i) {
+        const int ci = ci0 + ty * TT + i;
         if (ci >= cin) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int co = co0 + tx * 4 + j;
+        for (int j = 0; j < TT; ++j) {
+            const int co = co0 + tx * TT + j;
             if (co < cout) out[(size_t)ci * cout + co] = acc[i][j];
         }
     }
@@ -173,7 +185,7 @@ __global__ void __launch_bounds__(256) transpose_taps_kernel(const T* __restrict
 int host_taps(int kind) { return kind == NPVS_CONV_SUBM3 ? 27 : (kind == NPVS_CONV_HEAD1 ? 1 : 8); }
 
 struct BwdPlan {
-    int taps, n_db, n_chunks, rows_per_chunk, tiles;
+    int taps, n_db, n_chunks, tile, tiles;
     size_t el, acc, g_bytes, db_bytes, w_bytes, wt_bytes, conv_bytes;
     npvs_conv_desc td;  // the transposed convolution (dgrad)
     int mode;           // weight transpose: 1 plain, 2 with reversed taps
@@ -185,12 +197,12 @@ BwdPlan plan_bwd(const npvs_conv_desc& d) {
     p.el = d.dtype == NPVS_F64 ? 8 : (d.dtype == NPVS_BF16 ? 2 : 4);
     p.acc = d.dtype == NPVS_F64 ? 8 : 4;
     const int cap = std::max(d.cap_out, 1);
-    p.n_db = ceil_div(cap, kMaskRows);
-    p.tiles = ceil_div(d.cin, WB) * ceil_div(d.cout, WB);
-    int want = std::max(1, ceil_div(4LL * kNumSMs, (long long)p.tiles * p.taps));
-    want = std::min(want, std::max(1, ceil_div(cap, 4 * WK)));
-    p.rows_per_chunk = ceil_div(ceil_div(cap, want), WK) * WK;
-    p.n_chunks = ceil_div(cap, p.rows_per_chunk);
+    p.n_db = std::min(ceil_div(cap, kMaskRows), 2 * kNumSMs);
+    // 32-channel tiles when either side is narrow, 64 otherwise; about four CTAs per SM in total
+    p.tile = std::min(d.cin, d.cout) <= 32 ? 32 : 64;
+    p.tiles = ceil_div(d.cin, p.tile) * ceil_div(d.cout, p.tile);
+    p.n_chunks = std::max(1, std::min(256, ceil_div(4LL * kNumSMs, (long long)p.tiles * p.taps)));
+    p.n_chunks = std::min(p.n_chunks, std::max(1, ceil_div(cap, 64)));
     p.g_bytes = d.relu ? (size_t)cap * d.cout * p.el : 0;
     p.db_bytes = (size_t)p.n_db * d.cout * p.acc;
     p.w_bytes = (size_t)p.n_chunks * p.taps * d.cin * d.cout * p.acc;
@@ -238,8 +250,12 @@ npvs_status run_bwd(const npvs_conv_desc& d, BwdPlan& p, const void* x, const vo
     NPVS_TRY(check_launch("grad_mask_kernel"));
     const T* gg = d.relu ? g : (const T*)dy;
     dim3 wg(p.tiles, p.taps, p.n_chunks);
-    launch_k(wgrad_kernel<T, A>, wg, 256, 0, st, d.kind, d.map, d.n_out, cap, d.cin, d.cout, p.rows_per_chunk,
-             (const T*)x, gg, part_w);
+    if (p.tile == 32)
+        launch_k(wgrad_kernel<T, A, 2>, wg, 256, 0, st, d.kind, d.map, d.n_out, cap, d.cin, d.cout, p.n_chunks,
+                 (const T*)x, gg, part_w);
+    else
+        launch_k(wgrad_kernel<T, A, 4>, wg, 256, 0, st, d.kind, d.map, d.n_out, cap, d.cin, d.cout, p.n_chunks,
+                 (const T*)x, gg, part_w);
     NPVS_TRY(check_launch("wgrad_kernel"));
     const long long nW = (long long)p.taps * d.cin * d.cout;
     const int rg = std::max(1, std::min(ceil_div(nW + d.cout, 256), kNumSMs * 8));
