@@ -280,6 +280,53 @@ npvs_status npvs_pack_weights(int32_t kind, int32_t cin, int32_t cout, const flo
 npvs_status npvs_sparse_conv_fwd(const npvs_conv_desc* desc, const void* x, const void* w,
                                  const void* bias, const void* skip, void* y, void* stream);
 
+/* ---- a1-a7 as one call: the whole frame -------------------------------------------------- */
+
+/* One layer of a network for npvs_forward, in canonical order (a plain SubM3 stack, or a U-Net:
+ * stem, per level SubM3 layers and a DOWN2, then per decoder level an UP2 whose output gets the
+ * output of the layer just before the matching DOWN2 added after its ReLU, SubM3 layers, and a
+ * HEAD1 with d^3 outputs). tune_*: as npvs_conv_desc (0 = defaults). */
+typedef struct {
+    int32_t kind, cin, cout, relu;
+    const void* w;     /* device: BF16 packed image (npvs_pack_weights) or F32 [taps][cin][cout] */
+    const float* bias; /* device [cout], nullable */
+    int32_t tune_stages, tune_max_split, tune_lag, tune_gather, tune_gather_warps, tune_form;
+} npvs_layer;
+
+/* A frame plan: froxel grid (batch = number of viewcells), interleave factor d, input channels
+ * (1 occupancy, 2 + depth), supersampling, dtype (BF16 or F32), threshold tau, the largest box
+ * count of a call, level capacities in permille of each level's sites (0 = all sites: no overflow
+ * possible), and the layers (host array). */
+typedef struct {
+    npvs_grid grid;
+    int32_t d, in_ch, supersample, dtype;
+    float tau;
+    int32_t max_boxes;
+    int32_t capacity_permille;
+    int32_t n_layers;
+    const npvs_layer* layers;
+} npvs_net_desc;
+
+/* Bytes of the npvs_forward workspace of a plan (0 if the plan is invalid). */
+size_t npvs_forward_workspace_bytes(const npvs_net_desc* net);
+
+/* The whole per-frame path (Sec. 3.1-3.3): npvs_froxelize -> npvs_interleave -> neighbour maps and
+ * down-sampling rulebooks of every level -> every layer (npvs_sparse_conv_fwd) -> npvs_deinterleave
+ * (sigmoid, tau, AND G). Inputs as npvs_froxelize (boxes, box_offsets [B+1], cams [B], all
+ * device); outputs occ_bits (G) and pvs_bits [B][D][H][W/32], probs (nullable, [cap0][d^3] FP32 per
+ * level-0 row). All buffers (levels, rulebooks, activations, scratch) are carved from workspace in a
+ * fixed layout; nothing is allocated; the sequence can be captured in a CUDA graph. */
+npvs_status npvs_forward(const npvs_net_desc* net, const float* boxes, const int32_t* box_offsets,
+                         int32_t n_boxes, const npvs_camera* cams, uint32_t* occ_bits, uint32_t* pvs_bits,
+                         float* probs, int32_t* status, void* workspace, size_t workspace_bytes,
+                         void* stream);
+
+/* Where npvs_forward keeps layer `layer`'s output rows (layer -1: the interleaved input features) in
+ * a workspace: *rows (device [capacity][C], dtype; FP32 for the last layer), the level's capacity
+ * and its device row count. Host-only: reads nothing from the device. */
+npvs_status npvs_forward_layer_output(const npvs_net_desc* net, int32_t layer, void* workspace, void** rows,
+                                      int32_t* capacity, int32_t** n_rows);
+
 /* ---- training targets: ground-truth PVS (Sec. 3.2) ---------------------------------------- */
 
 /* From-region visibility by ray casting: for each viewpoint p_m of batch element e (device

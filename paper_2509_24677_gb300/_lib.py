@@ -67,6 +67,18 @@ class AdamParams(ctypes.Structure):
                 ("eps", ctypes.c_float), ("weight_decay", ctypes.c_float)]
 
 
+class NetLayer(ctypes.Structure):
+    _fields_ = [("kind", I32), ("cin", I32), ("cout", I32), ("relu", I32), ("w", P), ("bias", P),
+                ("tune_stages", I32), ("tune_max_split", I32), ("tune_lag", I32), ("tune_gather", I32),
+                ("tune_gather_warps", I32), ("tune_form", I32)]
+
+
+class NetDesc(ctypes.Structure):
+    _fields_ = [("grid", Grid), ("d", I32), ("in_ch", I32), ("supersample", I32), ("dtype", I32),
+                ("tau", ctypes.c_float), ("max_boxes", I32), ("capacity_permille", I32), ("n_layers", I32),
+                ("layers", ctypes.POINTER(NetLayer))]
+
+
 LOSS_TERMS = 12
 (LT_L, LT_DICE, LT_ATTR, LT_REP, LT_BCE, LT_GTP, LT_TP, LT_FN, LT_FP, LT_NOCC, LT_DTP,
  LT_DFP) = range(LOSS_TERMS)
@@ -91,6 +103,10 @@ SIGNATURES = {
     "npvs_pack_weights": (I32, [I32, I32, I32, P, P, P]),
     "npvs_sparse_conv_fwd": (I32, [ctypes.POINTER(ConvDesc), P, P, P, P, P, P]),
     "npvs_gt_raycast": (I32, [P, P, P, P, I32, Grid, I32, P, P, P]),
+    "npvs_forward_workspace_bytes": (SZ, [ctypes.POINTER(NetDesc)]),
+    "npvs_forward": (I32, [ctypes.POINTER(NetDesc), P, P, I32, P, P, P, P, P, P, SZ, P]),
+    "npvs_forward_layer_output": (I32, [ctypes.POINTER(NetDesc), I32, P, ctypes.POINTER(P),
+                                        ctypes.POINTER(I32), ctypes.POINTER(P)]),
     "npvs_conv_bwd_workspace_bytes": (SZ, [ctypes.POINTER(ConvDesc)]),
     "npvs_sparse_conv_bwd": (I32, [ctypes.POINTER(ConvDesc), P, P, P, P, P, P, P, P, P, SZ, P]),
     "npvs_loss_workspace_bytes": (SZ, [I32, I32]),

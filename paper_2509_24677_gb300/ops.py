@@ -215,6 +215,31 @@ def npvs_sparse_conv_fwd(desc: L.ConvDesc, x, w, bias, skip, y, stream=None):
           "npvs_sparse_conv_fwd")
 
 
+# ---- the whole frame ---------------------------------------------------------------------------
+
+def npvs_forward_workspace_bytes(net: L.NetDesc) -> int:
+    return int(_lib().npvs_forward_workspace_bytes(ctypes.byref(net)))
+
+
+def npvs_forward(net: L.NetDesc, boxes, box_offsets, n_boxes: int, cams_dev, occ_bits, pvs_bits, probs, status,
+                 workspace, stream=None):
+    _need_cuda(boxes, box_offsets, cams_dev, occ_bits, pvs_bits, probs, status, workspace)
+    _want(torch.float32, boxes=boxes, probs=probs)
+    check(_lib().npvs_forward(ctypes.byref(net), _p(boxes), _p(box_offsets), n_boxes, _p(cams_dev), _p(occ_bits),
+                              _p(pvs_bits), _p(probs), _p(status), _p(workspace),
+                              workspace.numel() * workspace.element_size(), _s(stream)), "npvs_forward")
+
+
+def npvs_forward_layer_output(net: L.NetDesc, layer: int, workspace):
+    """(byte offset into workspace, level capacity, byte offset of the level's row count)."""
+    rows, n_rows = ctypes.c_void_p(), ctypes.c_void_p()
+    cap = ctypes.c_int32()
+    check(_lib().npvs_forward_layer_output(ctypes.byref(net), layer, _p(workspace), ctypes.byref(rows),
+                                           ctypes.byref(cap), ctypes.byref(n_rows)), "npvs_forward_layer_output")
+    base = workspace.data_ptr()
+    return rows.value - base, cap.value, n_rows.value - base
+
+
 # ---- training: ground truth and a8-a11 ----------------------------------------------------------
 
 def npvs_gt_raycast(boxes, box_offsets, cams_dev, points, g: L.Grid, s_gt: int, gt_bits, g_bits=None,

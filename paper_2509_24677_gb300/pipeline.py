@@ -331,3 +331,73 @@ class FramePipeline:
         cam_buf.copy_(cam_host, non_blocking=True)
         graph.replay()
         pvs_host.copy_(self.pvs, non_blocking=True)
+
+
+class NativeFrame:
+    """A frame through the single native call npvs_forward: the same kernels in the same order as
+    FramePipeline, with every buffer carved from one caller-owned workspace. `tuned` (a
+    FramePipeline's descriptors) copies per-layer kernel configurations chosen by its autotuner."""
+
+    def __init__(self, wl, net: Net, batch: int = 1, dtype: int = L.BF16, tau: float = 0.5, max_boxes: int = 4096,
+                 device="cuda", capacity_frac: float = 1.0, tuned: Optional[Sequence[L.ConvDesc]] = None):
+        self.wl, self.net, self.B, self.dtype = wl, net, batch, dtype
+        W = net.operands(dtype)
+        Bs = net.biases(dtype)
+        self._keep = (W, Bs)
+        n = len(net.layers)
+        self.layers_c = (L.NetLayer * n)()
+        for i, l in enumerate(net.layers):
+            c = self.layers_c[i]
+            c.kind, c.cin, c.cout, c.relu = KIND[l.kind], l.cin, l.cout, int(l.relu)
+            c.w, c.bias = W[i].data_ptr(), Bs[i].data_ptr()
+            if tuned is not None:
+                for f in ("tune_stages", "tune_max_split", "tune_lag", "tune_gather", "tune_gather_warps", "tune_form"):
+                    setattr(c, f, getattr(tuned[i], f))
+        permille = 0 if capacity_frac >= 1.0 else max(1, int(round(capacity_frac * 1000)))
+        self.grid = L.Grid(wl.W, wl.H, wl.D, batch)
+        self.desc = L.NetDesc(self.grid, wl.d, wl.in_ch, wl.supersample, dtype, tau, max_boxes, permille, n,
+                              self.layers_c)
+        nbytes = ops.npvs_forward_workspace_bytes(self.desc)
+        if nbytes == 0:
+            raise ValueError("npvs_forward: invalid network plan")
+        self.ws = torch.zeros(nbytes, dtype=torch.uint8, device=device)
+        i32 = dict(dtype=torch.int32, device=device)
+        self.occ = torch.zeros(batch * wl.D * wl.H * (wl.W // 32), **i32)
+        self.pvs = torch.zeros_like(self.occ)
+        self.status = torch.zeros(1, **i32)
+        off, cap, _ = ops.npvs_forward_layer_output(self.desc, -1, self.ws)
+        self.probs = torch.zeros(cap, wl.d ** 3, dtype=torch.float32, device=device)
+
+    def layer_output(self, i: int):
+        """(rows [capacity][C] view into the workspace, row-count tensor view) of layer i (-1: the
+        interleaved input)."""
+        off, cap, noff = ops.npvs_forward_layer_output(self.desc, i, self.ws)
+        if i < 0:
+            C, dt = self.wl.feat_ch, TORCH_DT[self.dtype]
+        else:
+            C = self.net.layers[i].cout
+            dt = torch.float32 if i == len(self.net.layers) - 1 else TORCH_DT[self.dtype]
+        nb = cap * C * torch.empty(0, dtype=dt).element_size()
+        rows = self.ws[off:off + nb].view(dt).view(cap, C)
+        return rows, self.ws[noff:noff + 4].view(torch.int32)
+
+    def run(self, boxes, box_offsets, n_boxes: int, cams_dev, want_probs: bool = False):
+        ops.npvs_forward(self.desc, boxes, box_offsets, n_boxes, cams_dev, self.occ, self.pvs,
+                         self.probs if want_probs else None, self.status, self.ws)
+
+    def capture(self, boxes, box_offsets, n_boxes: int, cams_dev, want_probs: bool = False):
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self.run(boxes, box_offsets, n_boxes, cams_dev, want_probs)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.run(boxes, box_offsets, n_boxes, cams_dev, want_probs)
+        return g
+
+    def frame_from_host(self, graph, cam_buf, cam_host, pvs_host):
+        cam_buf.copy_(cam_host, non_blocking=True)
+        graph.replay()
+        pvs_host.copy_(self.pvs, non_blocking=True)

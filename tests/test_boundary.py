@@ -63,3 +63,20 @@ def test_camera_setup_rejects_bad_arguments():
         ops.npvs_camera_setup(vc, 257)
     with pytest.raises(NpvsError):
         ops.npvs_camera_setup(I.Viewcell(centre=(0.0, 0.0, 0.0), half=0.5, yaw=0.0, near=1.0, far=0.5), 8)
+
+
+def test_forward_plan_validation_on_host():
+    """npvs_forward_workspace_bytes validates a plan without touching a device: a network that does
+    not end in d^3 logits, or whose widths do not chain, has no workspace (0)."""
+    from paper_2509_24677_gb300 import _lib as L
+    lib = L.load()
+    lay = (L.NetLayer * 2)()
+    lay[0].kind, lay[0].cin, lay[0].cout, lay[0].relu, lay[0].w = L.CONV_SUBM3, 8, 16, 1, 1
+    lay[1].kind, lay[1].cin, lay[1].cout, lay[1].relu, lay[1].w = L.CONV_SUBM3, 16, 8, 0, 1
+    desc = L.NetDesc(L.Grid(64, 64, 32, 1), 2, 1, 8, L.F32, 0.5, 40, 0, 2, lay)
+    good = lib.npvs_forward_workspace_bytes(desc)
+    assert good > 64 * 64 * 32 // 8
+    lay[1].cout = 4
+    assert lib.npvs_forward_workspace_bytes(desc) == 0
+    lay[1].cout, lay[1].cin = 8, 12
+    assert lib.npvs_forward_workspace_bytes(desc) == 0
