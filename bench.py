@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle sample")
     ap.add_argument("--no-train", action="store_true", help="skip the training-step measurement")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-viewcell batched measurement")
     ap.add_argument("--train-points", type=int, default=256, help="ground-truth viewpoints per viewcell")
     return ap.parse_args()
 
@@ -272,6 +273,116 @@ def run_train(args, dev, flush):
             "gt_bits": gt_bits, "graph": "one CUDA graph replay per step; working set > L2"}
 
 
+def batched_scenes():
+    """Four seeded cities for the batched workload. The 2,000-building city tops out near 4 %
+    occupancy, so the other three are denser (6,000 / 12,000 / 24,000 buildings, the denser two
+    with the taller lognormal(2.3, 0.7) heights) to span the 1-15 % occupancy band."""
+    import dataclasses
+    specs = [(2000, 2.0, 0.6), (6000, 2.0, 0.6), (12000, 2.3, 0.7), (24000, 2.3, 0.7)]
+    return {sc: I.city_boxes(sc, dataclasses.replace(I.CityParams(), n_buildings=nb, mu=mu, sigma=sg))
+            for sc, (nb, mu, sg) in enumerate(specs)}
+
+
+def select_batched_viewcells(dev, wl, scenes, n_pick=64, per_scene=512, lo=0.01, hi=0.15):
+    """The batched-inference workload: a pool of street viewcells of the 4 cities with camera heights
+    2-60 (to widen the occupancy range), froxelized on the GPU; the n_pick cells nearest to n_pick
+    evenly spaced occupancy targets in [lo, hi] (each cell used once)."""
+    from paper_2509_24677_gb300 import _lib as L
+    from paper_2509_24677_gb300 import ops
+    pool = []
+    chunk = 64
+    for sc, boxes in scenes.items():
+        vcs = I.city_viewcells(sc, per_scene, height=(2.0, 60.0))
+        rep = torch.from_numpy(np.concatenate([boxes] * chunk)).to(dev)
+        off = torch.arange(chunk + 1, dtype=torch.int32, device=dev) * len(boxes)
+        occ = torch.empty(chunk * wl.D * wl.H * (wl.W // 32), dtype=torch.int32, device=dev)
+        for c0 in range(0, len(vcs), chunk):
+            part = vcs[c0:c0 + chunk]
+            cams = ops.cameras_to_device([ops.npvs_camera_setup(v, wl.D) for v in part]
+                                         + [ops.npvs_camera_setup(part[-1], wl.D)] * (chunk - len(part)), dev)
+            ops.npvs_froxelize(rep, off, cams, L.Grid(wl.W, wl.H, wl.D, chunk), wl.supersample, occ)
+            bits = occ.view(chunk, -1).cpu().numpy().view(np.uint8)
+            cnt = np.unpackbits(bits, axis=1).sum(1)
+            for v, c in zip(part, cnt[:len(part)]):
+                pool.append((sc, v, float(c) / (wl.W * wl.H * wl.D)))
+    used, picked = set(), []
+    for t in np.linspace(lo, hi, n_pick):
+        best = min((i for i in range(len(pool)) if i not in used), key=lambda i: abs(pool[i][2] - t))
+        used.add(best)
+        picked.append(pool[best])
+    return picked
+
+
+def run_batched(args, dev, net, tuned):
+    """64 viewcells of uneven occupancy in one batched frame (one launch per layer over the
+    concatenated rulebooks, one CUDA graph of npvs_forward), and each viewcell alone as a
+    single-frame graph replay for the per-viewcell latency distribution."""
+    from paper_2509_24677_gb300 import _lib as L
+    from paper_2509_24677_gb300 import ops, pipeline as P
+    wl = I.workload(WORKLOAD)
+    scenes = batched_scenes()
+    picked = select_batched_viewcells(dev, wl, scenes)
+    boxes = np.concatenate([scenes[sc] for sc, _, _ in picked]).astype(np.float32)
+    off = np.cumsum([0] + [len(scenes[sc]) for sc, _, _ in picked]).astype(np.int32)
+    bx = torch.from_numpy(boxes).to(dev)
+    of = torch.from_numpy(off).to(dev)
+    cams = ops.cameras_to_device([ops.npvs_camera_setup(v, wl.D) for _, v, _ in picked], dev)
+    B = len(picked)
+    frac = 0.6
+    fpb = P.FramePipeline(wl, net, B, L.BF16, device=dev, capacity_frac=frac)
+    tuned_b = fpb.autotune(bx, of, cams, reps=3)
+    nfb = P.NativeFrame(wl, net, B, L.BF16, max_boxes=len(boxes), device=dev, capacity_frac=frac, tuned=fpb.descs)
+    del fpb
+    g = nfb.capture(bx, of, len(boxes), cams)
+    st = torch.cuda.current_stream()
+    ts = []
+    for i in range(3 + max(5, args.steps // 3)):
+        s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s_.record(st)
+        g.replay()
+        e_.record(st)
+        if i >= 3:
+            ts.append((s_, e_))
+    torch.cuda.synchronize()
+    if ops.npvs_check_status(nfb.status) != 0:
+        raise RuntimeError("device status set in the batched frame")
+    batch_ms = statistics.median(s_.elapsed_time(e_) for s_, e_ in ts)
+    n_act = int(nfb.layer_output(-1)[1].item())
+    del g, nfb
+    # per-viewcell latency: each cell alone through one single-frame graph (buffers refilled per cell)
+    nmax = max(len(v) for v in scenes.values())
+    nf1 = P.NativeFrame(wl, net, 1, L.BF16, max_boxes=nmax, device=dev, tuned=tuned)
+    bx1 = torch.zeros(nmax, 6, dtype=torch.float32, device=dev)
+    of1 = torch.zeros(2, dtype=torch.int32, device=dev)
+    cams_b = cams.view(B, -1)                 # one npvs_camera (bytes) per row
+    cam1 = cams_b[0].clone()
+    g1 = nf1.capture(bx1, of1, nmax, cam1)
+    lat = []
+    for k, (sc, v, _) in enumerate(picked):
+        nbx = len(scenes[sc])
+        bx1[:nbx].copy_(torch.from_numpy(scenes[sc]))
+        of1[1] = nbx
+        cam1.copy_(cams_b[k])
+        rs = []
+        for i in range(6):
+            s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s_.record(st)
+            g1.replay()
+            e_.record(st)
+            if i >= 2:
+                rs.append((s_, e_))
+        torch.cuda.synchronize()
+        lat.append(statistics.median(s_.elapsed_time(e_) for s_, e_ in rs))
+    occs = [o for _, _, o in picked]
+    return {"viewcells": B, "scenes": "4 cities of 2k/6k/12k/24k buildings, seeds 0-3",
+            "occupancy_range": [round(min(occs), 4), round(max(occs), 4)],
+            "batch_ms": round(batch_ms, 4), "frames_per_s": round(B * 1000.0 / batch_ms, 2),
+            "per_viewcell_ms": {"p50": round(float(np.percentile(lat, 50)), 4),
+                                "p99": round(float(np.percentile(lat, 99)), 4), "max": round(max(lat), 4)},
+            "active_sites_level0": n_act, "capacity_frac": frac,
+            "autotuned_form": {k: v[0].get("tune_form", 0) for k, v in tuned_b.items()}}
+
+
 def run_ours(args):
     from paper_2509_24677_gb300 import _lib as L
     from paper_2509_24677_gb300 import ops, pipeline as P
@@ -429,6 +540,8 @@ def run_ours(args):
     }
     if clk:
         line["clocks"] = clk
+    if not args.no_batched:
+        line["batched"] = run_batched(args, dev, net, fp.descs)
     if not args.no_train:
         del g16, g32, g16t
         line["train"] = run_train(args, dev, flush)
