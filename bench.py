@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle sample")
     ap.add_argument("--no-train", action="store_true", help="skip the training-step measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-viewcell batched measurement")
+    ap.add_argument("--no-highres", action="store_true", help="skip the 512x512x192 measurement")
     ap.add_argument("--train-points", type=int, default=256, help="ground-truth viewpoints per viewcell")
     return ap.parse_args()
 
@@ -383,6 +384,68 @@ def run_batched(args, dev, net, tuned):
             "autotuned_form": {k: v[0].get("tune_form", 0) for k, v in tuned_b.items()}}
 
 
+def run_highres(args, dev, tf_bf16, hbm_gbs):
+    """512x512x192 froxels (s = 4), d = 8 (2 x 512 = 1024 input channels), U-Net 64/128/256/512,
+    BF16, batch 4: four street viewcells of the 10,000-building city (heights lognormal(2.3, 0.7)).
+    Per layer: achieved GB/s of the algorithmic bytes and TFLOP/s of the algorithmic FLOPs, from
+    stage events captured in a graph of the same frame."""
+    from paper_2509_24677_gb300 import _lib as L
+    from paper_2509_24677_gb300 import ops, pipeline as P
+    wl = I.workload("city512")
+    boxes = I.city_boxes(0, I.CITY_LARGE)
+    vcs = I.city_viewcells(0, 4, I.CITY_LARGE)
+    B = len(vcs)
+    bx = torch.from_numpy(np.concatenate([boxes] * B)).to(dev)
+    of = torch.arange(B + 1, dtype=torch.int32, device=dev) * len(boxes)
+    cams = ops.cameras_to_device([ops.npvs_camera_setup(v, wl.D) for v in vcs], dev)
+    ws, bs = I.kaiming_uniform(wl.layers, seed=0)
+    net = P.Net(wl.layers, ws, bs, dev)
+    fp = P.FramePipeline(wl, net, B, L.BF16, device=dev)
+    fp.run(bx, of, cams)
+    stt = ops.npvs_check_status(fp.status)
+    if stt != 0:
+        raise RuntimeError(f"device status {stt:#x} set in the 512-grid frame")
+    fp.autotune(bx, of, cams, reps=3)
+    nf = P.NativeFrame(wl, net, B, L.BF16, max_boxes=len(boxes) * B, device=dev, tuned=fp.descs)
+    g = nf.capture(bx, of, len(boxes) * B, cams)
+    st = torch.cuda.current_stream()
+    ts = []
+    for i in range(3 + max(5, args.steps // 3)):
+        s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s_.record(st)
+        g.replay()
+        e_.record(st)
+        if i >= 3:
+            ts.append((s_, e_))
+    torch.cuda.synchronize()
+    ms = statistics.median(s_.elapsed_time(e_) for s_, e_ in ts)
+    del g, nf
+    timer = P.StageTimer()
+    gt = fp.capture(bx, of, cams, timer=timer)
+    acc = {}
+    for i in range(5):
+        gt.replay()
+        torch.cuda.synchronize()
+        if i >= 2:
+            for k, v in timer.totals().items():
+                acc[k] = acc.get(k, 0.0) + v / 3
+    alg = layer_algorithmic(fp, wl)
+    per_layer = {}
+    for k, v in alg.items():
+        if k.startswith("conv:") and k in acc:
+            t = acc[k] * 1e-3
+            per_layer[k[5:]] = {"ms": round(acc[k], 4), "GB/s": round(v["bytes"] / t / 1e9, 1),
+                                "TFLOP/s": round(v["flops"] / t / 1e12, 2),
+                                "tensor_frac": round(v["flops"] / t / 1e12 / tf_bf16, 4)}
+    occ = float(np.unpackbits(fp.occ.cpu().numpy().view(np.uint8)).mean())
+    return {"workload": "city512: 512x512x192 froxels (s=4), d=8 (1024 ch), U-Net 64/128/256/512, "
+                        "10,000-building city seed 0, 4 viewcells", "batch": B, "ms_per_batch": round(ms, 3),
+            "frames_per_s": round(B * 1000.0 / ms, 2), "occupancy": round(occ, 4),
+            "active_sites": [int(lv.n_rows.item()) for lv in fp.levels],
+            "stage_ms": {k: round(v, 4) for k, v in sorted(acc.items(), key=lambda kv: -kv[1]) if not k.startswith("conv:")},
+            "conv_layers": per_layer, "peaks": {"hbm_gbs": hbm_gbs, "bf16_tflops": tf_bf16}}
+
+
 def run_ours(args):
     from paper_2509_24677_gb300 import _lib as L
     from paper_2509_24677_gb300 import ops, pipeline as P
@@ -542,6 +605,8 @@ def run_ours(args):
         line["clocks"] = clk
     if not args.no_batched:
         line["batched"] = run_batched(args, dev, net, fp.descs)
+    if not args.no_highres:
+        line["highres"] = run_highres(args, dev, tf_bf16, hbm_gbs)
     if not args.no_train:
         del g16, g32, g16t
         line["train"] = run_train(args, dev, flush)

@@ -272,7 +272,8 @@ def bf16_round(a):
 
 CONV_CASES = [
     ("subm3", 8, 16), ("subm3", 16, 16), ("subm3", 32, 32), ("subm3", 64, 64), ("subm3", 128, 32),
-    ("subm3", 128, 16), ("subm3", 256, 256), ("subm3", 16, 8), ("down2", 16, 32), ("down2", 32, 64),
+    ("subm3", 128, 16), ("subm3", 256, 256), ("subm3", 1024, 64), ("subm3", 16, 8), ("down2", 16, 32),
+    ("down2", 32, 64), ("down2", 256, 512), ("up2", 512, 256),
     ("down2", 128, 256), ("up2", 32, 16), ("up2", 64, 32), ("up2", 256, 128), ("head1", 16, 64),
     ("head1", 32, 64), ("head1", 64, 512),
 ]
