@@ -143,25 +143,47 @@ __device__ __forceinline__ int slice_of(const float* __restrict__ z, int D, floa
     return lo;
 }
 
-// SS: the supersampling factor as a compile-time constant (0: runtime value s, up to 16)
+// Normalised pixel centres n = (2a + 1 - S) / S of the supersampled raster, one binary32 division
+// each: xs[a] for a < sW, then ys[b] for b < sH.
+__global__ void __launch_bounds__(256) raster_centres_kernel(int sW, int sH, float* __restrict__ xs) {
+    pdl_begin();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < sW) xs[i] = __fdiv_rn((float)(2 * i + 1 - sW), (float)sW);
+    else if (i < sW + sH) xs[i] = __fdiv_rn((float)(2 * (i - sW) + 1 - sH), (float)sH);
+}
+
+// SS: the supersampling factor as a compile-time constant (0: runtime value s, up to 16).
+// Items (face, froxel column) are numbered face by face; a warp's 32 consecutive items belong to
+// one face or a few neighbouring ones, so lane 0 finds the face of the warp's first item by binary
+// search and every lane walks forward from it.
 template <int SS>
 __global__ void __launch_bounds__(256) froxel_items_kernel(
     const FaceRec* __restrict__ faces, const long long* __restrict__ offs, int n_faces,
     const long long* __restrict__ total_p, const npvs_camera* __restrict__ cams, npvs_grid g, int s_rt,
-    uint32_t* __restrict__ bits) {
+    const float* __restrict__ centres, uint32_t* __restrict__ bits) {
     pdl_begin();
     constexpr int CAP = SS ? SS : 16;
     const int s = SS ? SS : s_rt;
     const long long total = *total_p;
-    const int sW = s * g.W, sH = s * g.H, WW = g.W >> 5;
-    const float fsW = (float)sW, fsH = (float)sH;
-    for (long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x; item < total;
-         item += (long long)gridDim.x * blockDim.x) {
-        int lo = 0, hi = n_faces - 1;  // face = max f with offs[f] <= item
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (offs[mid] <= item) lo = mid; else hi = mid - 1;
+    const int sW = s * g.W, WW = g.W >> 5;
+    const float* ys = centres + sW;
+    const int lane = threadIdx.x & 31;
+    // the loop runs per warp (base = the warp's first item), so every lane reaches the shuffle
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long item = base + lane;
+        int f0 = 0;
+        if (lane == 0) {
+            int lo = 0, hi = n_faces - 1;  // max f with offs[f] <= base
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (offs[mid] <= base) lo = mid; else hi = mid - 1;
+            }
+            f0 = lo;
         }
+        int lo = __shfl_sync(0xffffffffu, f0, 0);
+        if (item >= total) continue;
+        while (lo + 1 < n_faces && offs[lo + 1] <= item) ++lo;
         const FaceRec fr = faces[lo];
         int local = (int)(item - offs[lo]);
         int x = fr.x0 + local % fr.nx, y = fr.y0 + local / fr.nx;
@@ -183,7 +205,7 @@ __global__ void __launch_bounds__(256) froxel_items_kernel(
 #pragma unroll
         for (int i = 0; i < CAP; ++i) {
             if (i >= s) break;
-            const float nx = __fdiv_rn((float)(2 * (x * s + i) + 1 - sW), fsW);
+            const float nx = centres[x * s + i];
             const float sx = __fmul_rn(nx, tanh_);
             ca_ax[i] = __fadd_rn(f_ax, __fmul_rn(sx, r_ax));
             ca_1[i] = __fadd_rn(f1, __fmul_rn(sx, r1));
@@ -192,7 +214,7 @@ __global__ void __launch_bounds__(256) froxel_items_kernel(
         int last_k = -1;
         float zlo = 0.f, zhi = -1.f;  // slice interval of last_k
         for (int bb = y * s; bb < y * s + s; ++bb) {
-            const float ny = __fdiv_rn((float)(2 * bb + 1 - sH), fsH);
+            const float ny = ys[bb];
             const float sy = __fmul_rn(ny, tanh_);
             const float su_ax = __fmul_rn(sy, u_ax), su_1 = __fmul_rn(sy, u1), su_2 = __fmul_rn(sy, u2);
 #pragma unroll
@@ -229,7 +251,7 @@ static size_t froxel_ws(int n_boxes) {
     size_t nchunk = (F + kScanChunk - 1) / kScanChunk;
     return Arena::round(F * sizeof(FaceRec)) + Arena::round(F * sizeof(int)) +
            Arena::round(F * sizeof(long long)) + 2 * Arena::round((nchunk + 1) * sizeof(int)) +
-           Arena::round(sizeof(long long)) + 256;
+           Arena::round(sizeof(long long)) + Arena::round(2 * 65536 * sizeof(float)) + 256;
 }
 
 extern "C" size_t npvs_froxelize_workspace_bytes(int32_t n_boxes) { return froxel_ws(n_boxes); }
@@ -259,6 +281,9 @@ extern "C" npvs_status npvs_froxelize(const float* boxes, const int32_t* box_off
     int* csum = ar.take<int>(nchunk + 1);
     int* coff = ar.take<int>(nchunk + 1);
     long long* total = ar.take<long long>(1);
+    float* centres = ar.take<float>((size_t)s * g.W + (size_t)s * g.H);
+    launch_k(raster_centres_kernel, ceil_div((long long)s * (g.W + g.H), 256), 256, 0, st, s * g.W, s * g.H, centres);
+    NPVS_TRY(check_launch("raster_centres_kernel"));
     launch_k(face_setup_kernel, ceil_div(F, 256), 256, 0, st, boxes, box_offsets, n_boxes, cams, g, faces, counts);
     NPVS_TRY(check_launch("face_setup_kernel"));
     launch_k(chunk_scan_kernel, nchunk, kScanChunk, 0, st, counts, offs, F, csum);
@@ -267,11 +292,11 @@ extern "C" npvs_status npvs_froxelize(const float* boxes, const int32_t* box_off
     launch_k(chunk_add_kernel, nchunk, kScanChunk, 0, st, offs, F, coff, counts, total);
     NPVS_TRY(check_launch("chunk_add_kernel"));
     switch (s) {
-        case 1: launch_k(froxel_items_kernel<1>, kNumSMs * 8, 256, 0, st, faces, offs, F, total, cams, g, s, occ_bits); break;
-        case 2: launch_k(froxel_items_kernel<2>, kNumSMs * 8, 256, 0, st, faces, offs, F, total, cams, g, s, occ_bits); break;
-        case 4: launch_k(froxel_items_kernel<4>, kNumSMs * 8, 256, 0, st, faces, offs, F, total, cams, g, s, occ_bits); break;
-        case 8: launch_k(froxel_items_kernel<8>, kNumSMs * 8, 256, 0, st, faces, offs, F, total, cams, g, s, occ_bits); break;
-        default: launch_k(froxel_items_kernel<0>, kNumSMs * 8, 256, 0, st, faces, offs, F, total, cams, g, s, occ_bits);
+        case 1: launch_k(froxel_items_kernel<1>, kNumSMs * 8, 256, 0, st, faces, offs, F, total, cams, g, s, centres, occ_bits); break;
+        case 2: launch_k(froxel_items_kernel<2>, kNumSMs * 8, 256, 0, st, faces, offs, F, total, cams, g, s, centres, occ_bits); break;
+        case 4: launch_k(froxel_items_kernel<4>, kNumSMs * 8, 256, 0, st, faces, offs, F, total, cams, g, s, centres, occ_bits); break;
+        case 8: launch_k(froxel_items_kernel<8>, kNumSMs * 8, 256, 0, st, faces, offs, F, total, cams, g, s, centres, occ_bits); break;
+        default: launch_k(froxel_items_kernel<0>, kNumSMs * 8, 256, 0, st, faces, offs, F, total, cams, g, s, centres, occ_bits);
     }
     return check_launch("froxel_items_kernel");
 }
