@@ -605,3 +605,13 @@ def test_gt_raycast_monotone_in_viewpoints():
 
 def popcount_u32(a):
     return int(np.unpackbits(np.ascontiguousarray(a).view(np.uint8)).sum())
+
+
+def test_train_eval_runs_small(capsys):
+    """The training / held-out evaluation driver end to end on a tiny pool."""
+    import json
+    from paper_2509_24677_gb300 import train_eval
+    train_eval.main(["--steps", "6", "--train-per-scene", "2", "--eval-per-scene", "1", "--points", "16"])
+    out = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert out["eval_cells"] == 4 and out["eval"]["GTP"] > 0
+    assert 0.0 <= out["eval"]["FNR"] <= 1.0
