@@ -13,6 +13,8 @@
 //
 // Determinism: every sum has a fixed order. Rows are cut into a fixed number of chunks of the device
 // row count; each chunk's partial sums are written to the workspace and added in chunk order.
+#include <type_traits>
+
 #include "common.cuh"
 #include "conv_tc.cuh"
 
@@ -186,6 +188,7 @@ int host_taps(int kind) { return kind == NPVS_CONV_SUBM3 ? 27 : (kind == NPVS_CO
 
 struct BwdPlan {
     int taps, n_db, n_chunks, tile, tiles;
+    bool tc_wgrad;  // BF16: weight gradient on the tensor cores (wgrad_tc)
     size_t el, acc, g_bytes, db_bytes, w_bytes, wt_bytes, conv_bytes;
     npvs_conv_desc td;  // the transposed convolution (dgrad)
     int mode;           // weight transpose: 1 plain, 2 with reversed taps
@@ -205,7 +208,8 @@ BwdPlan plan_bwd(const npvs_conv_desc& d) {
     p.n_chunks = std::min(p.n_chunks, std::max(1, ceil_div(cap, 64)));
     p.g_bytes = d.relu ? (size_t)cap * d.cout * p.el : 0;
     p.db_bytes = (size_t)p.n_db * d.cout * p.acc;
-    p.w_bytes = (size_t)p.n_chunks * p.taps * d.cin * d.cout * p.acc;
+    p.tc_wgrad = wgrad_tc_supported(d);
+    p.w_bytes = p.tc_wgrad ? wgrad_tc_bytes(d) : (size_t)p.n_chunks * p.taps * d.cin * d.cout * p.acc;
 
     npvs_conv_desc t = d;
     t.relu = 0;
@@ -238,17 +242,31 @@ BwdPlan plan_bwd(const npvs_conv_desc& d) {
 }
 
 template <typename T>
+npvs_status run_dgrad(const npvs_conv_desc& d, BwdPlan& p, const void* w, const T* gg, void* dx, const void* dx_add,
+                      Arena& ar, cudaStream_t st);
+
+template <typename T>
 npvs_status run_bwd(const npvs_conv_desc& d, BwdPlan& p, const void* x, const void* w, const void* y, const void* dy,
                     void* dx, const void* dx_add, void* dw, void* db, Arena& ar, cudaStream_t st) {
     using A = typename AccOf<T>::type;
     const int cap = d.cap_out;
     T* g = d.relu ? ar.take<T>((size_t)cap * d.cout) : nullptr;
     A* part_db = ar.take<A>((size_t)p.n_db * d.cout);
-    A* part_w = ar.take<A>((size_t)p.n_chunks * p.taps * d.cin * d.cout);
     launch_k(grad_mask_kernel<T, A>, p.n_db, 256, 0, st, (const T*)dy, (const T*)y, d.relu, d.n_out, cap, d.cout, g,
              part_db);
     NPVS_TRY(check_launch("grad_mask_kernel"));
     const T* gg = d.relu ? g : (const T*)dy;
+    if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+        if (p.tc_wgrad) {
+            Arena sub(ar.take<char>(p.w_bytes), p.w_bytes);
+            NPVS_TRY(wgrad_tc(d, (const __nv_bfloat16*)x, gg, (float*)dw, sub, st));
+            launch_k(grad_reduce_kernel<A>, 1, 256, 0, st, (const A*)nullptr, 0, 0LL, (const A*)part_db, p.n_db, d.cout,
+                     (A*)dw, (A*)db);
+            NPVS_TRY(check_launch("grad_reduce_kernel"));
+            return run_dgrad<T>(d, p, w, gg, dx, dx_add, ar, st);
+        }
+    }
+    A* part_w = ar.take<A>((size_t)p.n_chunks * p.taps * d.cin * d.cout);
     dim3 wg(p.tiles, p.taps, p.n_chunks);
     if (p.tile == 32)
         launch_k(wgrad_kernel<T, A, 2>, wg, 256, 0, st, d.kind, d.map, d.n_out, cap, d.cin, d.cout, p.n_chunks,
@@ -262,8 +280,14 @@ npvs_status run_bwd(const npvs_conv_desc& d, BwdPlan& p, const void* x, const vo
     launch_k(grad_reduce_kernel<A>, rg, 256, 0, st, (const A*)part_w, p.n_chunks, nW, (const A*)part_db, p.n_db, d.cout,
              (A*)dw, (A*)db);
     NPVS_TRY(check_launch("grad_reduce_kernel"));
+    return run_dgrad<T>(d, p, w, gg, dx, dx_add, ar, st);
+}
+
+// dgrad: the transposed convolution of g
+template <typename T>
+npvs_status run_dgrad(const npvs_conv_desc& d, BwdPlan& p, const void* w, const T* gg, void* dx, const void* dx_add,
+                      Arena& ar, cudaStream_t st) {
     if (!dx) return NPVS_OK;
-    // dgrad: the transposed convolution of g
     void* wt = ar.take<char>(p.wt_bytes);
     if (d.dtype == NPVS_BF16) {
         NPVS_TRY(pack_weights_mode(p.td.kind, p.td.cin, p.td.cout, (const float*)w, wt, p.mode, st));

@@ -41,6 +41,13 @@ TcShape tc_shape(int kind, int cin, int cout, int form);
 // reversed, the transpose of a submanifold convolution).
 npvs_status pack_weights_mode(int kind, int cin, int cout, const float* w, void* packed, int mode, cudaStream_t st);
 
+// BF16 weight gradient on the tensor cores (dW FP32 [taps][cin][cout]) from the layer input x and
+// the masked output gradient g; scratch from `ar` (wgrad_tc_bytes).
+bool wgrad_tc_supported(const npvs_conv_desc& d);
+size_t wgrad_tc_bytes(const npvs_conv_desc& d);
+npvs_status wgrad_tc(const npvs_conv_desc& d, const __nv_bfloat16* x, const __nv_bfloat16* g, float* dw, Arena& ar,
+                     cudaStream_t st);
+
 npvs_status conv_tc_fwd(const npvs_conv_desc& d, const void* x, const void* w, const float* bias,
                         const void* skip, void* y, cudaStream_t st);
 
