@@ -72,6 +72,75 @@ __global__ void __launch_bounds__(256) grad_mask_kernel(const T* __restrict__ dy
     }
 }
 
+// BF16 form of grad_mask_kernel: 8 channels (16 bytes) per thread, cout / 8 threads per row, 256 /
+// (cout / 8) rows per pass; the column partials are added over the passes' rows in fixed order.
+__global__ void __launch_bounds__(256) grad_mask_bf16_kernel(const __nv_bfloat16* __restrict__ dy,
+                                                             const __nv_bfloat16* __restrict__ y, int relu,
+                                                             const int32_t* __restrict__ n_out, int cap, int cout,
+                                                             __nv_bfloat16* __restrict__ g, float* __restrict__ part_db) {
+    pdl_begin();
+    __shared__ float s[256 * 8];
+    const int n = min(*n_out, cap);
+    const int rpc = (n + gridDim.x - 1) / gridDim.x;
+    const int row0 = min((int)blockIdx.x * rpc, n), rend = min(row0 + rpc, n);
+    const int cg = cout >> 3, rpp = 256 / cg;
+    const int q = threadIdx.x / cg, grp = threadIdx.x - q * cg;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (q < rpp) {
+        for (int r = row0 + q; r < rend; r += rpp) {
+            const size_t i = (size_t)r * cout + grp * 8;
+            uint4 v = *reinterpret_cast<const uint4*>(dy + i);
+            if (relu) {
+                const uint4 m = *reinterpret_cast<const uint4*>(y + i);
+                const uint32_t* mw = reinterpret_cast<const uint32_t*>(&m);
+                uint32_t* vw = reinterpret_cast<uint32_t*>(&v);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    // a BF16 is > 0 iff its sign bit is clear and it is not +0
+                    const uint32_t lo = mw[k] & 0xFFFFu, hi = mw[k] >> 16;
+                    const uint32_t keep = ((lo != 0 && !(lo & 0x8000u)) ? 0xFFFFu : 0u) |
+                                          ((hi != 0 && !(hi & 0x8000u)) ? 0xFFFF0000u : 0u);
+                    vw[k] &= keep;
+                }
+                *reinterpret_cast<uint4*>(g + i) = v;
+            }
+            const __nv_bfloat16* b = reinterpret_cast<const __nv_bfloat16*>(&v);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] += __bfloat162float(b[k]);
+        }
+    }
+    if (q < rpp) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s[q * cout + grp * 8 + k] = acc[k];
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < cout; o += 256) {
+        float t = 0.f;
+        for (int qq = 0; qq < rpp; ++qq) t += s[qq * cout + o];
+        part_db[(size_t)blockIdx.x * cout + o] = t;
+    }
+}
+
+// db[o] = sum over the chunks (in order) of the bias partials: 32 columns x 8 chunk phases per CTA.
+template <typename A>
+__global__ void __launch_bounds__(256) grad_db_reduce_kernel(const A* __restrict__ part_db, int n_db, int cout,
+                                                             A* __restrict__ db) {
+    pdl_begin();
+    __shared__ A s[8][32];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int o = blockIdx.x * 32 + tx;
+    A acc = 0;
+    if (o < cout)
+        for (int c = ty; c < n_db; c += 8) acc += part_db[(size_t)c * cout + o];
+    s[ty][tx] = acc;
+    __syncthreads();
+    if (ty == 0 && o < cout) {
+        A t = 0;
+        for (int k = 0; k < 8; ++k) t += s[k][tx];
+        db[o] = t;
+    }
+}
+
 // Per (ci tile, co tile) x tap x row chunk: sum over the chunk's rows n of x[map(n, t)]^T g[n].
 // The chunk's rows are cut from the device row count (n_chunks equal chunks), so the work spreads
 // over every chunk whatever the occupancy. Rows are visited in windows of 256: the rows whose
@@ -252,20 +321,25 @@ npvs_status run_bwd(const npvs_conv_desc& d, BwdPlan& p, const void* x, const vo
     const int cap = d.cap_out;
     T* g = d.relu ? ar.take<T>((size_t)cap * d.cout) : nullptr;
     A* part_db = ar.take<A>((size_t)p.n_db * d.cout);
-    launch_k(grad_mask_kernel<T, A>, p.n_db, 256, 0, st, (const T*)dy, (const T*)y, d.relu, d.n_out, cap, d.cout, g,
-             part_db);
-    NPVS_TRY(check_launch("grad_mask_kernel"));
     const T* gg = d.relu ? g : (const T*)dy;
     if constexpr (std::is_same<T, __nv_bfloat16>::value) {
-        if (p.tc_wgrad) {
+        if (p.tc_wgrad && d.cout <= 2048) {
+            launch_k(grad_mask_bf16_kernel, p.n_db, 256, 0, st, (const T*)dy, (const T*)y, d.relu, d.n_out, cap, d.cout,
+                     g, (float*)part_db);
+            NPVS_TRY(check_launch("grad_mask_bf16_kernel"));
             Arena sub(ar.take<char>(p.w_bytes), p.w_bytes);
             NPVS_TRY(wgrad_tc(d, (const __nv_bfloat16*)x, gg, (float*)dw, sub, st));
-            launch_k(grad_reduce_kernel<A>, 1, 256, 0, st, (const A*)nullptr, 0, 0LL, (const A*)part_db, p.n_db, d.cout,
-                     (A*)dw, (A*)db);
-            NPVS_TRY(check_launch("grad_reduce_kernel"));
+            if (db) {
+                launch_k(grad_db_reduce_kernel<A>, ceil_div(d.cout, 32), 256, 0, st, (const A*)part_db, p.n_db, d.cout,
+                         (A*)db);
+                NPVS_TRY(check_launch("grad_db_reduce_kernel"));
+            }
             return run_dgrad<T>(d, p, w, gg, dx, dx_add, ar, st);
         }
     }
+    launch_k(grad_mask_kernel<T, A>, p.n_db, 256, 0, st, (const T*)dy, (const T*)y, d.relu, d.n_out, cap, d.cout, g,
+             part_db);
+    NPVS_TRY(check_launch("grad_mask_kernel"));
     A* part_w = ar.take<A>((size_t)p.n_chunks * p.taps * d.cin * d.cout);
     dim3 wg(p.tiles, p.taps, p.n_chunks);
     if (p.tile == 32)
