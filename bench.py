@@ -117,6 +117,18 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
+def tuned_label(cfg: dict) -> str:
+    """Short name of an autotuned BF16 layer configuration."""
+    if cfg.get("tune_form") == 2:
+        return "product"
+    name = {3: "window", 2: "gather-cp.async"}.get(cfg.get("tune_gather", 0), "gather")
+    if cfg.get("tune_max_split") == 1:
+        name += "-nosplit"
+    if cfg.get("tune_gather_warps") == 4:
+        name += "-4w"
+    return name
+
+
 def layer_algorithmic(fp, wl):
     """Per stage: (bytes, flops, bound) from the actual rulebooks of the last frame (SURVEY-style
     algorithmic counts: each operand byte once, FLOPs = 2 * pairs * cin * cout)."""
@@ -381,7 +393,7 @@ def run_batched(args, dev, net, tuned):
             "per_viewcell_ms": {"p50": round(float(np.percentile(lat, 50)), 4),
                                 "p99": round(float(np.percentile(lat, 99)), 4), "max": round(max(lat), 4)},
             "active_sites_level0": n_act, "capacity_frac": frac,
-            "autotuned_form": {k: v[0].get("tune_form", 0) for k, v in tuned_b.items()}}
+            "autotuned": {k: tuned_label(v[0]) for k, v in tuned_b.items()}}
 
 
 def run_highres(args, dev, tf_bf16, hbm_gbs):
@@ -599,7 +611,7 @@ def run_ours(args):
         "frame_roofline": {"bytes": frame_bytes, "flops": frame_flops, "roof_ms": round(frame_roof_ms, 5),
                            "frac": round(frame_roof_ms / ms, 5)},
         "active_sites": [int(lv.n_rows.item()) for lv in fp.levels],
-        "autotuned": {k: [v[0].get("tune_form", 0), round(v[1], 2)] for k, v in tuned.items()},
+        "autotuned": {k: [tuned_label(v[0]), round(v[1], 2)] for k, v in tuned.items()},
     }
     if clk:
         line["clocks"] = clk

@@ -144,12 +144,15 @@ typedef struct {
                         counters at zero again. Calls sharing one workspace must not overlap on
                         the device. NULL: gather form without split-K. */
     size_t workspace_bytes;
-    int32_t tune_stages;    /* BF16: shared-memory pipeline stages, 3..12 (0 = the most that fit) */
+    int32_t tune_stages;    /* BF16: shared-memory pipeline stages, 3..12 (window gather 2..12;
+                               0 = the most that fit) */
     int32_t tune_max_split; /* BF16: largest split-K factor (0 = 8; 1 = never split) */
     int32_t tune_lag;       /* BF16 cp.async gather: groups in flight per thread before a stage is
                                published (0 = 2; clamped to stages - 1) */
     int32_t tune_gather;    /* BF16 gather form: 0 auto, 1 TMA tile::gather4 (cin % 32 == 0),
-                               2 cp.async */
+                               2 cp.async, 3 window gather (SUBM3, cin % 32 == 0: per 128-row tile
+                               and dz plane a dense TMA window of input rows, the A operand built
+                               from it in shared memory) */
     int32_t tune_gather_warps; /* BF16: gather warps per CTA, 4 or 8 (0 = 8) */
     int32_t tune_form;      /* BF16 SUBM3 / DOWN2 / UP2: 0 auto (product form when the workspace
                                holds T), 1 gather (UP2: scatter-epilogue) form, 2 product form */

@@ -26,6 +26,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <climits>
 #include <cstring>
 
 #include "conv_tc.cuh"
@@ -48,7 +49,10 @@ struct TcParams {
     int scatter;   // epilogue: GEMM column block j -> child row map2[n][j] (transposed stride-2 conv)
     int tout;      // epilogue: raw FP32 accumulators into T [rows][Ntot] (product form)
     int KB, Kflat, Ntot, Npad, BN, n_tiles, stages;
-    int gmode;     // A operand: 0 cp.async gather, 1 TMA gather4, 2 TMA dense tile (rows m0..m0+127)
+    int gmode;     // A operand: 0 cp.async gather, 1 TMA gather4, 2 TMA dense tile (rows m0..m0+127),
+                   // 3 window gather (SUBM3: dense TMA windows of input rows, A built in shared memory)
+    int win_rows;  // window gather: rows of one window (one window per dz plane)
+    int ncb;       // window gather: channel blocks of x (cin / BKE)
     int BKE, RB;   // k-block width (elements) and its row bytes
     int rows_x;    // rows of x (the out-of-range row used for absent neighbours)
     int taps;      // stride of the gather map (27, 8) or 0 when row n reads input row n
@@ -159,6 +163,38 @@ __device__ __forceinline__ void store16(const TcParams& p, int n, int ng, const 
     }
 }
 
+// Window gather: one warp stages the A tile of tap t (one channel block) for the 128 rows of a
+// tile. Row r (< rvalid) reads its neighbour map[r][t] from the window of t's dz plane (rows
+// loj ...), or from global memory past the window end; absent neighbours and rows are zeros. The tile is written with the
+// k-block's shared-memory swizzle, in batches of 8 chunks per lane (loads before stores).
+template <int CH>
+__device__ __forceinline__ void window_build_a(uint8_t* a_stage, const uint8_t* wj, const int* map_s, int t, int loj,
+                                               int win_rows, int rvalid, const __nv_bfloat16* __restrict__ x, int cin,
+                                               int col0, int lane) {
+    constexpr int RB = CH * 16, PER = kBM * CH / 32, BATCH = 8;
+#pragma unroll 1
+    for (int q0 = 0; q0 < PER; q0 += BATCH) {
+        uint4 v[BATCH];
+        int dst[BATCH];
+#pragma unroll
+        for (int q = 0; q < BATCH; ++q) {
+            const int i = lane + 32 * (q0 + q), r = i / CH, c = i % CH;
+            const int n = r < rvalid ? map_s[r * 27 + t] : -1;
+            v[q] = make_uint4(0u, 0u, 0u, 0u);
+            if (n >= 0) {
+                const int w = n - loj;  // >= 0: loj is the smallest neighbour row of the plane
+                if (w < win_rows)
+                    v[q] = *reinterpret_cast<const uint4*>(wj + w * RB + c * 16);
+                else
+                    v[q] = __ldg(reinterpret_cast<const uint4*>(x + (size_t)n * cin + col0) + c);
+            }
+            dst[q] = r * RB + ((c ^ (((r * RB) >> 7) & (CH - 1))) << 4);
+        }
+#pragma unroll
+        for (int q = 0; q < BATCH; ++q) *reinterpret_cast<uint4*>(a_stage + dst[q]) = v[q];
+    }
+}
+
 // Work units: (row tile, column tile, k-chunk). Layers with few row tiles may split their k-blocks
 // over up to gridDim.x CTAs; each writes an FP32 partial tile, and for every 32-row slice the last
 // epilogue warp to finish (atomic counter) sums the partials in k-chunk order, so results do not
@@ -175,23 +211,52 @@ __device__ __forceinline__ void store16(const TcParams& p, int n, int ng, const 
 template <int LAG, int PW>
 __global__ void __launch_bounds__(threads_for(PW), 1)
     conv_tc_kernel(const TcParams p, const __grid_constant__ CUtensorMap tmap) {
-    pdl_begin();
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int S = p.stages;
     const uint32_t a_bytes = (uint32_t)kBM * p.RB, b_bytes = (uint32_t)p.BN * p.RB;
+    const uint32_t win1 = p.gmode == 3 ? (uint32_t)p.win_rows * p.RB : 0u;  // bytes of one window
     uint8_t* sA = smem;
     uint8_t* sB = smem + (size_t)S * a_bytes;
-    int* map_s = reinterpret_cast<int*>(sB + (size_t)S * b_bytes);
+    uint8_t* win = sB + (size_t)S * b_bytes;  // window gather: 3 windows (dz = -1, 0, 1)
+    int* map_s = reinterpret_cast<int*>(win + 3 * (size_t)win1);
     float* s_bias = reinterpret_cast<float*>(map_s + kBM * p.taps + 4);  // [4 warps][256]
     uint64_t* bars = reinterpret_cast<uint64_t*>(s_bias + 4 * 256);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * S + 5);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * S + 8);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    int* part_lo = const_cast<int*>(abort_flag) + 1;  // window gather: [PW][3] per-warp window starts
     const uint32_t full0 = smem_u32(bars), bfull0 = smem_u32(bars + S), empty0 = smem_u32(bars + 2 * S);
     const uint32_t tfull0 = smem_u32(bars + 3 * S), tempty0 = smem_u32(bars + 3 * S + 2);
     const uint32_t mdone = smem_u32(bars + 3 * S + 4);
-
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // Set-up that reads nothing an earlier kernel writes runs before griddepcontrol.wait, so it
+    // overlaps the tail of the previous kernel on the stream.
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            // TMA: one expect_tx; cp.async: one arrival per gather warp; window gather: one arrival
+            // by the warp that built the stage (its weight bytes are expected on the same barrier)
+            mbar_init(full0 + 8 * s, p.gmode == 0 ? PW : 1);
+            mbar_init(bfull0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull0 + 8 * b, 1);
+            mbar_init(tempty0 + 8 * b, 4);  // one arrival per epilogue warp
+        }
+        mbar_init(mdone, 1);
+        mbar_init(mdone + 8, PW);  // window gather: gather-warp rendezvous
+        mbar_init(mdone + 16, 1);  // window gather: windows landed (transaction bytes)
+        mbar_init(mdone + 24, 1);  // window gather: the tile's neighbour map landed
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == PW + 4) {
+        tmem_alloc(smem_u32(tmem_slot), 2 * p.acc_cols);
+        tmem_relinquish();
+    }
+    pdl_begin();
+
     const int n_rows = min(*p.n_rows, p.cap_rows);
     const int tiles = ((n_rows + kBM - 1) / kBM) * p.n_tiles;
     int ksplit = 1, kbc = p.KB;
@@ -201,32 +266,14 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
         ksplit = (p.KB + kbc - 1) / kbc;
     }
     const int units = tiles * ksplit;
-    if ((int)blockIdx.x >= units) return;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < S; ++s) {
-            mbar_init(full0 + 8 * s, p.gmode ? 1 : PW);  // TMA: one expect_tx; cp.async: one per warp
-            mbar_init(bfull0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, 1);
-        }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(tfull0 + 8 * b, 1);
-            mbar_init(tempty0 + 8 * b, 4);  // one arrival per epilogue warp
-        }
-        mbar_init(mdone, 1);
-        *abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == PW + 4) {
-        tmem_alloc(smem_u32(tmem_slot), 2 * p.acc_cols);
-        tmem_relinquish();
-    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp < PW && p.gmode == 2) {
+    if ((int)blockIdx.x >= units) {
+        // no work: straight to the teardown (TMEM was allocated above)
+    } else     if (warp < PW && p.gmode == 2) {
         // ------------------------------------------------------------------ TMA dense A tile
         if (warp == 0) {
             uint32_t it = 0;
@@ -312,6 +359,151 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
         if (warp == 0 && lane == 0)  // nothing the TMA engine writes may still be landing when the CTA leaves
             for (uint32_t j = it >= (uint32_t)S ? it - S : 0; j < it; ++j)
                 mbar_wait(full0 + 8 * (j % S), (j / S) & 1, abort_flag);
+        __syncwarp();
+    } else if (warp < PW && p.gmode == 3) {
+        // ------------------------------------------------------------------ window gather (SUBM3)
+        // Rows are in linear site order, so the neighbours of a 128-row tile through the 9 taps of
+        // one dz plane lie in a short run of input rows starting at the smallest of them. Per
+        // channel block the three runs (windows of win_rows rows) come in as dense TMA tiles; each
+        // k-block (tap t, channel block cb) then builds its A stage row by row from the window of
+        // t's plane (a neighbour past the window end is read from global memory), so no row is
+        // fetched from global memory once per tap. Gather warps meet at an mbarrier (bounded waits).
+        const int tid = threadIdx.x;
+        const int RPW = kBM / PW;  // neighbour-map rows scanned by each warp
+        const uint32_t rdv = mdone + 8, wfull = mdone + 16, mfull = mdone + 24;
+        const int NB = min(PW, S);  // warps that build stages
+        uint32_t rdv_ph = 0, wf_ph = 0, mf_ph = 0, it = 0;
+        int s_it = 0, own_it = 0;   // stage (it % S) and builder warp (it % NB) of iteration it
+        uint32_t ph_it = 0;         // phase parity of iteration it on its stage ((it / S) & 1)
+        bool stop = false;
+        auto rendezvous = [&]() {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(rdv);
+            mbar_wait(rdv, rdv_ph & 1, abort_flag);
+            ++rdv_ph;
+            return __any_sync(0xffffffffu, *abort_flag) != 0;
+        };
+        for (int u = blockIdx.x; u < units && !stop; u += gridDim.x) {
+            const int tile = u / ksplit, kc = u - tile * ksplit;
+            const int mt = tile / p.n_tiles, nt = tile - mt * p.n_tiles;
+            const int m0 = mt * kBM;
+            const int kb0 = kc * kbc, kb1 = min(p.KB, kb0 + kbc);
+            fence_proxy_async();
+            if (rendezvous()) break;  // the previous unit's map, bounds and windows are no longer read
+            if (tid == 0) {
+                // the tile's neighbour-map rows (contiguous) in one bulk copy; the copy size must be a
+                // multiple of 16 bytes (4 rows), the last < 4 rows of the map come by plain loads
+                const int rows = min(kBM, p.cap_rows - m0), rows4 = rows & ~3;
+                for (int e = rows4 * 27; e < rows * 27; ++e) map_s[e] = __ldg(p.map + (size_t)m0 * 27 + e);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mfull),
+                             "r"((uint32_t)rows4 * 108u)
+                             : "memory");
+                if (rows4 > 0) bulk_g2s(smem_u32(map_s), p.map + (size_t)m0 * 27, (uint32_t)rows4 * 108u, mfull);
+            }
+            mbar_wait(mfull, mf_ph & 1, abort_flag);
+            ++mf_ph;
+            const int rvalid = n_rows - m0;  // rows of the tile that exist (map rows past it are stale)
+            int mn0 = INT_MAX, mn1 = INT_MAX, mn2 = INT_MAX;
+            for (int e = lane; e < RPW * 27; e += 32) {
+                const int r = warp * RPW + e / 27, t = e % 27;
+                const int v = r < rvalid ? map_s[r * 27 + t] : -1;
+                const int vv = v >= 0 ? v : INT_MAX;
+                if (t < 9) mn0 = min(mn0, vv);
+                else if (t < 18) mn1 = min(mn1, vv);
+                else mn2 = min(mn2, vv);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                mn0 = min(mn0, __shfl_xor_sync(0xffffffffu, mn0, o));
+                mn1 = min(mn1, __shfl_xor_sync(0xffffffffu, mn1, o));
+                mn2 = min(mn2, __shfl_xor_sync(0xffffffffu, mn2, o));
+            }
+            if (lane == 0) {
+                part_lo[warp * 3 + 0] = mn0;
+                part_lo[warp * 3 + 1] = mn1;
+                part_lo[warp * 3 + 2] = mn2;
+            }
+            if (rendezvous()) break;  // the per-warp minima are complete
+            int lo[3] = {INT_MAX, INT_MAX, INT_MAX};
+            for (int w2 = 0; w2 < PW; ++w2) {
+                lo[0] = min(lo[0], part_lo[w2 * 3 + 0]);
+                lo[1] = min(lo[1], part_lo[w2 * 3 + 1]);
+                lo[2] = min(lo[2], part_lo[w2 * 3 + 2]);
+            }
+            int cur = -1;
+            for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                const int s = s_it, own = own_it;
+                const uint32_t ph = ph_it;
+                if (++s_it == S) {
+                    s_it = 0;
+                    ph_it ^= 1u;
+                }
+                if (++own_it == NB) own_it = 0;
+                const int cb = kb / 27, t = kb - cb * 27;
+                if (cb != cur) {
+                    if (cur >= 0) {
+                        fence_proxy_async();
+                        if (rendezvous()) {  // every warp is done with the current windows
+                            stop = true;
+                            break;
+                        }
+                    }
+                    if (tid == 0) {
+                        // planes whose taps this unit runs in channel block cb (a k-split unit may hold a few taps)
+                        const int t_lo = max(kb0, cb * 27) - cb * 27, t_hi = min(kb1, cb * 27 + 27) - 1 - cb * 27;
+                        bool need[3];
+                        uint32_t bytes = 0;
+                        for (int j = 0; j < 3; ++j) {
+                            need[j] = lo[j] != INT_MAX && 9 * j <= t_hi && 9 * j + 8 >= t_lo;
+                            bytes += need[j] ? win1 : 0u;
+                        }
+                        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(wfull), "r"(bytes)
+                                     : "memory");
+                        for (int j = 0; j < 3; ++j)
+                            if (need[j]) tma_tile2d(smem_u32(win + j * win1), &tmap, cb * p.BKE, lo[j], wfull);
+                    }
+                    mbar_wait(wfull, wf_ph & 1, abort_flag);
+                    ++wf_ph;
+                    if (__any_sync(0xffffffffu, *abort_flag)) {
+                        stop = true;
+                        break;
+                    }
+                    cur = cb;
+                }
+                // stage `it` is built by warp it % NB alone, so the warps' wait / build / publish chains
+                // overlap. NB <= S keeps every wait within one phase of its barrier: the warp's
+                // previous stage (it - NB) waited for the release of it - NB - S >= it - 2S.
+                if (own != warp) continue;
+                mbar_wait(empty0 + 8 * s, ph ^ 1u, abort_flag);
+                if (__any_sync(0xffffffffu, *abort_flag)) {
+                    stop = true;
+                    break;
+                }
+                if (lane == 0) {  // the weight block lands on the stage's own barrier
+                    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(full0 + 8 * s),
+                                 "r"(b_bytes)
+                                 : "memory");
+                    const __nv_bfloat16* wsrc = p.w + ((size_t)(t * p.ncb + cb) * p.Npad + (size_t)nt * p.BN) * p.BKE;
+                    bulk_g2s(smem_u32(sB + (size_t)s * b_bytes), wsrc, b_bytes, full0 + 8 * s);
+                }
+                const int j = t / 9, loj = j == 0 ? lo[0] : (j == 1 ? lo[1] : lo[2]);
+                const uint8_t* wj = win + j * win1;
+                uint8_t* a_stage = sA + (size_t)s * a_bytes;
+                if (p.RB == 128)
+                    window_build_a<8>(a_stage, wj, map_s, t, loj, p.win_rows, rvalid, p.x, p.cin, cb * p.BKE, lane);
+                else
+                    window_build_a<4>(a_stage, wj, map_s, t, loj, p.win_rows, rvalid, p.x, p.cin, cb * p.BKE, lane);
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(full0 + 8 * s);
+            }
+        }
+        if (tid == 0) {  // nothing the TMA engine writes may still be landing when the CTA leaves
+            if (wf_ph > 0) mbar_wait(wfull, (wf_ph - 1) & 1, abort_flag);
+            if (mf_ph > 0) mbar_wait(mfull, (mf_ph - 1) & 1, abort_flag);
+            for (uint32_t j = it >= (uint32_t)S ? it - S : 0; j < it; ++j)
+                mbar_wait(full0 + 8 * (j % S), (j / S) & 1, abort_flag);
+        }
         __syncwarp();
     } else if (warp < PW) {
         // ------------------------------------------------------------------ cp.async gather
@@ -487,7 +679,9 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
             // -------------------------------------------------------------- MMA issuer
             const uint32_t idesc = make_idesc(kBM, p.BN);
             const int kk_steps = p.BKE / 16;
-            uint32_t it = 0, tc = 0;
+            uint32_t tc = 0;
+            int s = 0;          // stage of the next k-block
+            uint32_t ph = 0;    // its phase parity
             bool stop = false;
             for (int u = blockIdx.x; u < units && !stop; u += gridDim.x, ++tc) {
                 const int kc = u - (u / ksplit) * ksplit;
@@ -497,10 +691,9 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
                 mbar_wait(tempty0 + 8 * buf, ((tc >> 1) & 1) ^ 1, abort_flag);
                 if (*abort_flag) break;
                 tc_fence_after();
-                for (int kb = kb0; kb < kb1; ++kb, ++it) {
-                    const int s = (int)(it % S);
-                    mbar_wait(full0 + 8 * s, (it / S) & 1, abort_flag);
-                    if (p.gmode == 0) mbar_wait(bfull0 + 8 * s, (it / S) & 1, abort_flag);
+                for (int kb = kb0; kb < kb1; ++kb) {
+                    mbar_wait(full0 + 8 * s, ph, abort_flag);
+                    if (p.gmode == 0) mbar_wait(bfull0 + 8 * s, ph, abort_flag);
                     if (*abort_flag) {
                         stop = true;
                         break;
@@ -511,6 +704,10 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
                         tc_mma(acc, make_sdesc(a0 + 32 * k, p.RB), make_sdesc(b0 + 32 * k, p.RB), idesc,
                                (kb > kb0 || k > 0) ? 1u : 0u);
                     tc_commit(empty0 + 8 * s);
+                    if (++s == S) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
                 }
                 if (!stop) tc_commit(tfull0 + 8 * buf);
             }
@@ -641,14 +838,30 @@ __global__ void pack_weights_kernel(int kind, int cin, int cout, TcShape sh, con
 constexpr int kMaxStages = 12;
 constexpr size_t kMaxSmem = 227 * 1024;
 
-size_t tc_smem_bytes(int BN, int RB, int taps, int S) {
-    return 1024 + (size_t)S * (kBM + BN) * RB + (size_t)kBM * taps * 4 + 16 + 4 * 256 * 4 + (3 * S + 5) * 8 + 16;
+// win: bytes of the three windows of the window gather (0 otherwise).
+size_t tc_smem_bytes(int BN, int RB, int taps, int S, size_t win = 0) {
+    return 1024 + (size_t)S * (kBM + BN) * RB + win + (size_t)kBM * taps * 4 + 16 + 4 * 256 * 4 + (3 * S + 8) * 8 +
+           16 + 8 * 3 * 4;
 }
 
 int tc_stages(int BN, int RB, int taps) {
     for (int S = kMaxStages; S > 4; --S)
         if (tc_smem_bytes(BN, RB, taps, S) <= kMaxSmem) return S;
     return 4;
+}
+
+// Window gather: the longest window (256 or 128 rows) that leaves room for at least three stages
+// (two with 128-row windows); 0 when not even that fits.
+int win_rows_for(int BN, int RB, int* stages) {
+    for (int wr = 256; wr >= 128; wr -= 128) {
+        const size_t win = 3 * (size_t)wr * RB;
+        for (int S = kMaxStages; S >= (wr == 256 ? 3 : 2); --S)
+            if (tc_smem_bytes(BN, RB, 27, S, win) <= kMaxSmem) {
+                *stages = S;
+                return wr;
+            }
+    }
+    return 0;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -720,14 +933,22 @@ npvs_status run_gemm(TcParams& p, const TcShape& sh, const npvs_conv_desc& d, co
     p.n_tiles = sh.n_tiles;
     p.BKE = sh.BKE;
     p.RB = sh.RB;
-    p.stages = tc_stages(sh.BN, sh.RB, p.taps);
-    if (d.tune_stages >= 3 && d.tune_stages < p.stages) p.stages = d.tune_stages;
+    size_t win = 0;
+    if (p.gmode == 3) {
+        p.win_rows = win_rows_for(sh.BN, sh.RB, &p.stages);
+        NPVS_REQUIRE(p.win_rows > 0, NPVS_ERR_UNSUPPORTED, "BF16 conv: window gather does not fit this shape");
+        p.ncb = d.cin / sh.BKE;
+        win = 3 * (size_t)p.win_rows * sh.RB;
+    } else {
+        p.stages = tc_stages(sh.BN, sh.RB, p.taps);
+    }
+    if (d.tune_stages >= (p.gmode == 3 ? 2 : 3) && d.tune_stages < p.stages) p.stages = d.tune_stages;
     lag = std::min(lag, p.stages - 1);
     if (lag == 5) lag = 4;  // instantiated lags: 1, 2, 3, 4, 6 (all < stages)
     p.acc_cols = 32;
     while ((int)p.acc_cols < sh.BN) p.acc_cols <<= 1;
     if (p.cap_rows <= 0) return NPVS_OK;
-    const size_t smem = tc_smem_bytes(sh.BN, sh.RB, p.taps, p.stages);
+    const size_t smem = tc_smem_bytes(sh.BN, sh.RB, p.taps, p.stages, win);
     alignas(64) CUtensorMap tm;
     std::memset(&tm, 0, sizeof(tm));
     if (p.gmode != 0) {
@@ -735,11 +956,14 @@ npvs_status run_gemm(TcParams& p, const TcShape& sh, const npvs_conv_desc& d, co
         NPVS_REQUIRE(enc != nullptr, NPVS_ERR_CUDA, "BF16 conv: cuTensorMapEncodeTiled unavailable");
         const cuuint64_t gdim[2] = {(cuuint64_t)d.cin, (cuuint64_t)p.rows_x};
         const cuuint64_t gstride[1] = {(cuuint64_t)d.cin * 2};
-        const cuuint32_t box[2] = {(cuuint32_t)sh.BKE, p.gmode == 2 ? (cuuint32_t)kBM : 1u};
+        const cuuint32_t box_rows = p.gmode == 2 ? (cuuint32_t)kBM : (p.gmode == 3 ? (cuuint32_t)p.win_rows : 1u);
+        const cuuint32_t box[2] = {(cuuint32_t)sh.BKE, box_rows};
         const cuuint32_t estride[2] = {1, 1};
+        // windows are read row by row from shared memory: unswizzled
+        const CUtensorMapSwizzle swz = p.gmode == 3 ? CU_TENSOR_MAP_SWIZZLE_NONE
+                                                    : (sh.RB == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B);
         CUresult r = enc(&tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(x), gdim, gstride, box, estride,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE,
-                         sh.RB == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
             set_error("BF16 conv: cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -877,6 +1101,7 @@ npvs_status conv_tc_fwd(const npvs_conv_desc& d, const void* x, const void* w, c
     p.counters = counters;
     if (!sh.tma) p.gmode = 0;
     else if (p.taps == 0) p.gmode = 2;      // rows of x read in order: dense tiles
+    else if (d.tune_gather == 3 && d.kind == NPVS_CONV_SUBM3) p.gmode = 3;
     else p.gmode = (d.tune_gather == 2 && sh.BKE == 64) ? 0 : 1;
     return run_gemm(p, sh, d, x, lag, st);
 }

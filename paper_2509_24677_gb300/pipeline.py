@@ -243,18 +243,21 @@ class FramePipeline:
     # ---- autotuning ------------------------------------------------------------------------------
     CANDIDATES = {
         "subm3": [dict(tune_form=2), dict(tune_form=1, tune_gather_warps=8),
-                  dict(tune_form=1, tune_gather_warps=8, tune_max_split=1), dict(tune_form=1, tune_gather_warps=4)],
+                  dict(tune_form=1, tune_gather_warps=8, tune_max_split=1), dict(tune_form=1, tune_gather_warps=4),
+                  dict(tune_form=1, tune_gather=3), dict(tune_form=1, tune_gather=3, tune_max_split=1),
+                  dict(tune_form=1, tune_gather=3, tune_gather_warps=4)],
         "down2": [dict(tune_form=2), dict(tune_form=1, tune_gather_warps=8),
                   dict(tune_form=1, tune_gather_warps=8, tune_max_split=1)],
         "up2": [dict(tune_form=2), dict(tune_form=1)],
         "head1": [dict()],
     }
 
-    def autotune(self, boxes, box_offsets, cams_dev, reps: int = 10):
+    def autotune(self, boxes, box_offsets, cams_dev, reps: int = 10, record: Optional[dict] = None):
         """Times the candidate configurations of every BF16 layer on this frame (each as a CUDA
         graph of `reps` launches) and keeps the fastest in the layer's descriptor. The best choice
         depends on the active-site counts, so tune on a representative frame. Returns
-        {layer: (config, microseconds)}."""
+        {layer: (config, microseconds)}; `record`, if given, receives every candidate's time as
+        {layer: [(config, microseconds), ...]}."""
         if self.dtype != L.BF16:
             return {}
         self.run(boxes, box_offsets, cams_dev, want_probs=False)
@@ -282,6 +285,8 @@ class FramePipeline:
                 e1.record()
                 torch.cuda.synchronize()
                 us = e0.elapsed_time(e1) * 1000.0 / reps
+                if record is not None:
+                    record.setdefault(l.name, []).append((cfg, us))
                 if best is None or us < best[1]:
                     best = (cfg, us)
             for k, v in best[0].items():

@@ -279,21 +279,66 @@ CONV_CASES = [
 ]
 
 
+WINDOW_MODES = ("window", "window-split", "window-s2")
+
+
 @pytest.mark.parametrize("dt,mode", [("f32", None), ("bf16", "gather"), ("bf16", "gather-split"),
-                                     ("bf16", "product")])
+                                     ("bf16", "product"), ("bf16", "window"), ("bf16", "window-split")])
 @pytest.mark.parametrize("kind,cin,cout", CONV_CASES)
 def test_single_conv_parity(kind, cin, cout, dt, mode):
-    L, ops, P = lib()
     if dt == "bf16" and kind == "up2" and cout % 16:
         pytest.skip("BF16 up conv needs cout % 16 == 0")
     if mode == "product" and kind not in ("subm3", "down2", "up2"):
         pytest.skip("the product form applies to submanifold, strided and transposed convs")
+    if mode in WINDOW_MODES and (kind != "subm3" or cin % 32):
+        pytest.skip("the window gather applies to submanifold convs with cin % 32 == 0")
     rng = np.random.default_rng(sum(map(ord, kind)) * 100003 + cin * 1009 + cout)
     occ = rng.random((2, 10, 12, 14)) < 0.12          # ~ 800 fine sites: several 128-row tiles
+    got, ref, _ = single_conv(kind, cin, cout, dt, mode, occ, rng)
+    err = normwise(got, ref)
+    assert err <= (8e-3 if dt == "bf16" else 1e-5), err
+
+
+def dense_next_plane_occupancy():
+    """Coarse occupancy where the window gather's windows overflow: in each batch element, plane
+    z = 1 holds every 9th site of a 32 x 32 plane and plane z = 2 is full, so a 128-row tile of
+    plane 1 has its dz = +1 neighbours spread over ~1,000 rows of plane 2 (far more than one
+    window); the other planes are sparse, and the last tile is ragged."""
+    rng = np.random.default_rng(77)
+    occ = rng.random((2, 6, 32, 32)) < 0.05
+    occ[:, 1] = False
+    occ[:, 1].reshape(2, -1)[:, ::9] = True
+    occ[:, 2] = True
+    occ[1, 4, 5, :7] = True
+    return occ
+
+
+@pytest.mark.parametrize("cin,cout", [(32, 32), (64, 64), (128, 32), (256, 256)])
+@pytest.mark.parametrize("mode", WINDOW_MODES)
+def test_window_gather_window_overflow(cin, cout, mode):
+    """Neighbours past the end of a tile's window are read from global memory: results equal the
+    oracle, and (one channel block, same k order, no k-split) bitwise the gather form's."""
+    rng = np.random.default_rng(cin * 7 + cout)
+    occ = dense_next_plane_occupancy()
+    got, ref, y = single_conv("subm3", cin, cout, "bf16", mode, occ, rng)
+    assert normwise(got, ref) <= 8e-3
+    got_g, _, _ = single_conv("subm3", cin, cout, "bf16", "gather", occ, np.random.default_rng(cin * 7 + cout),
+                              want_ref=False)
+    if cin <= 64 and mode != "window-split":
+        np.testing.assert_array_equal(got, got_g)
+    else:   # another summation order of the FP32 accumulators: BF16 outputs may differ by an ulp
+        assert normwise(got, got_g) <= 2.0 ** -7
+
+
+def single_conv(kind, cin, cout, dt, mode, occ, rng, want_ref=True):
+    """One convolution of `kind` on the levels of coarse occupancy `occ` through the C ABI and the
+    oracle's masked dense convolution on the same (BF16-rounded where BF16) operands. Returns the
+    device output rows, the oracle's and the device output buffer (rows past n_out are NaN)."""
+    L, ops, P = lib()
     lvs, c0 = make_levels(occ, 2)
     build_rulebooks(lvs)
     torch.cuda.synchronize()
-    fine = onet.Level(c0, (2, 10, 12, 14))
+    fine = onet.Level(c0, occ.shape)
     coarse = fine.parent()
     layer = I.Layer("t", kind, cin, cout, True)
     ws, _ = I.kaiming_uniform([layer], seed=5)
@@ -312,9 +357,11 @@ def test_single_conv_parity(kind, cin, cout, dt, mode):
           "down2": lambda: onet.down2(fine, coarse, T(x_ref), T(w_ref), T(b)),
           "up2": lambda: onet.up2(coarse, fine, T(x_ref), T(w_ref), T(b)),
           "head1": lambda: onet.head1(fine, T(x_ref), T(w_ref), T(b))}[kind]
-    ref = torch.relu(fn()).numpy()
-    if s_ref is not None:
-        ref = ref + s_ref
+    ref = None
+    if want_ref:
+        ref = torch.relu(fn()).numpy()
+        if s_ref is not None:
+            ref = ref + s_ref
     # device side
     lv_out = lvs[1] if kind == "down2" else lvs[0]
     dtype = L.BF16 if dt == "bf16" else L.F32
@@ -334,8 +381,10 @@ def test_single_conv_parity(kind, cin, cout, dt, mode):
     lv_in = lvs[1] if kind == "up2" else lvs[0]
     desc = ops.conv_desc(kid, dtype, cin, cout, True, mp, lv_out.n_rows, lv_out.capacity, out_f32=out_f32,
                          map2=lvs[0].down if kind == "up2" else None, n_in=lv_in.n_rows, cap_in=lv_in.capacity,
-                         status=status, form={"gather": 1, "gather-split": 1, "product": 2}.get(mode, 0))
-    if mode in ("gather-split", "product"):
+                         status=status, form={"gather": 1, "gather-split": 1, "product": 2}.get(mode, 0),
+                         gather=3 if mode in WINDOW_MODES else 0, max_split=1 if mode in ("window", "window-s2") else 0,
+                         stages=2 if mode == "window-s2" else 0)
+    if mode in ("gather-split", "product", "window-split"):
         ws = ops.conv_workspace(ops.npvs_conv_workspace_bytes(desc), DEV)
         desc.workspace, desc.workspace_bytes = ws.data_ptr(), ws.numel()
     w_dev = torch.from_numpy(w).to(DEV).contiguous()
@@ -347,9 +396,8 @@ def test_single_conv_parity(kind, cin, cout, dt, mode):
     assert ops.npvs_check_status(status) == 0
     got = y[:n_out].float().cpu().numpy()
     assert not np.isnan(got).any()
-    err = normwise(got, ref)
-    assert err <= (8e-3 if dt == "bf16" else 1e-5), err
     assert torch.isnan(y[n_out:].float()).all()       # rows past n_out untouched
+    return got, ref, y
 
 
 # ------------------------------------------------------------------------------------------
