@@ -121,7 +121,7 @@ def tuned_label(cfg: dict) -> str:
     """Short name of an autotuned BF16 layer configuration."""
     if cfg.get("tune_form") == 2:
         return "product"
-    name = {3: "window", 2: "gather-cp.async"}.get(cfg.get("tune_gather", 0), "gather")
+    name = {3: "window", 4: "window3", 2: "gather-cp.async"}.get(cfg.get("tune_gather", 0), "gather")
     if cfg.get("tune_max_split") == 1:
         name += "-nosplit"
     if cfg.get("tune_gather_warps") == 4:

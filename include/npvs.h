@@ -152,7 +152,9 @@ typedef struct {
     int32_t tune_gather;    /* BF16 gather form: 0 auto, 1 TMA tile::gather4 (cin % 32 == 0),
                                2 cp.async, 3 window gather (SUBM3, cin % 32 == 0: per 128-row tile
                                and dz plane a dense TMA window of input rows, the A operand built
-                               from it in shared memory) */
+                               from it in shared memory), 4 window gather with the three taps of
+                               one (dz, dy) row per pipeline stage (one tap where three do not fit
+                               in shared memory) */
     int32_t tune_gather_warps; /* BF16: gather warps per CTA, 4 or 8 (0 = 8) */
     int32_t tune_form;      /* BF16 SUBM3 / DOWN2 / UP2: 0 auto (product form when the workspace
                                holds T), 1 gather (UP2: scatter-epilogue) form, 2 product form */

@@ -53,6 +53,7 @@ struct TcParams {
                    // 3 window gather (SUBM3: dense TMA windows of input rows, A built in shared memory)
     int win_rows;  // window gather: rows of one window (one window per dz plane)
     int ncb;       // window gather: channel blocks of x (cin / BKE)
+    int G;         // k-blocks per pipeline stage (window gather: taps of one (dz, dy) row; else 1)
     int BKE, RB;   // k-block width (elements) and its row bytes
     int rows_x;    // rows of x (the out-of-range row used for absent neighbours)
     int taps;      // stride of the gather map (27, 8) or 0 when row n reads input row n
@@ -175,23 +176,29 @@ __device__ __forceinline__ void window_build_a(uint8_t* a_stage, const uint8_t* 
 #pragma unroll 1
     for (int q0 = 0; q0 < PER; q0 += BATCH) {
         uint4 v[BATCH];
-        int dst[BATCH];
+        int nr[BATCH];
+        bool far = false;
 #pragma unroll
-        for (int q = 0; q < BATCH; ++q) {
-            const int i = lane + 32 * (q0 + q), r = i / CH, c = i % CH;
+        for (int q = 0; q < BATCH; ++q) {  // window rows: every load in bounds, absent ones discarded
+            const int r = (lane + 32 * (q0 + q)) / CH, c = lane % CH;
             const int n = r < rvalid ? map_s[r * 27 + t] : -1;
-            v[q] = make_uint4(0u, 0u, 0u, 0u);
-            if (n >= 0) {
-                const int w = n - loj;  // >= 0: loj is the smallest neighbour row of the plane
-                if (w < win_rows)
-                    v[q] = *reinterpret_cast<const uint4*>(wj + w * RB + c * 16);
-                else
-                    v[q] = __ldg(reinterpret_cast<const uint4*>(x + (size_t)n * cin + col0) + c);
-            }
-            dst[q] = r * RB + ((c ^ (((r * RB) >> 7) & (CH - 1))) << 4);
+            const int w = n - loj;  // >= 0 for present neighbours: loj is the plane's smallest
+            const bool in = n >= 0 && w < win_rows;
+            far |= n >= 0 && w >= win_rows;
+            const uint4 u = *reinterpret_cast<const uint4*>(wj + min(max(w, 0), win_rows - 1) * RB + c * 16);
+            v[q] = in ? u : make_uint4(0u, 0u, 0u, 0u);
+            nr[q] = (n >= 0 && !in) ? n : -1;
+        }
+        if (__any_sync(0xffffffffu, far)) {  // neighbours past the window end: from global memory
+#pragma unroll
+            for (int q = 0; q < BATCH; ++q)
+                if (nr[q] >= 0) v[q] = __ldg(reinterpret_cast<const uint4*>(x + (size_t)nr[q] * cin + col0) + lane % CH);
         }
 #pragma unroll
-        for (int q = 0; q < BATCH; ++q) *reinterpret_cast<uint4*>(a_stage + dst[q]) = v[q];
+        for (int q = 0; q < BATCH; ++q) {
+            const int r = (lane + 32 * (q0 + q)) / CH, c = lane % CH;
+            *reinterpret_cast<uint4*>(a_stage + r * RB + ((c ^ (((r * RB) >> 7) & (CH - 1))) << 4)) = v[q];
+        }
     }
 }
 
@@ -214,7 +221,9 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int S = p.stages;
-    const uint32_t a_bytes = (uint32_t)kBM * p.RB, b_bytes = (uint32_t)p.BN * p.RB;
+    // one stage holds G k-blocks: G A tiles of 128 rows and G B tiles of BN rows
+    const uint32_t a_sub = (uint32_t)kBM * p.RB, b_sub = (uint32_t)p.BN * p.RB;
+    const uint32_t a_bytes = p.G * a_sub, b_bytes = p.G * b_sub;
     const uint32_t win1 = p.gmode == 3 ? (uint32_t)p.win_rows * p.RB : 0u;  // bytes of one window
     uint8_t* sA = smem;
     uint8_t* sB = smem + (size_t)S * a_bytes;
@@ -224,7 +233,6 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
     uint64_t* bars = reinterpret_cast<uint64_t*>(s_bias + 4 * 256);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * S + 8);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    int* part_lo = const_cast<int*>(abort_flag) + 1;  // window gather: [PW][3] per-warp window starts
     const uint32_t full0 = smem_u32(bars), bfull0 = smem_u32(bars + S), empty0 = smem_u32(bars + 2 * S);
     const uint32_t tfull0 = smem_u32(bars + 3 * S), tempty0 = smem_u32(bars + 3 * S + 2);
     const uint32_t mdone = smem_u32(bars + 3 * S + 4);
@@ -369,9 +377,9 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
         // t's plane (a neighbour past the window end is read from global memory), so no row is
         // fetched from global memory once per tap. Gather warps meet at an mbarrier (bounded waits).
         const int tid = threadIdx.x;
-        const int RPW = kBM / PW;  // neighbour-map rows scanned by each warp
         const uint32_t rdv = mdone + 8, wfull = mdone + 16, mfull = mdone + 24;
         const int NB = min(PW, S);  // warps that build stages
+        const int TPS = 27 / p.G;   // stages per channel block (G taps of one (dz, dy) row per stage)
         uint32_t rdv_ph = 0, wf_ph = 0, mf_ph = 0, it = 0;
         int s_it = 0, own_it = 0;   // stage (it % S) and builder warp (it % NB) of iteration it
         uint32_t ph_it = 0;         // phase parity of iteration it on its stage ((it / S) & 1)
@@ -388,8 +396,10 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
             const int mt = tile / p.n_tiles, nt = tile - mt * p.n_tiles;
             const int m0 = mt * kBM;
             const int kb0 = kc * kbc, kb1 = min(p.KB, kb0 + kbc);
-            fence_proxy_async();
-            if (rendezvous()) break;  // the previous unit's map, bounds and windows are no longer read
+            if (u != (int)blockIdx.x) {
+                fence_proxy_async();
+                if (rendezvous()) break;  // the previous unit's map, bounds and windows are no longer read
+            }
             if (tid == 0) {
                 // the tile's neighbour-map rows (contiguous) in one bulk copy; the copy size must be a
                 // multiple of 16 bytes (4 rows), the last < 4 rows of the map come by plain loads
@@ -403,14 +413,18 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
             mbar_wait(mfull, mf_ph & 1, abort_flag);
             ++mf_ph;
             const int rvalid = n_rows - m0;  // rows of the tile that exist (map rows past it are stale)
+            // every warp finds the window starts (smallest neighbour row per dz plane) of the whole tile
             int mn0 = INT_MAX, mn1 = INT_MAX, mn2 = INT_MAX;
-            for (int e = lane; e < RPW * 27; e += 32) {
-                const int r = warp * RPW + e / 27, t = e % 27;
-                const int v = r < rvalid ? map_s[r * 27 + t] : -1;
-                const int vv = v >= 0 ? v : INT_MAX;
-                if (t < 9) mn0 = min(mn0, vv);
-                else if (t < 18) mn1 = min(mn1, vv);
-                else mn2 = min(mn2, vv);
+            for (int r = lane; r < min(rvalid, kBM); r += 32) {
+                const int* mr = map_s + r * 27;
+#pragma unroll
+                for (int t = 0; t < 27; ++t) {
+                    const int v = mr[t];
+                    const int vv = v >= 0 ? v : INT_MAX;
+                    if (t < 9) mn0 = min(mn0, vv);
+                    else if (t < 18) mn1 = min(mn1, vv);
+                    else mn2 = min(mn2, vv);
+                }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -418,18 +432,7 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
                 mn1 = min(mn1, __shfl_xor_sync(0xffffffffu, mn1, o));
                 mn2 = min(mn2, __shfl_xor_sync(0xffffffffu, mn2, o));
             }
-            if (lane == 0) {
-                part_lo[warp * 3 + 0] = mn0;
-                part_lo[warp * 3 + 1] = mn1;
-                part_lo[warp * 3 + 2] = mn2;
-            }
-            if (rendezvous()) break;  // the per-warp minima are complete
-            int lo[3] = {INT_MAX, INT_MAX, INT_MAX};
-            for (int w2 = 0; w2 < PW; ++w2) {
-                lo[0] = min(lo[0], part_lo[w2 * 3 + 0]);
-                lo[1] = min(lo[1], part_lo[w2 * 3 + 1]);
-                lo[2] = min(lo[2], part_lo[w2 * 3 + 2]);
-            }
+            const int lo[3] = {mn0, mn1, mn2};
             int cur = -1;
             for (int kb = kb0; kb < kb1; ++kb, ++it) {
                 const int s = s_it, own = own_it;
@@ -439,7 +442,7 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
                     ph_it ^= 1u;
                 }
                 if (++own_it == NB) own_it = 0;
-                const int cb = kb / 27, t = kb - cb * 27;
+                const int cb = kb / TPS, t = (kb - cb * TPS) * p.G;  // first tap of the stage
                 if (cb != cur) {
                     if (cur >= 0) {
                         fence_proxy_async();
@@ -450,7 +453,8 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
                     }
                     if (tid == 0) {
                         // planes whose taps this unit runs in channel block cb (a k-split unit may hold a few taps)
-                        const int t_lo = max(kb0, cb * 27) - cb * 27, t_hi = min(kb1, cb * 27 + 27) - 1 - cb * 27;
+                        const int t_lo = (max(kb0, cb * TPS) - cb * TPS) * p.G;
+                        const int t_hi = (min(kb1, cb * TPS + TPS) - cb * TPS) * p.G - 1;
                         bool need[3];
                         uint32_t bytes = 0;
                         for (int j = 0; j < 3; ++j) {
@@ -479,20 +483,28 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
                     stop = true;
                     break;
                 }
-                if (lane == 0) {  // the weight block lands on the stage's own barrier
+                if (lane == 0) {  // the stage's weight blocks land on its own barrier
                     asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(full0 + 8 * s),
                                  "r"(b_bytes)
                                  : "memory");
-                    const __nv_bfloat16* wsrc = p.w + ((size_t)(t * p.ncb + cb) * p.Npad + (size_t)nt * p.BN) * p.BKE;
-                    bulk_g2s(smem_u32(sB + (size_t)s * b_bytes), wsrc, b_bytes, full0 + 8 * s);
+                    for (int g = 0; g < p.G; ++g) {
+                        const __nv_bfloat16* wsrc =
+                            p.w + ((size_t)((t + g) * p.ncb + cb) * p.Npad + (size_t)nt * p.BN) * p.BKE;
+                        bulk_g2s(smem_u32(sB + (size_t)s * b_bytes + g * b_sub), wsrc, b_sub, full0 + 8 * s);
+                    }
                 }
+                // the stage's taps share dz (and dy): one window
                 const int j = t / 9, loj = j == 0 ? lo[0] : (j == 1 ? lo[1] : lo[2]);
                 const uint8_t* wj = win + j * win1;
                 uint8_t* a_stage = sA + (size_t)s * a_bytes;
-                if (p.RB == 128)
-                    window_build_a<8>(a_stage, wj, map_s, t, loj, p.win_rows, rvalid, p.x, p.cin, cb * p.BKE, lane);
-                else
-                    window_build_a<4>(a_stage, wj, map_s, t, loj, p.win_rows, rvalid, p.x, p.cin, cb * p.BKE, lane);
+                for (int g = 0; g < p.G; ++g) {
+                    if (p.RB == 128)
+                        window_build_a<8>(a_stage + g * a_sub, wj, map_s, t + g, loj, p.win_rows, rvalid, p.x, p.cin,
+                                          cb * p.BKE, lane);
+                    else
+                        window_build_a<4>(a_stage + g * a_sub, wj, map_s, t + g, loj, p.win_rows, rvalid, p.x, p.cin,
+                                          cb * p.BKE, lane);
+                }
                 fence_proxy_async();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(full0 + 8 * s);
@@ -678,7 +690,7 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
         if (lane == 0) {
             // -------------------------------------------------------------- MMA issuer
             const uint32_t idesc = make_idesc(kBM, p.BN);
-            const int kk_steps = p.BKE / 16;
+            const int kk_steps = p.BKE / 16;  // MMAs (K = 16) per k-block
             uint32_t tc = 0;
             int s = 0;          // stage of the next k-block
             uint32_t ph = 0;    // its phase parity
@@ -700,9 +712,10 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
                     }
                     tc_fence_after();
                     const uint32_t a0 = smem_u32(sA + (size_t)s * a_bytes), b0 = smem_u32(sB + (size_t)s * b_bytes);
-                    for (int k = 0; k < kk_steps; ++k)
-                        tc_mma(acc, make_sdesc(a0 + 32 * k, p.RB), make_sdesc(b0 + 32 * k, p.RB), idesc,
-                               (kb > kb0 || k > 0) ? 1u : 0u);
+                    for (int g = 0; g < p.G; ++g)
+                        for (int k = 0; k < kk_steps; ++k)
+                            tc_mma(acc, make_sdesc(a0 + g * a_sub + 32 * k, p.RB), make_sdesc(b0 + g * b_sub + 32 * k, p.RB),
+                                   idesc, (kb > kb0 || g > 0 || k > 0) ? 1u : 0u);
                     tc_commit(empty0 + 8 * s);
                     if (++s == S) {
                         s = 0;
@@ -838,10 +851,10 @@ __global__ void pack_weights_kernel(int kind, int cin, int cout, TcShape sh, con
 constexpr int kMaxStages = 12;
 constexpr size_t kMaxSmem = 227 * 1024;
 
-// win: bytes of the three windows of the window gather (0 otherwise).
-size_t tc_smem_bytes(int BN, int RB, int taps, int S, size_t win = 0) {
-    return 1024 + (size_t)S * (kBM + BN) * RB + win + (size_t)kBM * taps * 4 + 16 + 4 * 256 * 4 + (3 * S + 8) * 8 +
-           16 + 8 * 3 * 4;
+// win: bytes of the three windows of the window gather (0 otherwise); G: k-blocks per stage.
+size_t tc_smem_bytes(int BN, int RB, int taps, int S, size_t win = 0, int G = 1) {
+    return 1024 + (size_t)S * G * (kBM + BN) * RB + win + (size_t)kBM * taps * 4 + 16 + 4 * 256 * 4 +
+           (3 * S + 8) * 8 + 16 + 8 * 3 * 4;
 }
 
 int tc_stages(int BN, int RB, int taps) {
@@ -850,13 +863,13 @@ int tc_stages(int BN, int RB, int taps) {
     return 4;
 }
 
-// Window gather: the longest window (256 or 128 rows) that leaves room for at least three stages
-// (two with 128-row windows); 0 when not even that fits.
-int win_rows_for(int BN, int RB, int* stages) {
-    for (int wr = 256; wr >= 128; wr -= 128) {
+// Window gather with G taps per stage: the longest window (256, 192 or 128 rows) that leaves room
+// for at least three stages (two with shorter windows); 0 when not even that fits.
+int win_rows_for(int BN, int RB, int G, int* stages) {
+    for (int wr = 256; wr >= 128; wr -= 64) {
         const size_t win = 3 * (size_t)wr * RB;
         for (int S = kMaxStages; S >= (wr == 256 ? 3 : 2); --S)
-            if (tc_smem_bytes(BN, RB, 27, S, win) <= kMaxSmem) {
+            if (tc_smem_bytes(BN, RB, 27, S, win, G) <= kMaxSmem) {
                 *stages = S;
                 return wr;
             }
@@ -934,10 +947,17 @@ npvs_status run_gemm(TcParams& p, const TcShape& sh, const npvs_conv_desc& d, co
     p.BKE = sh.BKE;
     p.RB = sh.RB;
     size_t win = 0;
+    p.G = 1;
     if (p.gmode == 3) {
-        p.win_rows = win_rows_for(sh.BN, sh.RB, &p.stages);
+        p.G = d.tune_gather == 4 ? 3 : 1;
+        p.win_rows = win_rows_for(sh.BN, sh.RB, p.G, &p.stages);
+        if (p.win_rows == 0 && p.G > 1) {  // three taps per stage do not fit: one
+            p.G = 1;
+            p.win_rows = win_rows_for(sh.BN, sh.RB, p.G, &p.stages);
+        }
         NPVS_REQUIRE(p.win_rows > 0, NPVS_ERR_UNSUPPORTED, "BF16 conv: window gather does not fit this shape");
         p.ncb = d.cin / sh.BKE;
+        p.KB = 27 / p.G * p.ncb;  // pipeline stages of one tile
         win = 3 * (size_t)p.win_rows * sh.RB;
     } else {
         p.stages = tc_stages(sh.BN, sh.RB, p.taps);
@@ -948,7 +968,7 @@ npvs_status run_gemm(TcParams& p, const TcShape& sh, const npvs_conv_desc& d, co
     p.acc_cols = 32;
     while ((int)p.acc_cols < sh.BN) p.acc_cols <<= 1;
     if (p.cap_rows <= 0) return NPVS_OK;
-    const size_t smem = tc_smem_bytes(sh.BN, sh.RB, p.taps, p.stages, win);
+    const size_t smem = tc_smem_bytes(sh.BN, sh.RB, p.taps, p.stages, win, p.G);
     alignas(64) CUtensorMap tm;
     std::memset(&tm, 0, sizeof(tm));
     if (p.gmode != 0) {
@@ -971,7 +991,7 @@ npvs_status run_gemm(TcParams& p, const TcShape& sh, const npvs_conv_desc& d, co
         }
     }
     const long long tiles_cap = (long long)ceil_div(p.cap_rows, kBM) * sh.n_tiles;
-    const int grid = (int)std::min<long long>(tiles_cap * (p.part ? sh.KB : 1), kNumSMs);
+    const int grid = (int)std::min<long long>(tiles_cap * (p.part ? p.KB : 1), kNumSMs);
     return d.tune_gather_warps == 4 ? launch_tc_lag<4>(lag, p, tm, grid, smem, st)
                                     : launch_tc_lag<8>(lag, p, tm, grid, smem, st);
 }
@@ -1101,7 +1121,7 @@ npvs_status conv_tc_fwd(const npvs_conv_desc& d, const void* x, const void* w, c
     p.counters = counters;
     if (!sh.tma) p.gmode = 0;
     else if (p.taps == 0) p.gmode = 2;      // rows of x read in order: dense tiles
-    else if (d.tune_gather == 3 && d.kind == NPVS_CONV_SUBM3) p.gmode = 3;
+    else if ((d.tune_gather == 3 || d.tune_gather == 4) && d.kind == NPVS_CONV_SUBM3) p.gmode = 3;
     else p.gmode = (d.tune_gather == 2 && sh.BKE == 64) ? 0 : 1;
     return run_gemm(p, sh, d, x, lag, st);
 }

@@ -245,7 +245,8 @@ class FramePipeline:
         "subm3": [dict(tune_form=2), dict(tune_form=1, tune_gather_warps=8),
                   dict(tune_form=1, tune_gather_warps=8, tune_max_split=1), dict(tune_form=1, tune_gather_warps=4),
                   dict(tune_form=1, tune_gather=3), dict(tune_form=1, tune_gather=3, tune_max_split=1),
-                  dict(tune_form=1, tune_gather=3, tune_gather_warps=4)],
+                  dict(tune_form=1, tune_gather=3, tune_gather_warps=4), dict(tune_form=1, tune_gather=4),
+                  dict(tune_form=1, tune_gather=4, tune_max_split=1)],
         "down2": [dict(tune_form=2), dict(tune_form=1, tune_gather_warps=8),
                   dict(tune_form=1, tune_gather_warps=8, tune_max_split=1)],
         "up2": [dict(tune_form=2), dict(tune_form=1)],

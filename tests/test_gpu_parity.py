@@ -279,11 +279,12 @@ CONV_CASES = [
 ]
 
 
-WINDOW_MODES = ("window", "window-split", "window-s2")
+WINDOW_MODES = ("window", "window-split", "window-s2", "window3", "window3-split")
 
 
 @pytest.mark.parametrize("dt,mode", [("f32", None), ("bf16", "gather"), ("bf16", "gather-split"),
-                                     ("bf16", "product"), ("bf16", "window"), ("bf16", "window-split")])
+                                     ("bf16", "product"), ("bf16", "window"), ("bf16", "window-split"),
+                                     ("bf16", "window3")])
 @pytest.mark.parametrize("kind,cin,cout", CONV_CASES)
 def test_single_conv_parity(kind, cin, cout, dt, mode):
     if dt == "bf16" and kind == "up2" and cout % 16:
@@ -324,7 +325,7 @@ def test_window_gather_window_overflow(cin, cout, mode):
     assert normwise(got, ref) <= 8e-3
     got_g, _, _ = single_conv("subm3", cin, cout, "bf16", "gather", occ, np.random.default_rng(cin * 7 + cout),
                               want_ref=False)
-    if cin <= 64 and mode != "window-split":
+    if cin <= 64 and not mode.endswith("-split"):
         np.testing.assert_array_equal(got, got_g)
     else:   # another summation order of the FP32 accumulators: BF16 outputs may differ by an ulp
         assert normwise(got, got_g) <= 2.0 ** -7
@@ -382,9 +383,10 @@ def single_conv(kind, cin, cout, dt, mode, occ, rng, want_ref=True):
     desc = ops.conv_desc(kid, dtype, cin, cout, True, mp, lv_out.n_rows, lv_out.capacity, out_f32=out_f32,
                          map2=lvs[0].down if kind == "up2" else None, n_in=lv_in.n_rows, cap_in=lv_in.capacity,
                          status=status, form={"gather": 1, "gather-split": 1, "product": 2}.get(mode, 0),
-                         gather=3 if mode in WINDOW_MODES else 0, max_split=1 if mode in ("window", "window-s2") else 0,
+                         gather=(4 if mode.startswith("window3") else 3) if mode in WINDOW_MODES else 0,
+                         max_split=1 if mode in ("window", "window-s2", "window3") else 0,
                          stages=2 if mode == "window-s2" else 0)
-    if mode in ("gather-split", "product", "window-split"):
+    if mode in ("gather-split", "product", "window-split", "window3-split"):
         ws = ops.conv_workspace(ops.npvs_conv_workspace_bytes(desc), DEV)
         desc.workspace, desc.workspace_bytes = ws.data_ptr(), ws.numel()
     w_dev = torch.from_numpy(w).to(DEV).contiguous()
