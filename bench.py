@@ -570,6 +570,28 @@ def run_ours(args):
     h2d = boxes_h.numel() * 4 + cams_h[0].numel()
     d2h = pvs_h.numel() * 4
 
+    # ---- pruning (Sec. 3.2 / Sec. 5.6): every box of the scene tested against the frame's PVS
+    g16.replay()
+    torch.cuda.synchronize()
+    vis = torch.empty(nb, dtype=torch.uint8, device=dev)
+    g_pr = torch.cuda.CUDAGraph()
+    ops.npvs_prune(boxes_d, off_d, cam_buf, fp.grid, wl.supersample, nf.pvs, vis)   # workspace sized, untimed
+    with torch.cuda.graph(g_pr):
+        ops.npvs_prune(boxes_d, off_d, cam_buf, fp.grid, wl.supersample, nf.pvs, vis)
+    pr_ev = []
+    for i in range(3 + 20):
+        s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s_.record(st)
+        g_pr.replay()
+        e_.record(st)
+        if i >= 3:
+            pr_ev.append((s_, e_))
+    torch.cuda.synchronize()
+    ms_prune = statistics.median(s_.elapsed_time(e_) for s_, e_ in pr_ev)
+    prune = {"boxes": nb, "kept": int(vis.sum().item()), "ms": round(ms_prune, 4),
+             "boxes_per_s": round(nb * 1000.0 / ms_prune, 1),
+             "what": "npvs_prune of every scene box against the frame's PVS (one CUDA graph replay)"}
+
     # ---- roofline of the dominant kernel: the sparse-convolution kernels (conv_tc + reduce) take
     # most of the frame, so their algorithmic work over all layers is set against their summed time
     alg = layer_algorithmic(fp, wl)
@@ -615,6 +637,7 @@ def run_ours(args):
     }
     if clk:
         line["clocks"] = clk
+    line["prune"] = prune
     if not args.no_batched:
         line["batched"] = run_batched(args, dev, net, fp.descs)
     if not args.no_highres:

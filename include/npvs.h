@@ -204,6 +204,21 @@ npvs_status npvs_froxelize(const float* boxes, const int32_t* box_offsets, int32
                            const npvs_camera* cams, npvs_grid grid, int32_t supersample,
                            uint32_t* occ_bits, void* workspace, size_t workspace_bytes, void* stream);
 
+/* Pruning (Sec. 3.2: the PVS culls occlusion at once, since a fragment that falls in a froxel the
+ * PVS leaves empty can be discarded; Sec. 5.6: the temporal bounding volume of a dynamic object is
+ * froxelized and the object is dropped when none of its froxels is visible). visible[i] = 1 iff
+ * box i, froxelized alone by the rule of npvs_froxelize (same rays, same binary32 rounding), sets
+ * at least one froxel whose bit is set in pvs_bits of the box's batch element; else 0. The boxes
+ * may be the scene's primitives or bounding volumes of moving objects.
+ *  boxes, box_offsets, cams, grid, supersample: as npvs_froxelize; pvs_bits: device
+ *  [B][D][H][W/32] (for example npvs_deinterleave's output); visible: device uint8 [n_boxes],
+ *  written here (boxes outside [box_offsets[0], box_offsets[B]) get 0). Workspace:
+ *  npvs_froxelize_workspace_bytes(n_boxes). Errors: as npvs_froxelize, NULL pvs_bits / visible. */
+npvs_status npvs_prune(const float* boxes, const int32_t* box_offsets, int32_t n_boxes,
+                       const npvs_camera* cams, npvs_grid grid, int32_t supersample,
+                       const uint32_t* pvs_bits, uint8_t* visible, void* workspace,
+                       size_t workspace_bytes, void* stream);
+
 /* ---- a3: interleave / a7: de-interleave ------------------------------------------------------ */
 
 size_t npvs_interleave_workspace_bytes(npvs_grid grid, int32_t d);

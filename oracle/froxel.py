@@ -88,6 +88,19 @@ def froxel_columns(cam, boxes, W, H, D, s, cols: np.ndarray, precision: int = 32
     return out
 
 
+def prune(cam, boxes: np.ndarray, W: int, H: int, D: int, s: int, pvs_bits: np.ndarray,
+          precision: int = 32) -> np.ndarray:
+    """Pruning by the PVS. Sec. 3.2: a fragment that falls in a froxel the PVS leaves empty can be
+    discarded; Sec. 5.6: a moving object's temporal bounding volume is froxelized and the object is
+    dropped when none of its froxels is visible. Definition written out: box i is kept (1) iff the
+    froxelization of box i alone shares a froxel with pvs_bits [D][H][W/32]; else 0."""
+    out = np.zeros(len(boxes), dtype=np.uint8)
+    for i in range(len(boxes)):
+        gi = froxelize(cam, boxes[i:i + 1], W, H, D, s, precision)
+        out[i] = 1 if np.any(gi & pvs_bits) else 0
+    return out
+
+
 def slice_of(cam, t: float) -> int:
     z = np.ascontiguousarray(cam.slices, dtype=np.float32)
     return _load().oracle_slice_of(_ptr(z), len(z) - 1, float(np.float32(t)))

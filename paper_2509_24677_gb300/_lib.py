@@ -92,6 +92,7 @@ SIGNATURES = {
     "npvs_camera_setup": (I32, [ctypes.POINTER(Viewcell), I32, ctypes.POINTER(Camera)]),
     "npvs_froxelize_workspace_bytes": (SZ, [I32]),
     "npvs_froxelize": (I32, [P, P, I32, P, Grid, I32, P, P, SZ, P]),
+    "npvs_prune": (I32, [P, P, I32, P, Grid, I32, P, P, P, SZ, P]),
     "npvs_interleave_workspace_bytes": (SZ, [Grid, I32]),
     "npvs_interleave": (I32, [P, Grid, I32, I32, I32, I32, P, P, P, P, P, P, SZ, P]),
     "npvs_interleave_noalloc": (I32, [P, Grid, I32, I32, I32, I32, P, P, P, P, P, P]),

@@ -1,4 +1,6 @@
-// a2: froxelization of a box scene into the geometry grid G (Sec. 3.2, froxelization paragraph).
+// a2: froxelization of a box scene into the geometry grid G (Sec. 3.2, froxelization paragraph),
+// and pruning: the test of every box's froxels against a PVS (Sec. 3.2 occlusion culling, Sec. 5.6
+// temporal bounding volumes of dynamic objects).
 //
 // Work decomposition: every box face gets a conservative bounding rectangle of froxel columns
 // (the face clipped against half the near distance and projected); a prefix sum over the
@@ -156,11 +158,15 @@ __global__ void __launch_bounds__(256) raster_centres_kernel(int sW, int sH, flo
 // Items (face, froxel column) are numbered face by face; a warp's 32 consecutive items belong to
 // one face or a few neighbouring ones, so lane 0 finds the face of the warp's first item by binary
 // search and every lane walks forward from it.
-template <int SS>
+// TEST = false: a hit sets its froxel's bit in `bits`. TEST = true (pruning): a hit whose froxel
+// is set in `test_bits` marks the face's box (face index / 6) in `visible` and ends the item; items
+// of boxes already marked are skipped. The rays and their rounding are the same in both modes.
+template <int SS, bool TEST>
 __global__ void __launch_bounds__(256) froxel_items_kernel(
     const FaceRec* __restrict__ faces, const long long* __restrict__ offs, int n_faces,
     const long long* __restrict__ total_p, const npvs_camera* __restrict__ cams, npvs_grid g, int s_rt,
-    const float* __restrict__ centres, uint32_t* __restrict__ bits) {
+    const float* __restrict__ centres, uint32_t* __restrict__ bits, const uint32_t* __restrict__ test_bits,
+    uint8_t* visible) {
     pdl_begin();
     constexpr int CAP = SS ? SS : 16;
     const int s = SS ? SS : s_rt;
@@ -184,6 +190,7 @@ __global__ void __launch_bounds__(256) froxel_items_kernel(
         int lo = __shfl_sync(0xffffffffu, f0, 0);
         if (item >= total) continue;
         while (lo + 1 < n_faces && offs[lo + 1] <= item) ++lo;
+        if (TEST && *(volatile const uint8_t*)(visible + lo / 6)) continue;  // box already kept
         const FaceRec fr = faces[lo];
         int local = (int)(item - offs[lo]);
         int x = fr.x0 + local % fr.nx, y = fr.y0 + local / fr.nx;
@@ -213,7 +220,8 @@ __global__ void __launch_bounds__(256) froxel_items_kernel(
         }
         int last_k = -1;
         float zlo = 0.f, zhi = -1.f;  // slice interval of last_k
-        for (int bb = y * s; bb < y * s + s; ++bb) {
+        bool kept = false;            // TEST: the item found a froxel of the PVS
+        for (int bb = y * s; bb < y * s + s && !kept; ++bb) {
             const float ny = ys[bb];
             const float sy = __fmul_rn(ny, tanh_);
             const float su_ax = __fmul_rn(sy, u_ax), su_1 = __fmul_rn(sy, u1), su_2 = __fmul_rn(sy, u2);
@@ -230,7 +238,15 @@ __global__ void __launch_bounds__(256) froxel_items_kernel(
                 if (!(h2 >= fr.lo2 && h2 <= fr.hi2)) continue;
                 if (!(t >= zlo && t < zhi)) {
                     const int k = slice_of(z, g.D, t);
-                    atomicOr(bits + word_base + (size_t)k * g.H * WW, bit);
+                    if constexpr (TEST) {
+                        if (__ldg(test_bits + word_base + (size_t)k * g.H * WW) & bit) {
+                            visible[lo / 6] = 1;
+                            kept = true;
+                            break;
+                        }
+                    } else {
+                        atomicOr(bits + word_base + (size_t)k * g.H * WW, bit);
+                    }
                     last_k = k;
                     zlo = z[k];
                     zhi = z[k + 1];
@@ -256,21 +272,26 @@ static size_t froxel_ws(int n_boxes) {
 
 extern "C" size_t npvs_froxelize_workspace_bytes(int32_t n_boxes) { return froxel_ws(n_boxes); }
 
-extern "C" npvs_status npvs_froxelize(const float* boxes, const int32_t* box_offsets, int32_t n_boxes,
-                                      const npvs_camera* cams, npvs_grid g, int32_t s, uint32_t* occ_bits,
-                                      void* workspace, size_t workspace_bytes, void* stream) {
-    NPVS_REQUIRE(box_offsets && cams && occ_bits, NPVS_ERR_INVALID_ARG, "npvs_froxelize: NULL pointer");
-    NPVS_REQUIRE(n_boxes >= 0 && (n_boxes == 0 || boxes), NPVS_ERR_INVALID_ARG, "npvs_froxelize: bad boxes");
-    NPVS_REQUIRE(g.W > 0 && g.H > 0 && g.D > 0 && g.B > 0 && g.W % 32 == 0, NPVS_ERR_UNSUPPORTED,
-                 "npvs_froxelize: need W % 32 == 0 and positive sizes");
-    NPVS_REQUIRE(g.D <= NPVS_MAX_SLICES, NPVS_ERR_UNSUPPORTED, "npvs_froxelize: D > NPVS_MAX_SLICES");
-    NPVS_REQUIRE(s >= 1 && s <= 16 && (long long)s * g.W <= 65536 && (long long)s * g.H <= 65536,
-                 NPVS_ERR_UNSUPPORTED, "npvs_froxelize: supersampling must be 1..16 and s*W, s*H <= 65536");
-    NPVS_REQUIRE(workspace_bytes >= froxel_ws(n_boxes) && workspace, NPVS_ERR_WORKSPACE,
-                 "npvs_froxelize: workspace too small");
-    cudaStream_t st = as_stream(stream);
-    size_t nbytes = (size_t)g.B * g.D * g.H * (g.W / 32) * sizeof(uint32_t);
-    if (cudaMemsetAsync(occ_bits, 0, nbytes, st) != cudaSuccess) return check_launch("npvs_froxelize memset");
+// The face set-up, the scan of the per-face column counts and the item kernel; TEST: pruning.
+static npvs_status froxel_run(const float* boxes, const int32_t* box_offsets, int32_t n_boxes, const npvs_camera* cams,
+                              npvs_grid g, int32_t s, uint32_t* bits, const uint32_t* test_bits, uint8_t* visible,
+                              void* workspace, size_t workspace_bytes, cudaStream_t st, const char* who) {
+#define NPVS_CHECK_F(cond, code, what)        \
+    do {                                      \
+        if (!(cond)) {                        \
+            set_error("%s: %s", who, (what)); \
+            return (code);                    \
+        }                                     \
+    } while (0)
+    NPVS_CHECK_F(box_offsets && cams, NPVS_ERR_INVALID_ARG, "NULL pointer");
+    NPVS_CHECK_F(n_boxes >= 0 && (n_boxes == 0 || boxes), NPVS_ERR_INVALID_ARG, "bad boxes");
+    NPVS_CHECK_F(g.W > 0 && g.H > 0 && g.D > 0 && g.B > 0 && g.W % 32 == 0, NPVS_ERR_UNSUPPORTED,
+                 "need W % 32 == 0 and positive sizes");
+    NPVS_CHECK_F(g.D <= NPVS_MAX_SLICES, NPVS_ERR_UNSUPPORTED, "D > NPVS_MAX_SLICES");
+    NPVS_CHECK_F(s >= 1 && s <= 16 && (long long)s * g.W <= 65536 && (long long)s * g.H <= 65536, NPVS_ERR_UNSUPPORTED,
+                 "supersampling must be 1..16 and s*W, s*H <= 65536");
+    NPVS_CHECK_F(workspace_bytes >= froxel_ws(n_boxes) && workspace, NPVS_ERR_WORKSPACE, "workspace too small");
+#undef NPVS_CHECK_F
     if (n_boxes == 0) return NPVS_OK;
     const int F = n_boxes * 6;
     const int nchunk = ceil_div(F, kScanChunk);
@@ -291,12 +312,50 @@ extern "C" npvs_status npvs_froxelize(const float* boxes, const int32_t* box_off
     NPVS_TRY(scan_block_counts(csum, coff, nchunk, csum + nchunk, -1, nullptr, st));
     launch_k(chunk_add_kernel, nchunk, kScanChunk, 0, st, offs, F, coff, counts, total);
     NPVS_TRY(check_launch("chunk_add_kernel"));
-    switch (s) {
-        case 1: launch_k(froxel_items_kernel<1>, kNumSMs * 8, 256, 0, st, faces, offs, F, total, cams, g, s, centres, occ_bits); break;
-        case 2: launch_k(froxel_items_kernel<2>, kNumSMs * 8, 256, 0, st, faces, offs, F, total, cams, g, s, centres, occ_bits); break;
-        case 4: launch_k(froxel_items_kernel<4>, kNumSMs * 8, 256, 0, st, faces, offs, F, total, cams, g, s, centres, occ_bits); break;
-        case 8: launch_k(froxel_items_kernel<8>, kNumSMs * 8, 256, 0, st, faces, offs, F, total, cams, g, s, centres, occ_bits); break;
-        default: launch_k(froxel_items_kernel<0>, kNumSMs * 8, 256, 0, st, faces, offs, F, total, cams, g, s, centres, occ_bits);
+    const int grid = kNumSMs * 8;
+#define NPVS_ITEMS(SSV, T)                                                                                           \
+    launch_k(froxel_items_kernel<SSV, T>, grid, 256, 0, st, faces, offs, F, total, cams, g, s, centres, bits, test_bits, \
+             visible)
+    if (test_bits) {
+        switch (s) {
+            case 4: NPVS_ITEMS(4, true); break;
+            case 8: NPVS_ITEMS(8, true); break;
+            default: NPVS_ITEMS(0, true);
+        }
+    } else {
+        switch (s) {
+            case 1: NPVS_ITEMS(1, false); break;
+            case 2: NPVS_ITEMS(2, false); break;
+            case 4: NPVS_ITEMS(4, false); break;
+            case 8: NPVS_ITEMS(8, false); break;
+            default: NPVS_ITEMS(0, false);
+        }
     }
+#undef NPVS_ITEMS
     return check_launch("froxel_items_kernel");
+}
+
+extern "C" npvs_status npvs_froxelize(const float* boxes, const int32_t* box_offsets, int32_t n_boxes,
+                                      const npvs_camera* cams, npvs_grid g, int32_t s, uint32_t* occ_bits,
+                                      void* workspace, size_t workspace_bytes, void* stream) {
+    NPVS_REQUIRE(occ_bits, NPVS_ERR_INVALID_ARG, "npvs_froxelize: NULL pointer");
+    NPVS_REQUIRE(g.W > 0 && g.H > 0 && g.D > 0 && g.B > 0 && g.W % 32 == 0, NPVS_ERR_UNSUPPORTED,
+                 "npvs_froxelize: need W % 32 == 0 and positive sizes");
+    cudaStream_t st = as_stream(stream);
+    const size_t nbytes = (size_t)g.B * g.D * g.H * (g.W / 32) * sizeof(uint32_t);
+    if (cudaMemsetAsync(occ_bits, 0, nbytes, st) != cudaSuccess) return check_launch("npvs_froxelize memset");
+    return froxel_run(boxes, box_offsets, n_boxes, cams, g, s, occ_bits, nullptr, nullptr, workspace, workspace_bytes,
+                      st, "npvs_froxelize");
+}
+
+extern "C" npvs_status npvs_prune(const float* boxes, const int32_t* box_offsets, int32_t n_boxes,
+                                  const npvs_camera* cams, npvs_grid g, int32_t s, const uint32_t* pvs_bits,
+                                  uint8_t* visible, void* workspace, size_t workspace_bytes, void* stream) {
+    NPVS_REQUIRE(pvs_bits && (n_boxes == 0 || visible), NPVS_ERR_INVALID_ARG, "npvs_prune: NULL pointer");
+    NPVS_REQUIRE(n_boxes >= 0, NPVS_ERR_INVALID_ARG, "npvs_prune: bad boxes");
+    cudaStream_t st = as_stream(stream);
+    if (n_boxes > 0 && cudaMemsetAsync(visible, 0, (size_t)n_boxes, st) != cudaSuccess)
+        return check_launch("npvs_prune memset");
+    return froxel_run(boxes, box_offsets, n_boxes, cams, g, s, nullptr, pvs_bits, visible, workspace, workspace_bytes,
+                      st, "npvs_prune");
 }

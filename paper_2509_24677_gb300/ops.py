@@ -124,6 +124,20 @@ def npvs_froxelize(boxes, box_offsets, cams_dev, g: L.Grid, supersample: int, oc
                                 _p(w), w.numel(), _s(stream)), "npvs_froxelize")
 
 
+def npvs_prune(boxes, box_offsets, cams_dev, g: L.Grid, supersample: int, pvs_bits, visible,
+               ws: Optional[Workspace] = None, stream=None):
+    """visible[i] (uint8) = box i's own froxels meet the PVS of its batch element."""
+    _need_cuda(boxes, box_offsets, cams_dev, pvs_bits, visible)
+    _want(torch.uint8, visible=visible)
+    n = boxes.shape[0]
+    if visible.numel() < n:
+        raise ValueError("npvs_prune: visible needs one byte per box")
+    nb = _lib().npvs_froxelize_workspace_bytes(n)
+    w = _ws(ws, nb)
+    check(_lib().npvs_prune(_p(boxes), _p(box_offsets), n, _p(cams_dev), g, supersample, _p(pvs_bits),
+                            _p(visible), _p(w), w.numel(), _s(stream)), "npvs_prune")
+
+
 # ---- a3 / a7 ----------------------------------------------------------------------------------
 
 def npvs_interleave(occ_bits, g: L.Grid, d: int, in_ch: int, feat_dtype: int, capacity: int, coords, feats,
