@@ -298,6 +298,19 @@ class FramePipeline:
         torch.cuda.synchronize()
         return chosen
 
+    TUNE_FIELDS = ("tune_stages", "tune_max_split", "tune_lag", "tune_gather", "tune_gather_warps", "tune_form")
+
+    def tuned_configs(self) -> dict:
+        """The per-layer kernel configurations in use: {layer name: {field: value}}."""
+        return {l.name: {f: int(getattr(self.descs[i], f)) for f in self.TUNE_FIELDS}
+                for i, l in enumerate(self.net.layers)}
+
+    def apply_tuned(self, cfgs: dict):
+        """Sets per-layer kernel configurations saved by tuned_configs() (instead of autotune)."""
+        for i, l in enumerate(self.net.layers):
+            for f, v in cfgs[l.name].items():
+                setattr(self.descs[i], f, int(v))
+
     def deinterleave(self, want_probs=True):
         lv0 = self.levels[0]
         with self._t("deinterleave"):
