@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-train", action="store_true", help="skip the training-step measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-viewcell batched measurement")
     ap.add_argument("--no-highres", action="store_true", help="skip the 512x512x192 measurement")
+    ap.add_argument("--no-paper256", action="store_true", help="skip the 256^3, d=16 measurement")
     ap.add_argument("--train-points", type=int, default=256, help="ground-truth viewpoints per viewcell")
     ap.add_argument("--save-tuned", default=None,
                     help="write the autotuned per-layer kernel configurations of the headline frame (JSON)")
@@ -412,11 +413,30 @@ def run_highres(args, dev, tf_bf16, hbm_gbs):
     BF16, batch 4: four street viewcells of the 10,000-building city (heights lognormal(2.3, 0.7)).
     Per layer: achieved GB/s of the algorithmic bytes and TFLOP/s of the algorithmic FLOPs, from
     stage events captured in a graph of the same frame."""
-    from paper_2509_24677_gb300 import _lib as L
-    from paper_2509_24677_gb300 import ops, pipeline as P
-    wl = I.workload("city512")
     boxes = I.city_boxes(0, I.CITY_LARGE)
     vcs = I.city_viewcells(0, 4, I.CITY_LARGE)
+    return run_grid_workload(args, dev, tf_bf16, hbm_gbs, I.workload("city512"), boxes, vcs,
+                             "city512: 512x512x192 froxels (s=4), d=8 (1024 ch), U-Net 64/128/256/512, "
+                             "10,000-building city seed 0, 4 viewcells")
+
+
+def run_paper256(args, dev, tf_bf16, hbm_gbs):
+    """The paper's grid and interleave factor: 256x256x256 froxels (s = 8), d = 16 (one occupancy
+    channel, 4096 input channels per coarse site), stem submanifold conv 4096 -> 192 ("~200"),
+    U-Net 192/256, head to 4096 logits; BF16, batch 1 (one viewcell of the 2,000-building city), as
+    the paper's per-frame inference. Per layer: achieved GB/s and TFLOP/s of the algorithmic work."""
+    boxes = I.city_boxes(0)
+    vcs = I.city_viewcells(0, 1)
+    return run_grid_workload(args, dev, tf_bf16, hbm_gbs, I.workload("paper256"), boxes, vcs,
+                             "paper256: 256x256x256 froxels (s=8), d=16 (4096 ch), U-Net 192/256, "
+                             "2,001-box city seed 0, 1 viewcell")
+
+
+def run_grid_workload(args, dev, tf_bf16, hbm_gbs, wl, boxes, vcs, label):
+    """Batch of len(vcs) viewcells of one scene through the BF16 frame (autotuned, one graph of
+    npvs_forward), then stage and per-layer times from a stage-timed graph of the same frame."""
+    from paper_2509_24677_gb300 import _lib as L
+    from paper_2509_24677_gb300 import ops, pipeline as P
     B = len(vcs)
     bx = torch.from_numpy(np.concatenate([boxes] * B)).to(dev)
     of = torch.arange(B + 1, dtype=torch.int32, device=dev) * len(boxes)
@@ -427,7 +447,7 @@ def run_highres(args, dev, tf_bf16, hbm_gbs):
     fp.run(bx, of, cams)
     stt = ops.npvs_check_status(fp.status)
     if stt != 0:
-        raise RuntimeError(f"device status {stt:#x} set in the 512-grid frame")
+        raise RuntimeError(f"device status {stt:#x} set in the {wl.name} frame")
     fp.autotune(bx, of, cams, reps=3)
     nf = P.NativeFrame(wl, net, B, L.BF16, max_boxes=len(boxes) * B, device=dev, tuned=fp.descs)
     g = nf.capture(bx, of, len(boxes) * B, cams)
@@ -461,8 +481,7 @@ def run_highres(args, dev, tf_bf16, hbm_gbs):
                                 "TFLOP/s": round(v["flops"] / t / 1e12, 2),
                                 "tensor_frac": round(v["flops"] / t / 1e12 / tf_bf16, 4)}
     occ = float(np.unpackbits(fp.occ.cpu().numpy().view(np.uint8)).mean())
-    return {"workload": "city512: 512x512x192 froxels (s=4), d=8 (1024 ch), U-Net 64/128/256/512, "
-                        "10,000-building city seed 0, 4 viewcells", "batch": B, "ms_per_batch": round(ms, 3),
+    return {"workload": label, "batch": B, "ms_per_batch": round(ms, 3),
             "frames_per_s": round(B * 1000.0 / ms, 2), "occupancy": round(occ, 4),
             "active_sites": [int(lv.n_rows.item()) for lv in fp.levels],
             "stage_ms": {k: round(v, 4) for k, v in sorted(acc.items(), key=lambda kv: -kv[1]) if not k.startswith("conv:")},
@@ -668,6 +687,8 @@ def run_ours(args):
         line["batched"] = run_batched(args, dev, net, fp.descs)
     if not args.no_highres:
         line["highres"] = run_highres(args, dev, tf_bf16, hbm_gbs)
+    if not args.no_paper256:
+        line["paper256"] = run_paper256(args, dev, tf_bf16, hbm_gbs)
     if not args.no_train:
         del g16, g32, g16t
         line["train"] = run_train(args, dev, flush)

@@ -261,6 +261,10 @@ def workload(name: str) -> Workload:
         return Workload(name, 256, 256, 128, 4, 2, 8, tuple(unet_layers(128, [32, 64, 128, 256], 64)))
     if name == "city512":      # 512x512x192 froxels, d=8, occupancy + depth, U-Net 64/128/256/512
         return Workload(name, 512, 512, 192, 8, 2, 4, tuple(unet_layers(1024, [64, 128, 256, 512], 512)))
+    if name == "paper256":     # the paper's grid: 256^3 froxels, d=16 (4096 ch), stem to ~200 ch, 2 levels
+        return Workload(name, 256, 256, 256, 16, 1, 8, tuple(unet_layers(4096, [192, 256], 4096)))
+    if name == "paper64":      # the same network at d=16 on a 64^3 grid (4^3 coarse sites)
+        return Workload(name, 64, 64, 64, 16, 1, 8, tuple(unet_layers(4096, [192, 256], 4096)))
     raise KeyError(name)
 
 

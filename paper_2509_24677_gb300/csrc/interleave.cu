@@ -24,6 +24,9 @@ struct ILParams {
     long long n_sites;
 };
 
+// DD: the interleave factor as a compile-time constant (0: runtime p.d). The d row words of one
+// depth slice are loaded together and OR-ed; the test stops after the first occupied slice.
+template <int DD>
 __device__ __forceinline__ bool site_active(const ILParams& p, long long site, int& b, int& Z, int& Y,
                                             int& X) {
     X = (int)(site % p.Xc);
@@ -32,20 +35,24 @@ __device__ __forceinline__ bool site_active(const ILParams& p, long long site, i
     t /= p.Yc;
     Z = (int)(t % p.Zc);
     b = (int)(t / p.Zc);
-    const int d = p.d, WW = p.g.W >> 5, x0 = d * X;
+    const int d = DD ? DD : p.d, WW = p.g.W >> 5, x0 = d * X;
     const uint32_t mask = d == 32 ? 0xffffffffu : (((1u << d) - 1u) << (x0 & 31));
     const uint32_t* w = p.bits + (((size_t)b * p.g.D + (size_t)d * Z) * p.g.H + (size_t)d * Y) * WW + (x0 >> 5);
-    for (int dz = 0; dz < d; ++dz)
-        for (int dy = 0; dy < d; ++dy)
-            if (w[((size_t)dz * p.g.H + dy) * WW] & mask) return true;
+    for (int dz = 0; dz < d; ++dz) {
+        uint32_t acc = 0;
+#pragma unroll 16
+        for (int dy = 0; dy < (DD ? DD : d); ++dy) acc |= __ldg(w + ((size_t)dz * p.g.H + dy) * WW);
+        if (acc & mask) return true;
+    }
     return false;
 }
 
+template <int DD>
 __global__ void __launch_bounds__(kSitesPerCta) il_count_kernel(ILParams p, int* __restrict__ counts) {
     pdl_begin();
     long long site = (long long)blockIdx.x * kSitesPerCta + threadIdx.x;
     int b, Z, Y, X;
-    int f = site < p.n_sites ? (int)site_active(p, site, b, Z, Y, X) : 0;
+    int f = site < p.n_sites ? (int)site_active<DD>(p, site, b, Z, Y, X) : 0;
     int c = __syncthreads_count(f);
     if (threadIdx.x == 0) counts[blockIdx.x] = c;
 }
@@ -84,7 +91,7 @@ __global__ void __launch_bounds__(kSitesPerCta) il_write_kernel(ILParams p, cons
     long long site = (long long)blockIdx.x * kSitesPerCta + threadIdx.x;
     int b = 0, Z = 0, Y = 0, X = 0;
     bool in = site < p.n_sites;
-    int f = in ? (int)site_active(p, site, b, Z, Y, X) : 0;
+    int f = in ? (int)site_active<DD>(p, site, b, Z, Y, X) : 0;
     int nloc;
     int loc = block_exclusive_scan(f, sw, &nloc);
     int rank = block_off[blockIdx.x] + loc;
@@ -194,7 +201,18 @@ static void launch_il_write(const ILParams& p, int nb, const int* offs, int32_t*
         case 2: launch_k(il_write_kernel<2>, nb, kSitesPerCta, 0, st, p, offs, coords, feats, table, status); break;
         case 4: launch_k(il_write_kernel<4>, nb, kSitesPerCta, 0, st, p, offs, coords, feats, table, status); break;
         case 8: launch_k(il_write_kernel<8>, nb, kSitesPerCta, 0, st, p, offs, coords, feats, table, status); break;
+        case 16: launch_k(il_write_kernel<16>, nb, kSitesPerCta, 0, st, p, offs, coords, feats, table, status); break;
         default: launch_k(il_write_kernel<0>, nb, kSitesPerCta, 0, st, p, offs, coords, feats, table, status);
+    }
+}
+
+static void launch_il_count(const ILParams& p, int nb, int* counts, cudaStream_t st) {
+    switch (p.d) {
+        case 2: launch_k(il_count_kernel<2>, nb, kSitesPerCta, 0, st, p, counts); break;
+        case 4: launch_k(il_count_kernel<4>, nb, kSitesPerCta, 0, st, p, counts); break;
+        case 8: launch_k(il_count_kernel<8>, nb, kSitesPerCta, 0, st, p, counts); break;
+        case 16: launch_k(il_count_kernel<16>, nb, kSitesPerCta, 0, st, p, counts); break;
+        default: launch_k(il_count_kernel<0>, nb, kSitesPerCta, 0, st, p, counts);
     }
 }
 
@@ -236,7 +254,7 @@ extern "C" npvs_status npvs_interleave(const uint32_t* occ_bits, npvs_grid g, in
     Arena ar(workspace, workspace_bytes);
     int* counts = ar.take<int>(nb + 1);
     int* offs = ar.take<int>(nb + 1);
-    launch_k(il_count_kernel, nb, kSitesPerCta, 0, st, p, counts);
+    launch_il_count(p, nb, counts, st);
     NPVS_TRY(check_launch("il_count_kernel"));
     NPVS_TRY(scan_block_counts(counts, offs, nb, n_active, capacity, status, st));
     launch_il_write(p, nb, offs, coords, feats, table, status, st);
@@ -341,7 +359,7 @@ extern "C" npvs_status npvs_interleave_noalloc(const uint32_t* occ_bits, npvs_gr
     const int nb = ceil_div(p.n_sites, kSitesPerCta);
     int* counts = scratch;                      // fully rewritten by every call before it is read
     int* offs = scratch + kNoAllocMaxCtas + 1;  // likewise
-    launch_k(il_count_kernel, nb, kSitesPerCta, 0, st, p, counts);
+    launch_il_count(p, nb, counts, st);
     NPVS_TRY(check_launch("il_count_kernel"));
     NPVS_TRY(scan_block_counts(counts, offs, nb, n_active, capacity, status, st));
     launch_il_write(p, nb, offs, coords, feats, table, status, st);

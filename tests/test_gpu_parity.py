@@ -125,7 +125,8 @@ def clustered_bits(rng, B, D, H, W, frac=0.04):
     return occ
 
 
-@pytest.mark.parametrize("d,in_ch,dt", [(2, 1, "f32"), (4, 2, "bf16"), (4, 2, "f32"), (8, 2, "bf16"), (2, 2, "bf16")])
+@pytest.mark.parametrize("d,in_ch,dt", [(2, 1, "f32"), (4, 2, "bf16"), (4, 2, "f32"), (8, 2, "bf16"), (2, 2, "bf16"),
+                                        (16, 1, "bf16"), (16, 2, "f32")])
 def test_interleave_bit_exact(d, in_ch, dt):
     L, ops, _ = lib()
     rng = np.random.default_rng(d * 10 + in_ch)
@@ -434,7 +435,8 @@ def gpu_frame(wl, boxes, vc, ws, bs, dtype, tune=False):
 
 
 @pytest.mark.parametrize("name,dt", [("plain64", "f32"), ("plain64", "bf16"), ("city256", "bf16"), ("city256", "f32"),
-                                     ("city256", "bf16-tuned")])
+                                     ("city256", "bf16-tuned"), ("paper64", "bf16"), ("paper64", "f32"),
+                                     ("paper64", "bf16-tuned")])
 def test_frame_parity(name, dt):
     L, ops, P = lib()
     wl = I.workload(name)
