@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(256) raster_centres_kernel(int sW, int sH, flo
 // is set in `test_bits` marks the face's box (face index / 6) in `visible` and ends the item; items
 // of boxes already marked are skipped. The rays and their rounding are the same in both modes.
 template <int SS, bool TEST>
-__global__ void __launch_bounds__(256) froxel_items_kernel(
+__global__ void __launch_bounds__(256, 4) froxel_items_kernel(
     const FaceRec* __restrict__ faces, const long long* __restrict__ offs, int n_faces,
     const long long* __restrict__ total_p, const npvs_camera* __restrict__ cams, npvs_grid g, int s_rt,
     const float* __restrict__ centres, uint32_t* __restrict__ bits, const uint32_t* __restrict__ test_bits,
