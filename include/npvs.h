@@ -335,7 +335,11 @@ size_t npvs_forward_workspace_bytes(const npvs_net_desc* net);
  * (sigmoid, tau, AND G). Inputs as npvs_froxelize (boxes, box_offsets [B+1], cams [B], all
  * device); outputs occ_bits (G) and pvs_bits [B][D][H][W/32], probs (nullable, [cap0][d^3] FP32 per
  * level-0 row). All buffers (levels, rulebooks, activations, scratch) are carved from workspace in a
- * fixed layout; nothing is allocated; the sequence can be captured in a CUDA graph. */
+ * fixed layout; nothing is allocated; the sequence can be captured in a CUDA graph. The rulebooks of
+ * the coarser levels are built on a library-owned second stream of the device (created by the first
+ * call that is not inside a stream capture; a capturing first call keeps one stream), forked from
+ * and joined back into `stream` within the call, so they overlap the level-0 layers; the results do
+ * not depend on it. Calls sharing one workspace must not overlap. */
 npvs_status npvs_forward(const npvs_net_desc* net, const float* boxes, const int32_t* box_offsets,
                          int32_t n_boxes, const npvs_camera* cams, uint32_t* occ_bits, uint32_t* pvs_bits,
                          float* probs, int32_t* status, void* workspace, size_t workspace_bytes,

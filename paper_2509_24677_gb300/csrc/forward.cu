@@ -12,6 +12,8 @@
 #include <cstring>
 #include <vector>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace npvs {
@@ -194,6 +196,34 @@ extern "C" size_t npvs_forward_workspace_bytes(const npvs_net_desc* net) {
     return carve(*net, P, nullptr, 0, L, &feats, acts, &cw, &cwb, &sc, &scb);
 }
 
+// One library-owned side stream and two events per device (created on first use, never inside a
+// stream capture: a capturing call that finds none keeps everything on the caller's stream).
+struct SideStream {
+    bool ok = false;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+SideStream side_stream(cudaStream_t st) {
+    static std::mutex mu;
+    static SideStream per_dev[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SideStream();
+    std::lock_guard<std::mutex> lock(mu);
+    SideStream& s = per_dev[dev];
+    if (s.ok) return s;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return SideStream();
+    if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess) return SideStream();
+    if (cudaEventCreateWithFlags(&s.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s.join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return SideStream();
+    }
+    s.ok = true;
+    return s;
+}
+
 extern "C" npvs_status npvs_forward(const npvs_net_desc* net, const float* boxes, const int32_t* box_offsets,
                                     int32_t n_boxes, const npvs_camera* cams, uint32_t* occ_bits, uint32_t* pvs_bits,
                                     float* probs, int32_t* status, void* workspace, size_t workspace_bytes,
@@ -217,16 +247,36 @@ extern "C" npvs_status npvs_forward(const npvs_net_desc* net, const float* boxes
     NPVS_TRY(npvs_froxelize(boxes, box_offsets, n_boxes, cams, n.grid, n.supersample, occ_bits, sc, scb, st));
     NPVS_TRY(npvs_interleave(occ_bits, n.grid, n.d, n.in_ch, n.dtype, L[0].cap, L[0].coords, feats, L[0].n_rows,
                              L[0].table, status, sc, scb, st));
-    for (int li = 0; li < P.n_levels; ++li) {
-        npvs_level lv = {L[li].dims, L[li].cap, L[li].coords, L[li].n_rows, L[li].table};
-        NPVS_TRY(npvs_build_rulebook(NPVS_RB_SUBM3_TABLE, &lv, nullptr, L[li].nbr, nullptr, status, sc, scb, st));
-        if (li + 1 < P.n_levels) {
-            npvs_level nx = {L[li + 1].dims, L[li + 1].cap, L[li + 1].coords, L[li + 1].n_rows, L[li + 1].table};
-            NPVS_TRY(npvs_build_rulebook(NPVS_RB_DOWN2, &lv, &nx, L[li].down, L[li].up, status, sc, scb, st));
-        }
+    {
+        npvs_level lv = {L[0].dims, L[0].cap, L[0].coords, L[0].n_rows, L[0].table};
+        NPVS_TRY(npvs_build_rulebook(NPVS_RB_SUBM3_TABLE, &lv, nullptr, L[0].nbr, nullptr, status, sc, scb, st));
     }
+    // The rulebooks of the coarser levels depend only on the level-0 sites: they are built on a
+    // second stream while the level-0 convolutions run (those use the convolution workspace, the
+    // rulebooks the scratch region), and the caller's stream waits for them before the first layer
+    // that reads a coarser level.
+    SideStream side = side_stream(st);
+    cudaStream_t rs = side.ok ? side.stream : st;
+    if (side.ok && P.n_levels > 1) {
+        if (cudaEventRecord(side.fork, st) != cudaSuccess || cudaStreamWaitEvent(rs, side.fork, 0) != cudaSuccess)
+            return check_launch("npvs_forward: fork");
+    }
+    for (int li = 0; li + 1 < P.n_levels; ++li) {
+        npvs_level lv = {L[li].dims, L[li].cap, L[li].coords, L[li].n_rows, L[li].table};
+        npvs_level nx = {L[li + 1].dims, L[li + 1].cap, L[li + 1].coords, L[li + 1].n_rows, L[li + 1].table};
+        NPVS_TRY(npvs_build_rulebook(NPVS_RB_DOWN2, &lv, &nx, L[li].down, L[li].up, status, sc, scb, rs));
+        NPVS_TRY(npvs_build_rulebook(NPVS_RB_SUBM3_TABLE, &nx, nullptr, L[li + 1].nbr, nullptr, status, sc, scb, rs));
+    }
+    bool joined = !(side.ok && P.n_levels > 1);
+    if (!joined && cudaEventRecord(side.join, rs) != cudaSuccess) return check_launch("npvs_forward: join");
     const void* a = feats;
     for (int i = 0; i < n.n_layers; ++i) {
+        const bool level0_only =
+            P.level_of[i] == 0 && (n.layers[i].kind == NPVS_CONV_SUBM3 || n.layers[i].kind == NPVS_CONV_HEAD1);
+        if (!joined && !level0_only) {  // the first layer that reads a coarser level's rulebooks
+            if (cudaStreamWaitEvent(st, side.join, 0) != cudaSuccess) return check_launch("npvs_forward: join");
+            joined = true;
+        }
         npvs_conv_desc d = layer_desc(n, P, L, i, status);
         d.workspace = cw;
         d.workspace_bytes = cwb;
@@ -234,6 +284,7 @@ extern "C" npvs_status npvs_forward(const npvs_net_desc* net, const float* boxes
         NPVS_TRY(npvs_sparse_conv_fwd(&d, a, n.layers[i].w, n.layers[i].bias, skip, acts[i], st));
         a = acts[i];
     }
+    if (!joined && cudaStreamWaitEvent(st, side.join, 0) != cudaSuccess) return check_launch("npvs_forward: join");
     return npvs_deinterleave((const float*)acts[n.n_layers - 1], L[0].table, L[0].n_rows, n.grid, n.d, n.tau, occ_bits,
                              pvs_bits, probs, L[0].cap, st);
 }
