@@ -269,6 +269,7 @@ def run_train(args, dev, flush):
     ws, bs = I.kaiming_uniform(wl.layers, seed=0)
     tr = T.Trainer(wl, wl.layers, ws, bs, len(pairs), L.BF16, loss_prm=ops.loss_params(w_bce=1.0), device=dev)
     tr.gt.copy_(batch.gt)
+    tuned = tr.autotune(batch.boxes, batch.box_offsets, batch.cams)   # forward layers (untimed)
     l0 = ops.npvs_launch_count()
     g = tr.capture(batch.boxes, batch.box_offsets, batch.cams)
     launches = (ops.npvs_launch_count() - l0) // 2
@@ -295,7 +296,8 @@ def run_train(args, dev, flush):
             "master": "fp32", "optimizer": "adam lr 1e-3", "loss": "dice(alpha 0.9)+rvl(lambda 0.99)+bce(w 1)",
             "loss_first_last": [round(losses[0], 5), round(losses[-1], 5)], "gpu_launches_per_step": int(launches),
             "active_sites_level0": n_act, "gt_points": args.train_points, "gt_seconds": round(t_gt, 2),
-            "gt_bits": gt_bits, "graph": "one CUDA graph replay per step; working set > L2"}
+            "gt_bits": gt_bits, "graph": "one CUDA graph replay per step; working set > L2",
+            "forward_autotuned": {k: tuned_label(v[0]) for k, v in tuned.items()}}
 
 
 def batched_scenes():

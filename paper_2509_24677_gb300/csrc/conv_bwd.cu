@@ -290,6 +290,14 @@ BwdPlan plan_bwd(const npvs_conv_desc& d) {
     t.n_in = d.n_out;
     t.cap_in = d.cap_out;
     t.tune_stages = t.tune_max_split = t.tune_lag = t.tune_gather = t.tune_gather_warps = t.tune_form = 0;
+    if (d.kind == NPVS_CONV_SUBM3 && d.cin == d.cout && (d.tune_gather == 3 || d.tune_gather == 4)) {
+        // the transposed submanifold conv has the forward's shape and neighbour map: keep its window gather
+        t.tune_form = 1;
+        t.tune_gather = d.tune_gather;
+        t.tune_max_split = d.tune_max_split;
+        t.tune_gather_warps = d.tune_gather_warps;
+        t.tune_stages = d.tune_stages;
+    }
     t.workspace = nullptr;
     t.workspace_bytes = 0;
     p.mode = 1;

@@ -114,6 +114,11 @@ class Trainer:
                                                dtype=torch.uint8, device=device))
             self.repack()
 
+    def autotune(self, boxes, box_offsets, cams_dev, reps: int = 3):
+        """Per-layer kernel configurations of the forward convolutions, timed on this batch (see
+        FramePipeline.autotune); the backward keeps its defaults. Returns {layer: (config, us)}."""
+        return self.pipe.autotune(boxes, box_offsets, cams_dev, reps=reps)
+
     # ---- parts of a step ----------------------------------------------------------------------
     def repack(self):
         """BF16 tensor-core images of the current master weights."""

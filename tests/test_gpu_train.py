@@ -31,6 +31,18 @@ BWD_CASES = [("subm3", 8, 16), ("subm3", 16, 16), ("subm3", 32, 32), ("subm3", 6
 @pytest.mark.parametrize("dt", ["f32", "bf16", "f64"])
 @pytest.mark.parametrize("kind,cin,cout", BWD_CASES)
 def test_conv_bwd_parity(kind, cin, cout, dt):
+    run_bwd_case(kind, cin, cout, dt)
+
+
+@pytest.mark.parametrize("cin", [32, 64, 256])
+@pytest.mark.parametrize("gather,max_split", [(3, 1), (4, 1), (4, 0)])
+def test_conv_bwd_window_dgrad(cin, gather, max_split):
+    """A submanifold layer tuned to the window gather (cin = cout) runs its dgrad in the same form:
+    the same tolerances against the oracle's autograd as the default forms."""
+    run_bwd_case("subm3", cin, cin, "bf16", form=1, gather=gather, max_split=max_split)
+
+
+def run_bwd_case(kind, cin, cout, dt, **tune):
     L, ops, P = lib()
     rng = np.random.default_rng(sum(map(ord, kind)) * 7919 + cin * 31 + cout)
     occ = rng.random((2, 10, 12, 14)) < 0.12
@@ -78,7 +90,7 @@ def test_conv_bwd_parity(kind, cin, cout, dt):
     mp2 = {"down2": lvs[0].up, "up2": lvs[0].down}.get(kind)
     status = torch.zeros(1, dtype=torch.int32, device=DEV)
     desc = ops.conv_desc(P.KIND[kind], dtype, cin, cout, relu, mp, lv_out.n_rows, lv_out.capacity, map2=mp2,
-                         n_in=lv_in.n_rows, cap_in=lv_in.capacity, status=status)
+                         n_in=lv_in.n_rows, cap_in=lv_in.capacity, status=status, **tune)
     ws = ops.conv_workspace(ops.npvs_conv_bwd_workspace_bytes(desc), DEV)
     w_dev = torch.from_numpy(w).to(DEV).to(mdt).contiguous()
     results = []
