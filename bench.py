@@ -358,6 +358,20 @@ def run_batched(args, dev, net, tuned):
     frac = 0.6
     fpb = P.FramePipeline(wl, net, B, L.BF16, device=dev, capacity_frac=frac)
     tuned_b = fpb.autotune(bx, of, cams, reps=3)
+    # stage split of the batch: a stage-timed graph of the same frame, entry point by entry point
+    timer = P.StageTimer()
+    gst = fpb.capture(bx, of, cams, timer=timer)
+    acc = {}
+    for i in range(4):
+        gst.replay()
+        torch.cuda.synchronize()
+        if i >= 1:
+            for k, v in timer.totals().items():
+                acc[k] = acc.get(k, 0.0) + v / 3
+    conv_ms = sum(v for k, v in acc.items() if k.startswith("conv:"))
+    stages = {k: round(v, 3) for k, v in acc.items() if not k.startswith("conv:")}
+    stages["convs (22 layers)"] = round(conv_ms, 3)
+    del gst
     nfb = P.NativeFrame(wl, net, B, L.BF16, max_boxes=len(boxes), device=dev, capacity_frac=frac, tuned=fpb.descs)
     del fpb
     g = nfb.capture(bx, of, len(boxes), cams)
@@ -402,6 +416,7 @@ def run_batched(args, dev, net, tuned):
         lat.append(statistics.median(s_.elapsed_time(e_) for s_, e_ in rs))
     occs = [o for _, _, o in picked]
     return {"viewcells": B, "scenes": "4 cities of 2k/6k/12k/24k buildings, seeds 0-3",
+            "stage_ms": dict(sorted(stages.items(), key=lambda kv: -kv[1])),
             "occupancy_range": [round(min(occs), 4), round(max(occs), 4)],
             "batch_ms": round(batch_ms, 4), "frames_per_s": round(B * 1000.0 / batch_ms, 2),
             "per_viewcell_ms": {"p50": round(float(np.percentile(lat, 50)), 4),
