@@ -139,7 +139,8 @@ typedef struct {
     int32_t cap_in;
     int32_t* status; /* nullable device status word (NPVS_ERR_TIMEOUT from bounded waits) */
     void* workspace; /* nullable device scratch of npvs_conv_workspace_bytes(desc) bytes for BF16
-                        convs: split-K partial tiles and counters, and the product-form tiles T.
+                        and FP32 convs: split-K partial tiles and counters, and the product-form
+                        tiles T (FP32 uses the product form when T fits, else the gather kernel).
                         It must be zero-filled before its first use; every call leaves the
                         counters at zero again. Calls sharing one workspace must not overlap on
                         the device. NULL: gather form without split-K. */

@@ -1,11 +1,18 @@
 // a5/a6: sparse convolutions, SIMT FMA path (FP32 and FP64) and the npvs_sparse_conv_fwd entry.
 //
-// Output-stationary gather-GEMM (Sec. 2.3, masked dense definition): a CTA owns a 64-row x
-// 64-column output tile and walks the taps t and input-channel blocks; for each it gathers the
-// 64 input rows x[map(n, t)] (zeros where the neighbour is absent) and the weight block W_t into
-// shared memory and accumulates a 4 x 4 register tile per thread. Taps with no neighbour in the
-// whole tile are skipped. The epilogue adds bias, applies ReLU, adds the skip input and stores
-// each output row exactly once.
+// FP32 (when the descriptor's workspace holds the product tiles): the product form, as on the
+// tensor cores but in FP32 FMA: a dense GEMM T[n][j * cout + o] = sum_c x[n][c] W_j[c][o] over the
+// input rows (128 x 128 tiles, 8 x 8 per thread, double-buffered shared memory, the weights read
+// straight from the [taps][cin][cout] master), then y[m] = b + sum_t T[map(m, t)][t] over existing
+// neighbours in fixed tap order (+ReLU, +skip); a 1 x 1 conv writes y from the GEMM directly.
+// Otherwise (and for FP64): an output-stationary gather-GEMM (Sec. 2.3, masked dense definition):
+// a CTA owns a 64-row x 64-column output tile and walks the taps t and input-channel blocks; for
+// each it gathers the 64 input rows x[map(n, t)] (zeros where the neighbour is absent) and the
+// weight block W_t into shared memory and accumulates a 4 x 4 register tile per thread. Taps with
+// no neighbour in the whole tile are skipped. The epilogue adds bias, applies ReLU, adds the skip
+// input and stores each output row exactly once.
+#include <algorithm>
+
 #include "common.cuh"
 #include "conv_tc.cuh"
 
@@ -86,6 +93,189 @@ __global__ void __launch_bounds__(256) conv_simt_kernel(npvs_conv_desc dsc, cons
     }
 }
 
+// FP32 GEMM C = A B with A = x [rows][K] (row-major, K % 8 == 0), B[k][n] = w[(n / cout) * K + k]
+// [n % cout] (the master weights [J][K][cout], cout % 4 == 0), N = J * cout columns. direct == 0:
+// C is stored to T [rows][N]; direct == 1 (J == 1): y = relu?(C + b) (+ skip) is stored.
+constexpr int GM = 128, GN = 128, GK = 8;
+
+__global__ void __launch_bounds__(256) gemm_f32_kernel(const float* __restrict__ A, const int32_t* __restrict__ n_rows_p,
+                                                       int cap_rows, int K, const float* __restrict__ W, int cout, int N,
+                                                       float* __restrict__ C, int direct, const float* __restrict__ bias,
+                                                       int relu, const float* __restrict__ skip) {
+    pdl_begin();
+    __shared__ __align__(16) float sA[2][GK][GM];
+    __shared__ __align__(16) float sB[2][GK][GN];
+    const int rows = min(*n_rows_p, cap_rows);
+    const int m0 = blockIdx.x * GM, n0 = blockIdx.y * GN;
+    if (m0 >= rows) return;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    // global -> register loads of one k-block: A row tid/2, k (tid%2)*4; B k tid/32, column (tid%32)*4
+    const int a_row = tid >> 1, a_k = (tid & 1) * 4;
+    const int b_k = tid >> 5, b_n = (tid & 31) * 4;
+    const bool a_ok = m0 + a_row < rows;
+    const int bn = n0 + b_n;
+    const bool b_ok = bn < N;
+    const float* a_src = A + (size_t)(m0 + a_row) * K + a_k;
+    const float* b_src = b_ok ? W + ((size_t)(bn / cout) * K) * cout + (bn % cout) : W;
+    float4 ra, rb;
+    auto load = [&](int k0) {
+        ra = a_ok ? __ldg(reinterpret_cast<const float4*>(a_src + k0)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        rb = b_ok ? __ldg(reinterpret_cast<const float4*>(b_src + (size_t)(k0 + b_k) * cout))
+                  : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    auto store = [&](int buf) {
+        sA[buf][a_k + 0][a_row] = ra.x;
+        sA[buf][a_k + 1][a_row] = ra.y;
+        sA[buf][a_k + 2][a_row] = ra.z;
+        sA[buf][a_k + 3][a_row] = ra.w;
+        *reinterpret_cast<float4*>(&sB[buf][b_k][b_n]) = rb;
+    };
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    load(0);
+    store(0);
+    __syncthreads();
+    const int nk = K / GK;
+    for (int kb = 0; kb < nk; ++kb) {
+        const int buf = kb & 1;
+        if (kb + 1 < nk) load((kb + 1) * GK);
+#pragma unroll
+        for (int k = 0; k < GK; ++k) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&sA[buf][k][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&sA[buf][k][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&sB[buf][k][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&sB[buf][k][64 + tx * 4]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        if (kb + 1 < nk) {
+            store(buf ^ 1);
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+        if (m >= rows) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int n = n0 + h * 64 + tx * 4;
+            if (n >= N) continue;
+            float4 v = make_float4(acc[i][4 * h], acc[i][4 * h + 1], acc[i][4 * h + 2], acc[i][4 * h + 3]);
+            if (direct) {
+                const float4 bb = bias ? *reinterpret_cast<const float4*>(bias + n) : make_float4(0.f, 0.f, 0.f, 0.f);
+                v.x += bb.x;
+                v.y += bb.y;
+                v.z += bb.z;
+                v.w += bb.w;
+                if (relu) {
+                    v.x = fmaxf(v.x, 0.f);
+                    v.y = fmaxf(v.y, 0.f);
+                    v.z = fmaxf(v.z, 0.f);
+                    v.w = fmaxf(v.w, 0.f);
+                }
+                if (skip) {
+                    const float4 sk = *reinterpret_cast<const float4*>(skip + (size_t)m * N + n);
+                    v.x += sk.x;
+                    v.y += sk.y;
+                    v.z += sk.z;
+                    v.w += sk.w;
+                }
+            }
+            *reinterpret_cast<float4*>(C + (size_t)m * N + n) = v;
+        }
+    }
+}
+
+// y[m][o] = b[o] + sum_t T[map[m][t]][t * cout + o] over existing neighbours in tap order (taps == 0:
+// the transposed conv, T[u >> 3][(u & 7) * cout + o] with u = map[m]), then ReLU and the skip input.
+// One thread per (row, 4 channels).
+__global__ void __launch_bounds__(256) reduce_f32_kernel(const float* __restrict__ T, int ldT,
+                                                         const int32_t* __restrict__ map, int taps,
+                                                         const int32_t* __restrict__ n_out_p, int cap_out, int cout,
+                                                         const float* __restrict__ bias, int relu,
+                                                         const float* __restrict__ skip, float* __restrict__ y) {
+    pdl_begin();
+    const int n_out = min(*n_out_p, cap_out);
+    const int G = cout >> 2;
+    const long long total = (long long)n_out * G;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int m = (int)(e / G), o = (int)(e - (long long)m * G) * 4;
+        float4 acc = bias ? *reinterpret_cast<const float4*>(bias + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (taps == 0) {
+            const int u = __ldg(map + m);
+            if (u >= 0) {
+                const float4 v = __ldcg(reinterpret_cast<const float4*>(T + (size_t)(u >> 3) * ldT + (u & 7) * cout + o));
+                acc.x += v.x;
+                acc.y += v.y;
+                acc.z += v.z;
+                acc.w += v.w;
+            }
+        } else {
+            const int32_t* mp = map + (size_t)m * taps;
+#pragma unroll 9
+            for (int t = 0; t < taps; ++t) {
+                const int n = __ldg(mp + t);
+                if (n >= 0) {
+                    const float4 v = __ldcg(reinterpret_cast<const float4*>(T + (size_t)n * ldT + t * cout + o));
+                    acc.x += v.x;
+                    acc.y += v.y;
+                    acc.z += v.z;
+                    acc.w += v.w;
+                }
+            }
+        }
+        if (relu) {
+            acc.x = fmaxf(acc.x, 0.f);
+            acc.y = fmaxf(acc.y, 0.f);
+            acc.z = fmaxf(acc.z, 0.f);
+            acc.w = fmaxf(acc.w, 0.f);
+        }
+        const size_t off = (size_t)m * cout + o;
+        if (skip) {
+            const float4 sk = *reinterpret_cast<const float4*>(skip + off);
+            acc.x += sk.x;
+            acc.y += sk.y;
+            acc.z += sk.z;
+            acc.w += sk.w;
+        }
+        *reinterpret_cast<float4*>(y + off) = acc;
+    }
+}
+
+// The FP32 product form of npvs_sparse_conv_fwd; NPVS_ERR_UNSUPPORTED when it does not apply.
+npvs_status conv_f32_product(const npvs_conv_desc& d, const float* x, const float* w, const float* bias,
+                             const float* skip, float* y, cudaStream_t st) {
+    if (d.tune_form == 1 || d.cin % 8 != 0 || d.cout % 4 != 0) return NPVS_ERR_UNSUPPORTED;
+    if (d.kind == NPVS_CONV_HEAD1) {  // one tap: y directly
+        const int rows_cap = d.cap_out;
+        dim3 grid(ceil_div(rows_cap, GM), ceil_div(d.cout, GN));
+        launch_k(gemm_f32_kernel, grid, 256, 0, st, x, d.n_out, rows_cap, d.cin, w, d.cout, d.cout, y, 1, bias,
+                 d.relu, skip);
+        return check_launch("gemm_f32_kernel");
+    }
+    float* T = conv_product_tiles(d);
+    if (T == nullptr || d.n_in == nullptr || d.cap_in <= 0) return NPVS_ERR_UNSUPPORTED;
+    const int J = d.kind == NPVS_CONV_SUBM3 ? 27 : 8;
+    const int N = J * d.cout;
+    dim3 grid(ceil_div(d.cap_in, GM), ceil_div(N, GN));
+    launch_k(gemm_f32_kernel, grid, 256, 0, st, x, d.n_in, d.cap_in, d.cin, w, d.cout, N, T, 0, nullptr, 0, nullptr);
+    NPVS_TRY(check_launch("gemm_f32_kernel"));
+    const int taps = d.kind == NPVS_CONV_SUBM3 ? 27 : (d.kind == NPVS_CONV_DOWN2 ? 8 : 0);
+    const long long work = (long long)d.cap_out * (d.cout / 4);
+    const int rg = (int)std::max<long long>(1, std::min<long long>(ceil_div(work, 256), kNumSMs * 8));
+    launch_k(reduce_f32_kernel, rg, 256, 0, st, T, N, d.map, taps, d.n_out, d.cap_out, d.cout, bias, d.relu, skip, y);
+    return check_launch("reduce_f32_kernel");
+}
+
 }  // namespace
 }  // namespace npvs
 
@@ -102,6 +292,11 @@ extern "C" npvs_status npvs_sparse_conv_fwd(const npvs_conv_desc* dsc, const voi
     cudaStream_t st = as_stream(stream);
     if (dsc->cap_out == 0) return NPVS_OK;
     if (dsc->dtype == NPVS_BF16) return conv_tc_fwd(*dsc, x, w, (const float*)bias, skip, y, st);
+    if (dsc->dtype == NPVS_F32) {
+        const npvs_status s = conv_f32_product(*dsc, (const float*)x, (const float*)w, (const float*)bias,
+                                               (const float*)skip, (float*)y, st);
+        if (s != NPVS_ERR_UNSUPPORTED) return s;
+    }
     dim3 grid(ceil_div(dsc->cap_out, BM), ceil_div(dsc->cout, BN));
     if (dsc->dtype == NPVS_F32) {
         launch_k(conv_simt_kernel<float>, grid, 256, 0, st, *dsc, (const float*)x, (const float*)w, (const float*)bias, (const float*)skip,

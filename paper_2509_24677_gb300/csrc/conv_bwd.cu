@@ -313,7 +313,7 @@ BwdPlan plan_bwd(const npvs_conv_desc& d) {
         p.conv_bytes = npvs_conv_workspace_bytes(&t);
     } else {
         p.wt_bytes = (size_t)p.taps * d.cin * d.cout * p.el;
-        p.conv_bytes = 0;
+        p.conv_bytes = d.dtype == NPVS_F32 ? npvs_conv_workspace_bytes(&t) : 0;  // FP32 product tiles
     }
     return p;
 }
@@ -381,6 +381,10 @@ npvs_status run_dgrad(const npvs_conv_desc& d, BwdPlan& p, const void* w, const 
         launch_k(transpose_taps_kernel<T>, tg, 256, 0, st, (const T*)w, p.taps, d.cin, d.cout, p.mode == 2 ? 1 : 0,
                  (T*)wt);
         NPVS_TRY(check_launch("transpose_taps_kernel"));
+        if (p.conv_bytes) {
+            p.td.workspace = ar.take<char>(p.conv_bytes);
+            p.td.workspace_bytes = p.conv_bytes;
+        }
     }
     return npvs_sparse_conv_fwd(&p.td, gg, wt, nullptr, dx_add, dx, st);
 }

@@ -998,6 +998,15 @@ npvs_status run_gemm(TcParams& p, const TcShape& sh, const npvs_conv_desc& d, co
 
 }  // namespace
 
+float* conv_product_tiles(const npvs_conv_desc& d) {
+    if (d.workspace == nullptr) return nullptr;
+    Arena ar(d.workspace, d.workspace_bytes);  // the layout of conv_tc_fwd: split-K region, then T
+    if (!ar.take<int>(4 * kSplitSlots) || !ar.take<float>((size_t)kSplitSlots * kBM * 256)) return nullptr;
+    const size_t tb = product_region_bytes(d);
+    if (tb == 0 || ar.size - Arena::round(ar.used) < tb) return nullptr;
+    return ar.take<float>(tb / sizeof(float));
+}
+
 TcShape tc_shape(int kind, int cin, int cout, int form) {
     TcShape s;
     s.form = form;

@@ -51,4 +51,8 @@ npvs_status wgrad_tc(const npvs_conv_desc& d, const __nv_bfloat16* x, const __nv
 npvs_status conv_tc_fwd(const npvs_conv_desc& d, const void* x, const void* w, const float* bias,
                         const void* skip, void* y, cudaStream_t st);
 
+// The FP32 product tiles T [rows][J * cout] of a convolution in its workspace (the region
+// npvs_conv_workspace_bytes() reserves), or nullptr when the workspace lacks them.
+float* conv_product_tiles(const npvs_conv_desc& d);
+
 }  // namespace npvs

@@ -164,7 +164,7 @@ size_t carve(const npvs_net_desc& n, FwdPlan& P, void* base, size_t size, std::v
         acts[i] = ar.take<char>((size_t)L[P.level_of[i]].cap * n.layers[i].cout * el);
     }
     size_t cw = 0;
-    if (n.dtype == NPVS_BF16) {
+    if (n.dtype == NPVS_BF16 || n.dtype == NPVS_F32) {
         for (int i = 0; i < n.n_layers; ++i) {
             npvs_conv_desc d = layer_desc(n, P, L, i, nullptr);
             cw = std::max(cw, npvs_conv_workspace_bytes(&d));

@@ -222,7 +222,7 @@ class FramePipeline:
                                   n_in=lv.n_rows, cap_in=lv.capacity, **common)
             self.descs.append(d)
         self.conv_ws = None
-        if self.dtype == L.BF16:
+        if self.dtype in (L.BF16, L.F32):     # tensor-core / FP32 product tiles and split-K partials
             nbytes = max(ops.npvs_conv_workspace_bytes(d) for d in self.descs)
             self.conv_ws = ops.conv_workspace(nbytes, self.device)
             for d in self.descs:

@@ -285,7 +285,7 @@ WINDOW_MODES = ("window", "window-split", "window-s2", "window3", "window3-split
 
 @pytest.mark.parametrize("dt,mode", [("f32", None), ("bf16", "gather"), ("bf16", "gather-split"),
                                      ("bf16", "product"), ("bf16", "window"), ("bf16", "window-split"),
-                                     ("bf16", "window3")])
+                                     ("bf16", "window3"), ("f32", "product"), ("f32", "gather")])
 @pytest.mark.parametrize("kind,cin,cout", CONV_CASES)
 def test_single_conv_parity(kind, cin, cout, dt, mode):
     if dt == "bf16" and kind == "up2" and cout % 16:
