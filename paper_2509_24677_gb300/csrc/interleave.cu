@@ -24,8 +24,9 @@ struct ILParams {
     long long n_sites;
 };
 
-// DD: the interleave factor as a compile-time constant (0: runtime p.d). The d row words of one
-// depth slice are loaded together and OR-ed; the test stops after the first occupied slice.
+// DD: the interleave factor as a compile-time constant (0: runtime p.d). The d row words of SG
+// depth slices (SG = 4 for d >= 16, else 1) are loaded together and OR-ed; the test stops after
+// the first occupied group.
 template <int DD>
 __device__ __forceinline__ bool site_active(const ILParams& p, long long site, int& b, int& Z, int& Y,
                                             int& X) {
@@ -38,10 +39,14 @@ __device__ __forceinline__ bool site_active(const ILParams& p, long long site, i
     const int d = DD ? DD : p.d, WW = p.g.W >> 5, x0 = d * X;
     const uint32_t mask = d == 32 ? 0xffffffffu : (((1u << d) - 1u) << (x0 & 31));
     const uint32_t* w = p.bits + (((size_t)b * p.g.D + (size_t)d * Z) * p.g.H + (size_t)d * Y) * WW + (x0 >> 5);
-    for (int dz = 0; dz < d; ++dz) {
+    constexpr int SG = DD >= 16 ? 4 : 1;
+    for (int dz0 = 0; dz0 < d; dz0 += SG) {
         uint32_t acc = 0;
+#pragma unroll
+        for (int q = 0; q < SG; ++q) {
 #pragma unroll 16
-        for (int dy = 0; dy < (DD ? DD : d); ++dy) acc |= __ldg(w + ((size_t)dz * p.g.H + dy) * WW);
+            for (int dy = 0; dy < (DD ? DD : d); ++dy) acc |= __ldg(w + ((size_t)(dz0 + q) * p.g.H + dy) * WW);
+        }
         if (acc & mask) return true;
     }
     return false;
@@ -80,10 +85,42 @@ __device__ __forceinline__ void store_vals(void* feats, int dtype, size_t off, c
 }
 
 // DD: the interleave factor as a compile-time constant (0: runtime p.d)
+// Writes the d^2 occupancy values (and, with in_ch = 2, the d^2 depth values) of slab dz of the
+// active site st (b, Z, Y, X in .x .. .w) at feature row r.
+template <int DD>
+__device__ __forceinline__ void il_write_slab(const ILParams& p, int4 st, int r, int dz, void* __restrict__ feats) {
+    const int d = DD ? DD : p.d, d2 = d * d, d3 = d2 * d, C = p.in_ch * d3, WW = p.g.W >> 5;
+    const int grp = d2 >= 8 ? 8 : d2;  // values per vector store
+    const int k = d * st.y + dz, x0 = d * st.w;
+    const float dep = __fdiv_rn((float)(2 * k + 1), (float)(2 * p.g.D));
+    const uint32_t* wrow = p.bits + (((size_t)st.x * p.g.D + k) * p.g.H + (size_t)d * st.z) * WW + (x0 >> 5);
+    const size_t base = (size_t)r * C + (size_t)dz * d2;
+    float vo[8], vd[8];
+    int nv = 0, j0 = 0;
+#pragma unroll
+    for (int dy = 0; dy < (DD ? DD : d); ++dy) {
+        const uint32_t wbits = wrow[(size_t)dy * WW] >> (x0 & 31);
+#pragma unroll
+        for (int dx = 0; dx < (DD ? DD : d); ++dx) {
+            const bool occ = (wbits >> dx) & 1u;
+            vo[nv] = occ ? 1.0f : 0.0f;
+            vd[nv] = occ ? dep : 0.0f;
+            if (++nv == grp) {
+                store_vals(feats, p.dtype, base + j0, vo, grp);
+                if (p.in_ch == 2) store_vals(feats, p.dtype, base + d3 + j0, vd, grp);
+                j0 += grp;
+                nv = 0;
+            }
+        }
+    }
+}
+
+// write_feats == 0: coordinates and table only (the features follow in il_feats_kernel).
 template <int DD>
 __global__ void __launch_bounds__(kSitesPerCta) il_write_kernel(ILParams p, const int* __restrict__ block_off,
                                                                 int32_t* __restrict__ coords, void* __restrict__ feats,
-                                                                int32_t* __restrict__ table, int32_t* status) {
+                                                                int32_t* __restrict__ table, int32_t* status,
+                                                                int write_feats) {
     pdl_begin();
     __shared__ int sw[33];
     __shared__ int4 s_site[kSitesPerCta];
@@ -108,35 +145,28 @@ __global__ void __launch_bounds__(kSitesPerCta) il_write_kernel(ILParams p, cons
     __syncthreads();
     // one thread per (active site, dz): the d x d occupancy bits of that slab (d words), written as
     // d^2 occupancy values and, with in_ch = 2, d^2 depth values (one quotient per slab)
-    const int d = DD ? DD : p.d, d2 = d * d, d3 = d2 * d, C = p.in_ch * d3, WW = p.g.W >> 5;
-    const int grp = d2 >= 8 ? 8 : d2;  // values per vector store
+    if (!write_feats) return;
+    const int d = DD ? DD : p.d;
     for (int e = threadIdx.x; e < nloc * d; e += kSitesPerCta) {
         const int i = e / d, dz = e - i * d;
         const int r = s_rank[i];
         if (r >= p.cap) continue;
-        const int4 st = s_site[i];
-        const int k = d * st.y + dz, x0 = d * st.w;
-        const float dep = __fdiv_rn((float)(2 * k + 1), (float)(2 * p.g.D));
-        const uint32_t* wrow = p.bits + (((size_t)st.x * p.g.D + k) * p.g.H + (size_t)d * st.z) * WW + (x0 >> 5);
-        const size_t base = (size_t)r * C + (size_t)dz * d2;
-        float vo[8], vd[8];
-        int nv = 0, j0 = 0;
-#pragma unroll
-        for (int dy = 0; dy < (DD ? DD : d); ++dy) {
-            const uint32_t wbits = wrow[(size_t)dy * WW] >> (x0 & 31);
-#pragma unroll
-            for (int dx = 0; dx < (DD ? DD : d); ++dx) {
-                const bool occ = (wbits >> dx) & 1u;
-                vo[nv] = occ ? 1.0f : 0.0f;
-                vd[nv] = occ ? dep : 0.0f;
-                if (++nv == grp) {
-                    store_vals(feats, p.dtype, base + j0, vo, grp);
-                    if (p.in_ch == 2) store_vals(feats, p.dtype, base + d3 + j0, vd, grp);
-                    j0 += grp;
-                    nv = 0;
-                }
-            }
-        }
+        il_write_slab<DD>(p, s_site[i], r, dz, feats);
+    }
+}
+
+// The features of large interleave factors, spread over the whole device: one item per (feature
+// row, slab dz) of the rows il_write_kernel compacted (n_active, device).
+template <int DD>
+__global__ void __launch_bounds__(256) il_feats_kernel(ILParams p, const int32_t* __restrict__ coords,
+                                                       const int32_t* __restrict__ n_active, void* __restrict__ feats) {
+    pdl_begin();
+    const int d = DD ? DD : p.d;
+    const long long n = (long long)min(*n_active, p.cap) * d;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / d), dz = (int)(e - (long long)r * d);
+        const int4 st = reinterpret_cast<const int4*>(coords)[r];
+        il_write_slab<DD>(p, st, r, dz, feats);
     }
 }
 
@@ -195,15 +225,23 @@ using namespace npvs;
 
 static bool valid_d(int d) { return d == 1 || d == 2 || d == 4 || d == 8 || d == 16 || d == 32; }
 
+// Compaction, coordinates and table; the features in the same kernel for d <= 8, in a separate
+// device-wide kernel for d >= 16 (a site's d slabs of d^2 values are too much work for 256 sites
+// per CTA). n_active: the device row count the compaction writes.
 static void launch_il_write(const ILParams& p, int nb, const int* offs, int32_t* coords, void* feats, int32_t* table,
-                            int32_t* status, cudaStream_t st) {
+                            int32_t* status, const int32_t* n_active, cudaStream_t st) {
+    const int wf = p.d >= 16 ? 0 : 1;
     switch (p.d) {
-        case 2: launch_k(il_write_kernel<2>, nb, kSitesPerCta, 0, st, p, offs, coords, feats, table, status); break;
-        case 4: launch_k(il_write_kernel<4>, nb, kSitesPerCta, 0, st, p, offs, coords, feats, table, status); break;
-        case 8: launch_k(il_write_kernel<8>, nb, kSitesPerCta, 0, st, p, offs, coords, feats, table, status); break;
-        case 16: launch_k(il_write_kernel<16>, nb, kSitesPerCta, 0, st, p, offs, coords, feats, table, status); break;
-        default: launch_k(il_write_kernel<0>, nb, kSitesPerCta, 0, st, p, offs, coords, feats, table, status);
+        case 2: launch_k(il_write_kernel<2>, nb, kSitesPerCta, 0, st, p, offs, coords, feats, table, status, wf); break;
+        case 4: launch_k(il_write_kernel<4>, nb, kSitesPerCta, 0, st, p, offs, coords, feats, table, status, wf); break;
+        case 8: launch_k(il_write_kernel<8>, nb, kSitesPerCta, 0, st, p, offs, coords, feats, table, status, wf); break;
+        case 16: launch_k(il_write_kernel<16>, nb, kSitesPerCta, 0, st, p, offs, coords, feats, table, status, wf); break;
+        default: launch_k(il_write_kernel<0>, nb, kSitesPerCta, 0, st, p, offs, coords, feats, table, status, wf);
     }
+    if (wf) return;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(ceil_div((long long)p.cap * p.d, 256), kNumSMs * 8));
+    if (p.d == 16) launch_k(il_feats_kernel<16>, grid, 256, 0, st, p, coords, n_active, feats);
+    else launch_k(il_feats_kernel<0>, grid, 256, 0, st, p, coords, n_active, feats);
 }
 
 static void launch_il_count(const ILParams& p, int nb, int* counts, cudaStream_t st) {
@@ -257,7 +295,7 @@ extern "C" npvs_status npvs_interleave(const uint32_t* occ_bits, npvs_grid g, in
     launch_il_count(p, nb, counts, st);
     NPVS_TRY(check_launch("il_count_kernel"));
     NPVS_TRY(scan_block_counts(counts, offs, nb, n_active, capacity, status, st));
-    launch_il_write(p, nb, offs, coords, feats, table, status, st);
+    launch_il_write(p, nb, offs, coords, feats, table, status, n_active, st);
     return check_launch("il_write_kernel");
 }
 
@@ -362,6 +400,6 @@ extern "C" npvs_status npvs_interleave_noalloc(const uint32_t* occ_bits, npvs_gr
     launch_il_count(p, nb, counts, st);
     NPVS_TRY(check_launch("il_count_kernel"));
     NPVS_TRY(scan_block_counts(counts, offs, nb, n_active, capacity, status, st));
-    launch_il_write(p, nb, offs, coords, feats, table, status, st);
+    launch_il_write(p, nb, offs, coords, feats, table, status, n_active, st);
     return check_launch("il_write_kernel");
 }
