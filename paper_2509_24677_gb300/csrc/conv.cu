@@ -204,11 +204,10 @@ __global__ void __launch_bounds__(256) reduce_f32_kernel(const float* __restrict
                                                          const float* __restrict__ skip, float* __restrict__ y) {
     pdl_begin();
     const int n_out = min(*n_out_p, cap_out);
-    const int G = cout >> 2;
-    const long long total = (long long)n_out * G;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int m = (int)(e / G), o = (int)(e - (long long)m * G) * 4;
+    const uint32_t G = (uint32_t)cout >> 2;
+    const uint32_t total = (uint32_t)n_out * G;  // < 2^31: checked by the launcher
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int m = (int)(e / G), o = (int)(e - (uint32_t)m * G) * 4;
         float4 acc = bias ? *reinterpret_cast<const float4*>(bias + o) : make_float4(0.f, 0.f, 0.f, 0.f);
         if (taps == 0) {
             const int u = __ldg(map + m);
@@ -264,13 +263,14 @@ npvs_status conv_f32_product(const npvs_conv_desc& d, const float* x, const floa
     }
     float* T = conv_product_tiles(d);
     if (T == nullptr || d.n_in == nullptr || d.cap_in <= 0) return NPVS_ERR_UNSUPPORTED;
+    const long long work = (long long)d.cap_out * (d.cout / 4);
+    if (work >= (1LL << 31)) return NPVS_ERR_UNSUPPORTED;  // the gather kernel handles any size
     const int J = d.kind == NPVS_CONV_SUBM3 ? 27 : 8;
     const int N = J * d.cout;
     dim3 grid(ceil_div(d.cap_in, GM), ceil_div(N, GN));
     launch_k(gemm_f32_kernel, grid, 256, 0, st, x, d.n_in, d.cap_in, d.cin, w, d.cout, N, T, 0, nullptr, 0, nullptr);
     NPVS_TRY(check_launch("gemm_f32_kernel"));
     const int taps = d.kind == NPVS_CONV_SUBM3 ? 27 : (d.kind == NPVS_CONV_DOWN2 ? 8 : 0);
-    const long long work = (long long)d.cap_out * (d.cout / 4);
     const int rg = (int)std::max<long long>(1, std::min<long long>(ceil_div(work, 256), kNumSMs * 8));
     launch_k(reduce_f32_kernel, rg, 256, 0, st, T, N, d.map, taps, d.n_out, d.cap_out, d.cout, bias, d.relu, skip, y);
     return check_launch("reduce_f32_kernel");

@@ -751,11 +751,10 @@ __global__ void __launch_bounds__(256) conv_reduce_kernel(const float* __restric
                                                           const __nv_bfloat16* __restrict__ skip, OutT* __restrict__ y) {
     pdl_begin();
     const int n_out = min(*n_out_p, cap_out);
-    const int G = cout >> 2;
-    const long long total = (long long)n_out * G;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int m = (int)(e / G), o = (int)(e - (long long)m * G) * 4;
+    const uint32_t G = (uint32_t)cout >> 2;
+    const uint32_t total = (uint32_t)n_out * G;  // < 2^31: checked by the launcher
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int m = (int)(e / G), o = (int)(e - (uint32_t)m * G) * 4;
         float4 acc = bias ? *reinterpret_cast<const float4*>(bias + o) : make_float4(0.f, 0.f, 0.f, 0.f);
         if (taps == 0) {
             const int u = __ldg(map + m);
@@ -1107,6 +1106,7 @@ npvs_status conv_tc_fwd(const npvs_conv_desc& d, const void* x, const void* w, c
         NPVS_TRY(run_gemm(p, sh, d, x, lag, st));
         const int taps = d.kind == NPVS_CONV_SUBM3 ? 27 : (up ? 0 : 8);
         const long long work = (long long)d.cap_out * (d.cout / 4);
+        NPVS_REQUIRE(work < (1LL << 31), NPVS_ERR_UNSUPPORTED, "BF16 conv: more than 2^31 output groups");
         const int grid = (int)std::max<long long>(1, std::min<long long>(ceil_div(work, 256), kNumSMs * 8));
         if (d.out_f32)
             launch_k(conv_reduce_kernel<float>, grid, 256, 0, st, T, sh.Ntot, d.map, taps, d.n_out, d.cap_out, d.cout, bias,

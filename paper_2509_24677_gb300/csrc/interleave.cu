@@ -172,32 +172,31 @@ __global__ void __launch_bounds__(256) il_feats_kernel(ILParams p, const int32_t
 
 // ---- de-interleave ------------------------------------------------------------------------
 
+// One thread per PVS word (32 froxels along x); index arithmetic in 32 bits (the host checks that
+// the word count fits) and shifts by log2(d) (d is a power of two).
 __global__ void deinterleave_kernel(const float* __restrict__ logits, const int32_t* __restrict__ table,
-                                    const int32_t* __restrict__ n_active, npvs_grid g, int d, float tau,
+                                    const int32_t* __restrict__ n_active, npvs_grid g, int d, int ld, float tau,
                                     const uint32_t* __restrict__ mask_bits, uint32_t* __restrict__ pvs) {
     pdl_begin();
-    const int WW = g.W >> 5;
-    const long long n_words = (long long)g.B * g.D * g.H * WW;
+    const uint32_t WW = (uint32_t)g.W >> 5, H = (uint32_t)g.H, D = (uint32_t)g.D;
+    const uint32_t n_words = (uint32_t)g.B * D * H * WW;
     const int n = *n_active;
-    const int Xc = g.W / d, Yc = g.H / d, Zc = g.D / d, d3 = d * d * d;
-    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < n_words;
-         w += (long long)gridDim.x * blockDim.x) {
+    const int Xc = g.W >> ld, Yc = g.H >> ld, Zc = g.D >> ld, d3 = d * d * d, dm = d - 1;
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < n_words; w += gridDim.x * blockDim.x) {
         uint32_t m = mask_bits[w];
         uint32_t out = 0;
         if (m) {
-            int xw = (int)(w % WW);
-            long long t = w / WW;
-            int y = (int)(t % g.H);
-            t /= g.H;
-            int k = (int)(t % g.D);
-            int b = (int)(t / g.D);
-            int Y = y / d, dy = y - Y * d, Z = k / d, dz = k - Z * d;
-            long long rowbase = (((long long)b * Zc + Z) * Yc + Y) * Xc;
+            const uint32_t xw = w % WW, t = w / WW;
+            const int y = (int)(t % H);
+            const uint32_t t2 = t / H;
+            const int k = (int)(t2 % D), b = (int)(t2 / D);
+            const int Y = y >> ld, dy = y & dm, Z = k >> ld, dz = k & dm;
+            const long long rowbase = (((long long)b * Zc + Z) * Yc + Y) * Xc;
             while (m) {
-                int i = __ffs(m) - 1;
+                const int i = __ffs(m) - 1;
                 m &= m - 1;
-                int x = xw * 32 + i, X = x / d, dx = x - X * d;
-                int row = table[rowbase + X];
+                const int x = (int)xw * 32 + i, X = x >> ld, dx = x & dm;
+                const int row = table[rowbase + X];
                 if (row >= 0 && row < n) {
                     float z = logits[(size_t)row * d3 + (dz * d + dy) * d + dx];
                     float pr = 1.0f / (1.0f + expf(-z));
@@ -308,8 +307,11 @@ extern "C" npvs_status npvs_deinterleave(const float* logits, const int32_t* tab
                  NPVS_ERR_UNSUPPORTED, "npvs_deinterleave: unsupported grid / d");
     cudaStream_t st = as_stream(stream);
     long long words = (long long)g.B * g.D * g.H * (g.W / 32);
+    NPVS_REQUIRE(words < (1LL << 31), NPVS_ERR_UNSUPPORTED, "npvs_deinterleave: more than 2^31 PVS words");
+    int ld = 0;
+    while ((1 << ld) < d) ++ld;
     int blocks = (int)std::min<long long>(ceil_div(words, 256), kNumSMs * 16);
-    launch_k(deinterleave_kernel, blocks, 256, 0, st, logits, table, n_active, g, d, tau, mask_bits, pvs_bits);
+    launch_k(deinterleave_kernel, blocks, 256, 0, st, logits, table, n_active, g, d, ld, tau, mask_bits, pvs_bits);
     NPVS_TRY(check_launch("deinterleave_kernel"));
     if (probs_out) {
         int d3 = d * d * d;
