@@ -254,7 +254,7 @@ class FramePipeline:
     }
 
     def autotune(self, boxes, box_offsets, cams_dev, reps: int = 10, record: Optional[dict] = None,
-                 margin: float = 0.05):
+                 margin: float = 0.05, refine_window: float = 0.15):
         """Times the candidate configurations of every BF16 layer on this frame (each as a CUDA
         graph of `reps` launches) and keeps the fastest in the layer's descriptor. The best choice
         depends on the active-site counts, so tune on a representative frame. A candidate replaces
@@ -262,6 +262,9 @@ class FramePipeline:
         faster by more than `margin`: timed alone, one layer's launches understate the in-frame
         cost of the one-kernel forms against the two-kernel product form by a few percent (level-1
         layers of the 256x256x128 frame: 24.5 / 23.8 us alone, 30.5 / 27.3 us in the frame).
+        Then every layer whose runner-up (another form) is within `refine_window` of its best is
+        decided in the frame: the frame is captured with the stage timer once with the winners and
+        once with the runners-up, and per layer the form with the shorter in-frame time is kept.
         Returns {layer: (config, microseconds)}; `record`, if given, receives every candidate's
         time as {layer: [(config, microseconds), ...]}."""
         if self.dtype != L.BF16:
@@ -270,6 +273,7 @@ class FramePipeline:
         torch.cuda.synchronize()
         W = self.net.operands(self.dtype)
         chosen = {}
+        times: Dict[int, list] = {}
         x = self.feats
         for i, l in enumerate(self.net.layers):
             y = self.acts[l.name]
@@ -291,17 +295,54 @@ class FramePipeline:
                 e1.record()
                 torch.cuda.synchronize()
                 us = e0.elapsed_time(e1) * 1000.0 / reps
+                times.setdefault(i, []).append((cfg, us))
                 if record is not None:
                     record.setdefault(l.name, []).append((cfg, us))
                 if best is None or us < best[1] * (1.0 - margin):
                     best = (cfg, us)
-            for k, v in best[0].items():
-                setattr(self.descs[i], k, v)
+            self._apply_cfg(i, best[0])
             chosen[l.name] = best
             x = y
+        # close calls are decided in the frame
+        alt = {}
+        for i, l in enumerate(self.net.layers):
+            cfg, us = chosen[l.name]
+            runners = sorted((c for c in times[i] if c[0] != cfg), key=lambda c: c[1])
+            if runners and runners[0][1] <= us * (1.0 + refine_window):
+                alt[i] = runners[0]
+        if alt:
+            t_best = self._frame_layer_times(boxes, box_offsets, cams_dev)
+            for i, (cfg, _) in alt.items():
+                self._apply_cfg(i, cfg)
+            t_alt = self._frame_layer_times(boxes, box_offsets, cams_dev)
+            for i, (cfg, us) in alt.items():
+                name = self.net.layers[i].name
+                if t_alt[name] < t_best[name]:
+                    chosen[name] = (cfg, us)
+                else:
+                    self._apply_cfg(i, chosen[name][0])
         self.run(boxes, box_offsets, cams_dev, want_probs=False)   # outputs with the chosen configs
         torch.cuda.synchronize()
         return chosen
+
+    def _apply_cfg(self, i: int, cfg: dict):
+        for f in self.TUNE_FIELDS:
+            setattr(self.descs[i], f, int(cfg.get(f, 0)))
+
+    def _frame_layer_times(self, boxes, box_offsets, cams_dev, replays: int = 6) -> Dict[str, float]:
+        """Per-layer times (ms) inside a stage-timed graph of this frame with the current configs."""
+        timer = StageTimer()
+        g = self.capture(boxes, box_offsets, cams_dev, want_probs=False, timer=timer)
+        acc: Dict[str, float] = {}
+        for r in range(replays):
+            g.replay()
+            torch.cuda.synchronize()
+            if r >= 1:
+                for k, v in timer.totals().items():
+                    if k.startswith("conv:"):
+                        acc[k[5:]] = acc.get(k[5:], 0.0) + v
+        del g
+        return acc
 
     TUNE_FIELDS = ("tune_stages", "tune_max_split", "tune_lag", "tune_gather", "tune_gather_warps", "tune_form")
 
