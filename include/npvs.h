@@ -340,7 +340,8 @@ size_t npvs_forward_workspace_bytes(const npvs_net_desc* net);
  * the coarser levels are built on a library-owned second stream of the device (created by the first
  * call that is not inside a stream capture; a capturing first call keeps one stream), forked from
  * and joined back into `stream` within the call, so they overlap the level-0 layers; the results do
- * not depend on it. Calls sharing one workspace must not overlap. */
+ * not depend on it (calls from several host threads enqueue their fork and join one at a time).
+ * Calls sharing one workspace must not overlap. */
 npvs_status npvs_forward(const npvs_net_desc* net, const float* boxes, const int32_t* box_offsets,
                          int32_t n_boxes, const npvs_camera* cams, uint32_t* occ_bits, uint32_t* pvs_bits,
                          float* probs, int32_t* status, void* workspace, size_t workspace_bytes,

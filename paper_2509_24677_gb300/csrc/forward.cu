@@ -202,10 +202,12 @@ struct SideStream {
     bool ok = false;
     cudaStream_t stream = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
+    std::mutex* order = nullptr;  // held from the fork record to the join wait of one call
 };
 
 SideStream side_stream(cudaStream_t st) {
     static std::mutex mu;
+    static std::mutex order[64];
     static SideStream per_dev[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SideStream();
@@ -220,6 +222,7 @@ SideStream side_stream(cudaStream_t st) {
         cudaGetLastError();
         return SideStream();
     }
+    s.order = &order[dev];
     s.ok = true;
     return s;
 }
@@ -257,6 +260,9 @@ extern "C" npvs_status npvs_forward(const npvs_net_desc* net, const float* boxes
     // that reads a coarser level.
     SideStream side = side_stream(st);
     cudaStream_t rs = side.ok ? side.stream : st;
+    // calls from several host threads share the device's events: one call's fork ... join at a time
+    std::unique_lock<std::mutex> in_order;
+    if (side.ok) in_order = std::unique_lock<std::mutex>(*side.order);
     if (side.ok && P.n_levels > 1) {
         if (cudaEventRecord(side.fork, st) != cudaSuccess || cudaStreamWaitEvent(rs, side.fork, 0) != cudaSuccess)
             return check_launch("npvs_forward: fork");
