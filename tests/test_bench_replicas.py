@@ -1,0 +1,54 @@
+"""The bench's multi-GPU path is replicas only (viewcells are independent; the path has no exchange
+step): every rank times its own frames and the whole-job rate uses the slowest rank. Checked on the
+CPU with two gloo ranks: the rank environment is parsed, the per-step time is the maximum over the
+ranks on every rank, and the rate is world x units / time."""
+import os
+import socket
+import sys
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    import bench
+    w, r, local = bench.dist_env()
+    dist.init_process_group("gloo", init_method="env://")
+    try:
+        mine = 1.5 + 2.0 * rank                      # rank 1 is the slow one
+        slowest = bench.max_over_ranks(mine, "cpu")
+        out[rank] = (w, r, local, slowest, bench.replica_rate(w, 1, slowest))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_replicas_time_by_slowest_rank():
+    world = 2
+    manager = mp.get_context("spawn").Manager()
+    out = manager.dict()
+    mp.start_processes(_rank_main, args=(world, _free_port(), out), nprocs=world, join=True, start_method="spawn")
+    for rank in range(world):
+        w, r, local, slowest, rate = out[rank]
+        assert (w, r, local) == (world, rank, rank)
+        assert slowest == pytest.approx(3.5)
+        assert rate == pytest.approx(world * 1000.0 / 3.5)
+
+
+def test_single_process_needs_no_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(2.25, "cpu") == 2.25
+    assert bench.replica_rate(1, 8, 4.0) == pytest.approx(2000.0)
