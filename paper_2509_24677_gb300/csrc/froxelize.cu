@@ -136,6 +136,22 @@ __global__ void chunk_add_kernel(long long* __restrict__ offs, int n, const int*
     }
 }
 
+// Slice of t given z[0] <= t < z[D]: a guess from the exponential spacing of the slice table
+// (lz0 = log2 z[0], kscale = D / log2(z[D] / z[0])), verified against the stored bounds and
+// corrected to a neighbour; any other table falls back to the binary search. The result is the
+// unique k with z[k] <= t < z[k + 1] either way.
+__device__ __forceinline__ int slice_of(const float* __restrict__ z, int D, float t);
+
+__device__ __forceinline__ int slice_guess(const float* __restrict__ z, int D, float t, float lz0, float kscale) {
+    int k = (int)((__log2f(t) - lz0) * kscale);
+    k = min(max(k, 0), D - 1);
+    const float lo = z[k], hi = z[k + 1];
+    if (lo <= t && t < hi) return k;
+    if (t < lo && k > 0 && z[k - 1] <= t) return k - 1;
+    if (t >= hi && k + 1 < D && t < z[k + 2]) return k + 1;
+    return slice_of(z, D, t);
+}
+
 __device__ __forceinline__ int slice_of(const float* __restrict__ z, int D, float t) {
     int lo = 0, hi = D - 1;  // max k in [0, D-1] with z[k] <= t (z[0] <= t holds)
     while (lo < hi) {
@@ -203,6 +219,7 @@ __global__ void __launch_bounds__(256, 4) froxel_items_kernel(
         const float tanh_ = c.tan_half;
         const float* z = c.slices;
         const float z0 = z[0], zD = z[g.D];
+        const float lz0 = __log2f(z0), kscale = (float)g.D / (__log2f(zD) - lz0);
         const float num = __fsub_rn(fr.P, o_ax);
         size_t word_base = (((size_t)fr.b * g.D) * g.H + y) * WW + (x >> 5);
         const uint32_t bit = 1u << (x & 31);
@@ -237,7 +254,7 @@ __global__ void __launch_bounds__(256, 4) froxel_items_kernel(
                 const float h2 = __fadd_rn(o2, __fmul_rn(t, __fadd_rn(ca_2[i], su_2)));
                 if (!(h2 >= fr.lo2 && h2 <= fr.hi2)) continue;
                 if (!(t >= zlo && t < zhi)) {
-                    const int k = slice_of(z, g.D, t);
+                    const int k = slice_guess(z, g.D, t, lz0, kscale);
                     if constexpr (TEST) {
                         if (__ldg(test_bits + word_base + (size_t)k * g.H * WW) & bit) {
                             visible[lo / 6] = 1;
