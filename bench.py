@@ -147,6 +147,13 @@ class Clocks:
 CONV_FRAME_DRAM_BYTES = {"level1-window": 65_664_000, "level1-product": 68_955_648}
 
 
+def conv_frame_traffic(tuned: dict):
+    """Measured convolution DRAM bytes per frame for the tuned configuration `tuned` ({layer:
+    (config, us)}), or None when its level-1 form was not captured."""
+    lvl1 = {tuned_label(tuned[k][0]).split("-")[0] for k in ("enc1a", "enc1b", "dec1a", "dec1b")}
+    return CONV_FRAME_DRAM_BYTES.get("level1-" + lvl1.pop()) if len(lvl1) == 1 else None
+
+
 def tuned_label(cfg: dict) -> str:
     """Short name of an autotuned BF16 layer configuration."""
     if cfg.get("tune_form") == 2:
@@ -682,8 +689,7 @@ def run_ours(args):
     roof["frac"] = round(roof["achieved"] / roof["peak"], 5)
     # DRAM bytes of the 37 convolution launches of one timed frame (ncu, caches not flushed between
     # kernels, L2 flushed before the frame as here): profiles/city256_bf16_frame_launches.md
-    lvl1 = {tuned_label(tuned[k][0]).split("-")[0] for k in ("enc1a", "enc1b", "dec1a", "dec1b")}
-    roof["traffic"] = CONV_FRAME_DRAM_BYTES.get("level1-" + lvl1.pop()) if len(lvl1) == 1 else None
+    roof["traffic"] = conv_frame_traffic(tuned)
     roof["time_ms"] = round(t_s * 1e3, 4)
     roof["kernel"] = dom
     roof["peak_source"] = peak_src

@@ -52,3 +52,24 @@ def test_single_process_needs_no_group():
     import bench
     assert bench.max_over_ranks(2.25, "cpu") == 2.25
     assert bench.replica_rate(1, 8, 4.0) == pytest.approx(2000.0)
+
+
+def test_tuned_labels_and_traffic_selection():
+    """The bench names the tuned forms and reports the measured convolution traffic only for a
+    level-1 form that was captured."""
+    sys.path.insert(0, ROOT)
+    import bench
+    prod = {"tune_form": 2}
+    win = {"tune_form": 1, "tune_gather": 3, "tune_max_split": 1}
+    win3 = {"tune_form": 1, "tune_gather": 4}
+    gat = {"tune_form": 1, "tune_gather_warps": 4}
+    assert bench.tuned_label(prod) == "product"
+    assert bench.tuned_label(win) == "window-nosplit"
+    assert bench.tuned_label(win3) == "window3"
+    assert bench.tuned_label(gat) == "gather-4w"
+    l1 = ("enc1a", "enc1b", "dec1a", "dec1b")
+    assert bench.conv_frame_traffic({k: (win, 1.0) for k in l1}) == bench.CONV_FRAME_DRAM_BYTES["level1-window"]
+    assert bench.conv_frame_traffic({k: (prod, 1.0) for k in l1}) == bench.CONV_FRAME_DRAM_BYTES["level1-product"]
+    assert bench.conv_frame_traffic({k: (win3, 1.0) for k in l1}) is None
+    mixed = {k: (prod if k == "enc1a" else win, 1.0) for k in l1}
+    assert bench.conv_frame_traffic(mixed) is None
