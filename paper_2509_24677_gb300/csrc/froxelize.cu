@@ -194,16 +194,24 @@ __global__ void __launch_bounds__(256, 4) froxel_items_kernel(
     for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total;
          base += (long long)gridDim.x * blockDim.x) {
         const long long item = base + lane;
-        int f0 = 0;
-        if (lane == 0) {
-            int lo = 0, hi = n_faces - 1;  // max f with offs[f] <= base
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (offs[mid] <= base) lo = mid; else hi = mid - 1;
-            }
-            f0 = lo;
+        // max f with offs[f] <= base (offs[0] = 0, non-decreasing), searched by the whole warp: each
+        // round the lanes probe 32 evenly spaced faces of [flo, fhi] and a ballot keeps the span of
+        // the last probe that is <= base, so about three rounds of loads instead of log2(n_faces)
+        int flo = 0, fhi = n_faces - 1;
+        while (fhi - flo >= 32) {
+            const int step = (fhi - flo + 32) / 32;
+            const int pos = min(flo + lane * step, fhi);
+            const unsigned ok = __ballot_sync(0xffffffffu, offs[pos] <= base);  // lane 0 (pos = flo) holds
+            const int k = 31 - __clz(ok);
+            flo = min(flo + k * step, fhi);
+            fhi = min(flo + step - 1, fhi);
         }
-        int lo = __shfl_sync(0xffffffffu, f0, 0);
+        {
+            const int pos = flo + lane;
+            const unsigned ok = __ballot_sync(0xffffffffu, pos <= fhi && offs[pos] <= base);
+            flo += 31 - __clz(ok);
+        }
+        int lo = flo;
         if (item >= total) continue;
         while (lo + 1 < n_faces && offs[lo + 1] <= item) ++lo;
         if (TEST && *(volatile const uint8_t*)(visible + lo / 6)) continue;  // box already kept
