@@ -167,8 +167,8 @@ def tuned_label(cfg: dict) -> str:
 
 
 def layer_algorithmic(fp, wl):
-    """Per stage: (bytes, flops, bound) from the actual rulebooks of the last frame (SURVEY-style
-    algorithmic counts: each operand byte once, FLOPs = 2 * pairs * cin * cout)."""
+    """Per stage: (bytes, flops, bound) from the actual rulebooks of the last frame (algorithmic
+    counts: each operand byte once, FLOPs = 2 * pairs * cin * cout)."""
     out = {}
     lv_of = fp._level_of_layers()
     n = [int(lv.n_rows.item()) for lv in fp.levels]
