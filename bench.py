@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--no-train", action="store_true", help="skip the training-step measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-viewcell batched measurement")
     ap.add_argument("--no-highres", action="store_true", help="skip the 512x512x192 measurement")
-    ap.add_argument("--no-paper256", action="store_true", help="skip the 256^3, d=16 measurement")
+    ap.add_argument("--no-paper256", action="store_true",
+                    help="skip the 256^3 measurements (d=16, and d=1 without interleave)")
     ap.add_argument("--train-points", type=int, default=256, help="ground-truth viewpoints per viewcell")
     ap.add_argument("--save-tuned", default=None,
                     help="write the autotuned per-layer kernel configurations of the headline frame (JSON)")
@@ -216,7 +217,7 @@ def cpu_oracle_frame_estimate(budget_s: float):
     """Times the FP64 oracle on a bounded sample of one frame of the same workload: the
     froxelization of a random sample of froxel columns (scaled to the whole grid) plus interleave,
     network and de-interleave of the full frame (on G from a one-ray-per-column raster). Returns
-    (ms per frame, description, cores)."""
+    (ms per frame, description, cores, seconds spent, ms per stage)."""
     from oracle import camera as ocam
     from oracle import froxel as ofx
     from oracle import interleave as oil
@@ -230,12 +231,16 @@ def cpu_oracle_frame_estimate(budget_s: float):
     rng = np.random.default_rng(0)
     t0 = time.perf_counter()
     G1 = ofx.froxelize(cam, boxes, wl.W, wl.H, wl.D, 1)[None]
+    t1 = time.perf_counter()
     coords, feats, _ = oil.interleave(G1, wl.W, wl.d, wl.in_ch)
+    t2 = time.perf_counter()
     levels = onet.build_levels(coords, (1, wl.D // wl.d, wl.H // wl.d, wl.W // wl.d), 4)
     with torch.no_grad():
         logits = onet.forward(list(wl.layers), W_, B_, levels, torch.tensor(feats)).numpy()
+    t3 = time.perf_counter()
     oil.pvs_from_logits(coords, logits, G1, wl.W, wl.d)
-    t_rest = time.perf_counter() - t0
+    t4 = time.perf_counter()
+    t_rest = t4 - t1
     # froxel columns at full supersampling, sized to the remaining budget
     probe = 256
     cols = np.stack([rng.integers(0, wl.W, probe), rng.integers(0, wl.H, probe)], 1)
@@ -247,10 +252,13 @@ def cpu_oracle_frame_estimate(budget_s: float):
     t0 = time.perf_counter()
     ofx.froxel_columns(cam, boxes, wl.W, wl.H, wl.D, wl.supersample, cols)
     t_cols = time.perf_counter() - t0
-    ms = 1e3 * (t_cols * (wl.W * wl.H) / n_cols + t_rest)
+    t_frox = t_cols * (wl.W * wl.H) / n_cols
+    ms = 1e3 * (t_frox + t_rest)
     desc = (f"FP64/binary32-mirror oracle: froxelization of {n_cols} of {wl.W * wl.H} froxel columns "
             f"(s=8, scaled to the grid) + interleave, U-Net and de-interleave of one full frame")
-    return ms, desc, os.cpu_count(), t_cols + t_rest
+    stages = {"froxelize": 1e3 * t_frox, "interleave": 1e3 * (t2 - t1), "rulebooks+network": 1e3 * (t3 - t2),
+              "deinterleave": 1e3 * (t4 - t3)}
+    return ms, desc, os.cpu_count(), t_cols + t_rest + (t1 - t0), {k: round(v, 1) for k, v in stages.items()}
 
 
 def run_reference(args):
@@ -260,7 +268,7 @@ def run_reference(args):
     steps = []
     per_step = max(2.0, min(12.0, 150.0 / max(1, args.steps + args.warmup)))
     for i in range(args.warmup + args.steps):
-        ms, desc, cores, _ = cpu_oracle_frame_estimate(per_step)
+        ms, desc, cores, _, _ = cpu_oracle_frame_estimate(per_step)
         if i >= args.warmup:
             steps.append(ms)
     ms = statistics.mean(steps)
@@ -474,24 +482,41 @@ def run_paper256(args, dev, tf_bf16, hbm_gbs):
                              "2,001-box city seed 0, 1 viewcell")
 
 
-def run_grid_workload(args, dev, tf_bf16, hbm_gbs, wl, boxes, vcs, label):
+def run_paper256_d1(args, dev, tf_bf16, hbm_gbs):
+    """The paper's "no interleave" ablation (Sec. 5.4, ablation table): the paper256 scene and U-Net
+    (192/256) on the 256^3 froxel grid itself, d = 1, one occupancy channel per froxel (stem 1 ->
+    192, head 256 -> 1 logit). Level capacities at 10 % of the sites (1.9 % are occupied)."""
+    boxes = I.city_boxes(0)
+    vcs = I.city_viewcells(0, 1)
+    return run_grid_workload(args, dev, tf_bf16, hbm_gbs, I.workload("paper256_d1"), boxes, vcs,
+                             "paper256_d1: 256x256x256 froxels (s=8), d=1 (1 ch), U-Net 192/256, "
+                             "2,001-box city seed 0, 1 viewcell", capacity_frac=0.1)
+
+
+def run_grid_workload(args, dev, tf_bf16, hbm_gbs, wl, boxes, vcs, label, capacity_frac=1.0):
     """Batch of len(vcs) viewcells of one scene through the BF16 frame (autotuned, one graph of
-    npvs_forward), then stage and per-layer times from a stage-timed graph of the same frame."""
+    npvs_forward), then stage and per-layer times from a stage-timed graph of the same frame.
+    Also reports the peak device memory the frame objects held and the bytes of the layer outputs
+    for the rows that are active."""
     from paper_2509_24677_gb300 import _lib as L
     from paper_2509_24677_gb300 import ops, pipeline as P
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats()
+    mem0 = torch.cuda.memory_allocated()
     B = len(vcs)
     bx = torch.from_numpy(np.concatenate([boxes] * B)).to(dev)
     of = torch.arange(B + 1, dtype=torch.int32, device=dev) * len(boxes)
     cams = ops.cameras_to_device([ops.npvs_camera_setup(v, wl.D) for v in vcs], dev)
     ws, bs = I.kaiming_uniform(wl.layers, seed=0)
     net = P.Net(wl.layers, ws, bs, dev)
-    fp = P.FramePipeline(wl, net, B, L.BF16, device=dev)
+    fp = P.FramePipeline(wl, net, B, L.BF16, device=dev, capacity_frac=capacity_frac)
     fp.run(bx, of, cams)
     stt = ops.npvs_check_status(fp.status)
     if stt != 0:
         raise RuntimeError(f"device status {stt:#x} set in the {wl.name} frame")
-    fp.autotune(bx, of, cams, reps=3)
-    nf = P.NativeFrame(wl, net, B, L.BF16, max_boxes=len(boxes) * B, device=dev, tuned=fp.descs)
+    tuned = fp.autotune(bx, of, cams, reps=3)
+    nf = P.NativeFrame(wl, net, B, L.BF16, max_boxes=len(boxes) * B, device=dev, tuned=fp.descs,
+                       capacity_frac=capacity_frac)
     g = nf.capture(bx, of, len(boxes) * B, cams)
     st = torch.cuda.current_stream()
     ts = []
@@ -523,11 +548,18 @@ def run_grid_workload(args, dev, tf_bf16, hbm_gbs, wl, boxes, vcs, label):
                                 "TFLOP/s": round(v["flops"] / t / 1e12, 2),
                                 "tensor_frac": round(v["flops"] / t / 1e12 / tf_bf16, 4)}
     occ = float(np.unpackbits(fp.occ.cpu().numpy().view(np.uint8)).mean())
+    n_lv = [int(lv.n_rows.item()) for lv in fp.levels]
+    lv_of = fp._level_of_layers()
+    act_bytes = sum(n_lv[lv_of[l.name]] * l.cout * (4 if l.kind == "head1" else 2) for l in wl.layers)
+    peak_mb = (torch.cuda.max_memory_allocated() - mem0) / 2**20
     return {"workload": label, "batch": B, "ms_per_batch": round(ms, 3),
+            "memory_mb": {"peak_device": round(peak_mb, 1), "layer_outputs_active": round(act_bytes / 2**20, 1)},
             "frames_per_s": round(B * 1000.0 / ms, 2), "occupancy": round(occ, 4),
             "active_sites": [int(lv.n_rows.item()) for lv in fp.levels],
             "stage_ms": {k: round(v, 4) for k, v in sorted(acc.items(), key=lambda kv: -kv[1]) if not k.startswith("conv:")},
-            "conv_layers": per_layer, "peaks": {"hbm_gbs": hbm_gbs, "bf16_tflops": tf_bf16}}
+            "conv_layers": per_layer, "peaks": {"hbm_gbs": hbm_gbs, "bf16_tflops": tf_bf16},
+            "autotuned": {l.name: ("simt" if l.cin % 8 or l.cout % 8 else tuned_label(tuned[l.name][0]))
+                          for l in wl.layers}}
 
 
 def run_ours(args):
@@ -727,13 +759,18 @@ def run_ours(args):
         line["highres"] = run_highres(args, dev, tf_bf16, hbm_gbs)
     if not args.no_paper256:
         line["paper256"] = run_paper256(args, dev, tf_bf16, hbm_gbs)
+        d1 = run_paper256_d1(args, dev, tf_bf16, hbm_gbs)
+        d1["vs_interleaved"] = {"time_ratio": round(d1["ms_per_batch"] / line["paper256"]["ms_per_batch"], 2),
+                                "what": "ms per frame without interleave / with d=16 (the paper's Sec. 5.4 ablation "
+                                        "table: 25.4 / 10.1 ms)"}
+        line["paper256_d1"] = d1
     if not args.no_train:
         del g16, g32, g16t
         line["train"] = run_train(args, dev, flush)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cms, desc, cores, spent = cpu_oracle_frame_estimate(args.cpu_seconds)
+        cms, desc, cores, spent, cstages = cpu_oracle_frame_estimate(args.cpu_seconds)
         line["cpu_baseline"] = {"value": round(1000.0 / cms, 5), "unit": "frames/s", "cores": cores, "kind": "oracle",
-                                "sample": desc, "seconds": round(spent, 1)}
+                                "sample": desc, "seconds": round(spent, 1), "stage_ms": cstages}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -124,7 +124,11 @@ typedef enum {
  *  n_out: device row count of the output level; cap_out its capacity (grid sizing).
  *  x: [cap_in][cin]; y: [cap_out][cout]; skip (nullable): [cap_out][cout] added after ReLU.
  *  dtype: F32 / F64 (SIMT FMA kernels, weights [taps][cin][cout]) or BF16 (tcgen05 kernels,
- *  weights packed by npvs_pack_weights, FP32 accumulation); out_f32: with BF16, write FP32 y. */
+ *  weights packed by npvs_pack_weights, FP32 accumulation); out_f32: with BF16, write FP32 y.
+ *  BF16 with cin or cout not a multiple of 8 (the one- or two-channel stem and the one-logit head of
+ *  a network without interleave, d = 1): a SIMT kernel with FP32 accumulation, the packed image is
+ *  plain BF16 [taps][cin][cout], the tune fields and the workspace are not used, and
+ *  npvs_sparse_conv_bwd returns NPVS_ERR_UNSUPPORTED. */
 typedef struct {
     int32_t kind;
     int32_t dtype;

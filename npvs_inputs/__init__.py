@@ -265,6 +265,10 @@ def workload(name: str) -> Workload:
         return Workload(name, 256, 256, 256, 16, 1, 8, tuple(unet_layers(4096, [192, 256], 4096)))
     if name == "paper64":      # the same network at d=16 on a 64^3 grid (4^3 coarse sites)
         return Workload(name, 64, 64, 64, 16, 1, 8, tuple(unet_layers(4096, [192, 256], 4096)))
+    if name == "paper256_d1":  # the paper256 network without interleave: one channel per froxel
+        return Workload(name, 256, 256, 256, 1, 1, 8, tuple(unet_layers(1, [192, 256], 1)))
+    if name == "nointerleave64":  # d=1 on a 64^3 grid, narrow widths (small enough for the oracle)
+        return Workload(name, 64, 64, 64, 1, 1, 8, tuple(unet_layers(1, [16, 32], 1)))
     raise KeyError(name)
 
 

@@ -1,4 +1,5 @@
-// a5/a6: sparse convolutions, SIMT FMA path (FP32 and FP64) and the npvs_sparse_conv_fwd entry.
+// a5/a6: sparse convolutions, SIMT FMA path (FP32 and FP64; BF16 shapes that do not fit the tensor-core
+// tiles) and the npvs_sparse_conv_fwd entry.
 //
 // FP32 (when the descriptor's workspace holds the product tiles): the product form, as on the
 // tensor cores but in FP32 FMA: a dense GEMM T[n][j * cout + o] = sum_c x[n][c] W_j[c][o] over the
@@ -250,6 +251,148 @@ __global__ void __launch_bounds__(256) reduce_f32_kernel(const float* __restrict
     }
 }
 
+// BF16 convolutions whose channel counts do not fit the tensor-core tiles (cin or cout not a
+// multiple of 8: the stem and the head of a network without interleave, d = 1, have one or two
+// input channels and one logit per site). One thread per output element (row n, channel o; o
+// fastest, so a warp shares the row's neighbour rows and reads a contiguous weight row), FP32
+// accumulation over the taps in order and the input channels in order (eight at a time from a
+// 16-byte load when cin % 8 == 0), then bias, ReLU, skip and one rounding to the output type.
+__global__ void __launch_bounds__(256) conv_narrow_bf16_kernel(npvs_conv_desc dsc, const __nv_bfloat16* __restrict__ x,
+                                                               const __nv_bfloat16* __restrict__ w,
+                                                               const float* __restrict__ bias,
+                                                               const __nv_bfloat16* __restrict__ skip, void* __restrict__ y,
+                                                               int vec8) {
+    pdl_begin();
+    const int n_out = min(*dsc.n_out, dsc.cap_out);
+    const int taps = conv_taps(dsc.kind), cin = dsc.cin, cout = dsc.cout;
+    const long long total = (long long)n_out * cout;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int n = (int)(e / cout), o = (int)(e - (long long)n * cout);
+        float acc = 0.0f;
+        for (int t = 0; t < taps; ++t) {
+            const int r = gather_row(dsc.kind, dsc.map, n, t);
+            if (r < 0) continue;
+            const __nv_bfloat16* xr = x + (size_t)r * cin;
+            const __nv_bfloat16* wt = w + (size_t)t * cin * cout + o;
+            if (vec8) {
+                for (int k = 0; k < cin; k += 8) {
+                    const uint4 q = __ldg(reinterpret_cast<const uint4*>(xr + k));
+                    const __nv_bfloat16* xv = reinterpret_cast<const __nv_bfloat16*>(&q);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        acc = fmaf(__bfloat162float(xv[j]), __bfloat162float(wt[(size_t)(k + j) * cout]), acc);
+                }
+            } else {
+                for (int k = 0; k < cin; ++k)
+                    acc = fmaf(__bfloat162float(xr[k]), __bfloat162float(wt[(size_t)k * cout]), acc);
+            }
+        }
+        float v = acc + (bias ? bias[o] : 0.0f);
+        if (dsc.relu) v = fmaxf(v, 0.0f);
+        if (skip) v += __bfloat162float(skip[e]);
+        if (dsc.out_f32)
+            static_cast<float*>(y)[e] = v;
+        else
+            static_cast<__nv_bfloat16*>(y)[e] = __float2bfloat16_rn(v);
+    }
+}
+
+// The same convolution for few input channels (cin <= 8) and 16..256 output channels (the stem of a
+// network without interleave): one warp per output row. Lane t < taps fetches the row's neighbour
+// index and that neighbour's cin inputs once (the loads of all taps in flight together); the taps
+// are then walked in order, the index and inputs broadcast by shuffle, and lane l accumulates the
+// output channels l, l + 32, ... against weights staged in shared memory as FP32, in the summation
+// order of conv_narrow_bf16_kernel.
+constexpr int kNarrowMaxCin = 8;
+template <int NJ>
+__global__ void __launch_bounds__(256) conv_narrow_rows_kernel(npvs_conv_desc dsc, const __nv_bfloat16* __restrict__ x,
+                                                               const __nv_bfloat16* __restrict__ w,
+                                                               const float* __restrict__ bias,
+                                                               const __nv_bfloat16* __restrict__ skip, void* __restrict__ y) {
+    extern __shared__ float s_w[];  // [taps][cin][cout]
+    const int taps = conv_taps(dsc.kind), cin = dsc.cin, cout = dsc.cout;
+    const int nw = taps * cin * cout;
+    pdl_begin();  // the weights may come from a packing kernel just before
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) s_w[i] = __bfloat162float(w[i]);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int n_out = min(*dsc.n_out, dsc.cap_out);
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int n = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); n < n_out; n += warps) {
+        int r = -1;
+        float xk[kNarrowMaxCin];
+#pragma unroll
+        for (int k = 0; k < kNarrowMaxCin; ++k) xk[k] = 0.0f;
+        if (lane < taps) {
+            r = gather_row(dsc.kind, dsc.map, n, lane);
+            if (r >= 0) {
+#pragma unroll
+                for (int k = 0; k < kNarrowMaxCin; ++k)
+                    if (k < cin) xk[k] = __bfloat162float(x[(size_t)r * cin + k]);
+            }
+        }
+        float acc[NJ];
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) acc[j] = 0.0f;
+        for (int t = 0; t < taps; ++t) {
+            const int rt = __shfl_sync(0xffffffffu, r, t);
+            if (rt < 0) continue;  // warp-uniform
+#pragma unroll
+            for (int k = 0; k < kNarrowMaxCin; ++k) {
+                if (k >= cin) break;
+                const float xv = __shfl_sync(0xffffffffu, xk[k], t);
+                const float* wr = s_w + (t * cin + k) * cout;
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) {
+                    const int o = lane + 32 * j;
+                    if (o < cout) acc[j] = fmaf(xv, wr[o], acc[j]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            const int o = lane + 32 * j;
+            if (o >= cout) continue;
+            const size_t e = (size_t)n * cout + o;
+            float v = acc[j] + (bias ? bias[o] : 0.0f);
+            if (dsc.relu) v = fmaxf(v, 0.0f);
+            if (skip) v += __bfloat162float(skip[e]);
+            if (dsc.out_f32)
+                static_cast<float*>(y)[e] = v;
+            else
+                static_cast<__nv_bfloat16*>(y)[e] = __float2bfloat16_rn(v);
+        }
+    }
+}
+
+template <int NJ>
+npvs_status launch_narrow_rows(const npvs_conv_desc& d, const void* x, const void* w, const float* bias,
+                               const void* skip, void* y, size_t smem, cudaStream_t st) {
+    const int grid = (int)std::max<long long>(1, std::min<long long>(ceil_div((long long)d.cap_out, 8), (long long)kNumSMs * 8));
+    launch_k(conv_narrow_rows_kernel<NJ>, grid, 256, smem, st, d, (const __nv_bfloat16*)x, (const __nv_bfloat16*)w,
+             bias, (const __nv_bfloat16*)skip, y);
+    return check_launch("conv_narrow_rows_kernel");
+}
+
+npvs_status conv_narrow_bf16(const npvs_conv_desc& d, const void* x, const void* w, const float* bias,
+                             const void* skip, void* y, cudaStream_t st) {
+    const int taps = d.kind == NPVS_CONV_SUBM3 ? 27 : (d.kind == NPVS_CONV_HEAD1 ? 1 : 8);
+    const size_t smem = (size_t)taps * d.cin * d.cout * sizeof(float);
+    if (d.cin <= kNarrowMaxCin && d.cout >= 16 && d.cout <= 256 && smem <= 48 * 1024) {
+        if (d.cout <= 32) return launch_narrow_rows<1>(d, x, w, bias, skip, y, smem, st);
+        if (d.cout <= 64) return launch_narrow_rows<2>(d, x, w, bias, skip, y, smem, st);
+        if (d.cout <= 128) return launch_narrow_rows<4>(d, x, w, bias, skip, y, smem, st);
+        return launch_narrow_rows<8>(d, x, w, bias, skip, y, smem, st);
+    }
+    const long long total = (long long)d.cap_out * d.cout;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(ceil_div(total, 256), (long long)kNumSMs * 16));
+    const int vec8 = d.cin % 8 == 0 && (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+    launch_k(conv_narrow_bf16_kernel, grid, 256, 0, st, d, (const __nv_bfloat16*)x, (const __nv_bfloat16*)w, bias,
+             (const __nv_bfloat16*)skip, y, vec8);
+    return check_launch("conv_narrow_bf16_kernel");
+}
+
 // The FP32 product form of npvs_sparse_conv_fwd; NPVS_ERR_UNSUPPORTED when it does not apply.
 npvs_status conv_f32_product(const npvs_conv_desc& d, const float* x, const float* w, const float* bias,
                              const float* skip, float* y, cudaStream_t st) {
@@ -291,7 +434,9 @@ extern "C" npvs_status npvs_sparse_conv_fwd(const npvs_conv_desc* dsc, const voi
                  "npvs_sparse_conv_fwd: bad sizes");
     cudaStream_t st = as_stream(stream);
     if (dsc->cap_out == 0) return NPVS_OK;
-    if (dsc->dtype == NPVS_BF16) return conv_tc_fwd(*dsc, x, w, (const float*)bias, skip, y, st);
+    if (dsc->dtype == NPVS_BF16)
+        return bf16_narrow(dsc->cin, dsc->cout) ? conv_narrow_bf16(*dsc, x, w, (const float*)bias, skip, y, st)
+                                                : conv_tc_fwd(*dsc, x, w, (const float*)bias, skip, y, st);
     if (dsc->dtype == NPVS_F32) {
         const npvs_status s = conv_f32_product(*dsc, (const float*)x, (const float*)w, (const float*)bias,
                                                (const float*)skip, (float*)y, st);

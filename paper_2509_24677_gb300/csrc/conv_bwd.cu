@@ -414,6 +414,8 @@ extern "C" npvs_status npvs_sparse_conv_bwd(const npvs_conv_desc* desc, const vo
                  "npvs_sparse_conv_bwd: unknown kind");
     NPVS_REQUIRE(d.cin > 0 && d.cout > 0 && d.cap_out >= 0, NPVS_ERR_INVALID_ARG, "npvs_sparse_conv_bwd: bad sizes");
     NPVS_REQUIRE(d.kind == NPVS_CONV_HEAD1 || d.map, NPVS_ERR_INVALID_ARG, "npvs_sparse_conv_bwd: map is NULL");
+    NPVS_REQUIRE(d.dtype != NPVS_BF16 || !bf16_narrow(d.cin, d.cout), NPVS_ERR_UNSUPPORTED,
+                 "npvs_sparse_conv_bwd: BF16 needs cin and cout multiples of 8");
     NPVS_REQUIRE(!d.relu || y, NPVS_ERR_INVALID_ARG, "npvs_sparse_conv_bwd: a ReLU layer needs its output y");
     NPVS_REQUIRE(!(d.relu && d.out_f32), NPVS_ERR_UNSUPPORTED, "npvs_sparse_conv_bwd: ReLU with out_f32 is not supported");
     NPVS_REQUIRE(!dx || d.kind == NPVS_CONV_SUBM3 || d.kind == NPVS_CONV_HEAD1 || d.map2, NPVS_ERR_INVALID_ARG,

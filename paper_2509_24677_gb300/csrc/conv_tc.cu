@@ -847,6 +847,15 @@ __global__ void pack_weights_kernel(int kind, int cin, int cout, TcShape sh, con
     }
 }
 
+// Plain BF16 image [taps][cin][cout] (round to nearest even) of the SIMT-path convolutions.
+__global__ void pack_plain_kernel(size_t total, const float* __restrict__ w, __nv_bfloat16* __restrict__ out) {
+    pdl_begin();
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x)
+        out[e] = __float2bfloat16_rn(w[e]);
+}
+
+int conv_taps_host(int kind) { return kind == NPVS_CONV_SUBM3 ? 27 : (kind == NPVS_CONV_HEAD1 ? 1 : 8); }
+
 constexpr int kMaxStages = 12;
 constexpr size_t kMaxSmem = 227 * 1024;
 
@@ -930,6 +939,7 @@ size_t split_region_bytes() {
 
 size_t product_region_bytes(const npvs_conv_desc& d) {
     if (!has_product_form(d.kind) && d.kind != NPVS_CONV_UP2) return 0;
+    if (d.dtype == NPVS_BF16 && bf16_narrow(d.cin, d.cout)) return 0;
     const int J = d.kind == NPVS_CONV_SUBM3 ? 27 : 8;
     const int rows = d.cap_in > 0 ? d.cap_in : d.cap_out;
     return Arena::round((size_t)rows * J * d.cout * sizeof(float));
@@ -1144,6 +1154,10 @@ extern "C" size_t npvs_conv_workspace_bytes(const npvs_conv_desc* d) {
 }
 
 extern "C" size_t npvs_packed_weight_bytes(int32_t kind, int32_t cin, int32_t cout) {
+    if (kind < NPVS_CONV_SUBM3 || kind > NPVS_CONV_HEAD1 || cin <= 0 || cout <= 0) return 0;
+    if (bf16_narrow(cin, cout)) {
+        return Arena::round((size_t)conv_taps_host(kind) * cin * cout * sizeof(__nv_bfloat16));
+    }
     size_t b = packed_image_bytes(kind, cin, cout, 0);
     if (has_product_form(kind)) b += packed_image_bytes(kind, cin, cout, 1);
     return b;
@@ -1155,6 +1169,13 @@ npvs_status pack_weights_mode(int kind, int cin, int cout, const float* w, void*
     NPVS_REQUIRE(w && packed && cin > 0 && cout > 0, NPVS_ERR_INVALID_ARG, "npvs_pack_weights: bad arguments");
     NPVS_REQUIRE(kind >= NPVS_CONV_SUBM3 && kind <= NPVS_CONV_HEAD1, NPVS_ERR_UNSUPPORTED,
                  "npvs_pack_weights: unknown kind");
+    if (bf16_narrow(cin, cout)) {
+        NPVS_REQUIRE(mode == 0, NPVS_ERR_UNSUPPORTED, "BF16 conv: transposed packing needs cin and cout multiples of 8");
+        const size_t total = (size_t)conv_taps_host(kind) * cin * cout;
+        const int grid = (int)std::min<size_t>((total + 255) / 256, (size_t)kNumSMs * 16);
+        launch_k(pack_plain_kernel, grid, 256, 0, st, total, w, (__nv_bfloat16*)packed);
+        return check_launch("pack_plain_kernel");
+    }
     const int nforms = has_product_form(kind) ? 2 : 1;
     char* out = (char*)packed;
     for (int f = 0; f < nforms; ++f) {

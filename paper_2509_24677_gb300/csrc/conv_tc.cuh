@@ -21,6 +21,10 @@ __device__ __forceinline__ int gather_row(int kind, const int32_t* __restrict__ 
     }
 }
 
+// BF16 convolutions with cin or cout not a multiple of 8 run on a SIMT kernel (FP32 accumulation)
+// with plain BF16 weights [taps][cin][cout] as their packed image, not on the tensor cores.
+inline bool bf16_narrow(int cin, int cout) { return cin % 8 != 0 || cout % 8 != 0; }
+
 // GEMM view of a convolution: rows x (Kflat = taps_eff * cin) x Ntot.
 //   G-form (SUBM3, DOWN2, HEAD1): row = output row, k = tap * cin + ci, n = co.
 //   S-form (UP2): row = coarse input row, k = ci, n = child_tap * cout + co; the epilogue scatters

@@ -80,3 +80,21 @@ def test_forward_plan_validation_on_host():
     assert lib.npvs_forward_workspace_bytes(desc) == 0
     lay[1].cout, lay[1].cin = 8, 12
     assert lib.npvs_forward_workspace_bytes(desc) == 0
+
+
+def test_packed_weight_and_workspace_sizes_of_narrow_bf16_convs():
+    """BF16 convolutions with cin or cout off the tensor-core tiles (the stem and head of a network
+    without interleave) keep plain BF16 weights [taps][cin][cout] and need no product tiles; the
+    tensor-core shapes keep their larger tiled images."""
+    from paper_2509_24677_gb300 import _lib as L
+    from paper_2509_24677_gb300 import ops
+    rnd = lambda b: (b + 255) // 256 * 256
+    for kind, taps in ((L.CONV_SUBM3, 27), (L.CONV_DOWN2, 8), (L.CONV_UP2, 8), (L.CONV_HEAD1, 1)):
+        for cin, cout in ((1, 16), (2, 192), (3, 5), (192, 1), (16, 1)):
+            assert ops.npvs_packed_weight_bytes(kind, cin, cout) == rnd(taps * cin * cout * 2), (kind, cin, cout)
+        assert ops.npvs_packed_weight_bytes(kind, 16, 16) >= taps * 16 * 16 * 2
+    base = ops.npvs_conv_workspace_bytes(None)
+    narrow = ops.conv_desc(L.CONV_SUBM3, L.BF16, 1, 192, True, None, None, 1000)
+    wide = ops.conv_desc(L.CONV_SUBM3, L.BF16, 16, 192, True, None, None, 1000)
+    assert ops.npvs_conv_workspace_bytes(narrow) == base
+    assert ops.npvs_conv_workspace_bytes(wide) >= base + 1000 * 27 * 192 * 4

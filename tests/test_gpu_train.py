@@ -156,6 +156,15 @@ def test_conv_bwd_argument_errors():
         ops.npvs_sparse_conv_bwd(d, z, torch.zeros(8, 16, 16, device=DEV), z, z, z, None,
                                  torch.zeros(8, 16, 16, device=DEV), None, ws[:16])
     assert e.value.status == L.ERR_WORKSPACE
+    # BF16 channel counts off the tensor-core tiles have a forward kernel only
+    d1 = ops.conv_desc(L.CONV_SUBM3, L.BF16, 1, 16, True, lvs[0].nbr, lvs[0].n_rows, lvs[0].capacity)
+    ws1 = ops.conv_workspace(ops.npvs_conv_bwd_workspace_bytes(d1), DEV)
+    xb = torch.zeros(64, 1, dtype=torch.bfloat16, device=DEV)
+    yb = torch.zeros(64, 16, dtype=torch.bfloat16, device=DEV)
+    with pytest.raises(L.NpvsError) as e:
+        ops.npvs_sparse_conv_bwd(d1, xb, torch.zeros(27, 1, 16, device=DEV), yb, yb, None, None,
+                                 torch.zeros(27, 1, 16, device=DEV), None, ws1)
+    assert e.value.status == L.ERR_UNSUPPORTED
 
 
 # ------------------------------------------------------------------------------------------

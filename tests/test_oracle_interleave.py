@@ -53,6 +53,21 @@ def test_channel_order_by_loops():
     assert n == len(coords)
 
 
+def test_d1_is_the_list_of_occupied_froxels():
+    """Without interleave (d = 1, Sec. 5.4's ablation) the active sites are the occupied froxels in
+    linear order, each with occupancy 1 and its slice-centre depth (k + 1/2) / D."""
+    rng = np.random.default_rng(3)
+    B, D, H, W = 2, 5, 3, 64
+    dense = rng.random((B, D, H, W)) < 0.1
+    coords, feats, active = IL.interleave(IL.pack_bits(dense), W, 1, 2)
+    occ = [(b, z, y, x) for b in range(B) for z in range(D) for y in range(H) for x in range(W) if dense[b, z, y, x]]
+    assert [tuple(c) for c in coords] == occ
+    assert feats.shape == (len(occ), 2)
+    assert (feats[:, 0] == 1.0).all()
+    for (b, z, y, x), dep in zip(occ, feats[:, 1]):
+        assert dep == np.float32((z + 0.5) / D)
+
+
 def test_depth_channel_exact():
     for D in (32, 128, 192):
         v = IL.depth_channel(D)
