@@ -106,13 +106,22 @@ typedef struct {
     int32_t* table;   /* device [B*Z*Y*X] */
 } npvs_level;
 
-typedef enum { NPVS_RB_SUBM3 = 0, NPVS_RB_DOWN2 = 1, NPVS_RB_SUBM3_TABLE = 2 } npvs_rulebook_kind;
+typedef enum {
+    NPVS_RB_SUBM3 = 0,
+    NPVS_RB_DOWN2 = 1,
+    NPVS_RB_SUBM3_TABLE = 2,
+    NPVS_RB_DOWN3 = 3
+} npvs_rulebook_kind;
 
 typedef enum {
     NPVS_CONV_SUBM3 = 0, /* submanifold 3x3x3: output set = input set */
     NPVS_CONV_DOWN2 = 1, /* 2x2x2 stride 2: output set = parents */
     NPVS_CONV_UP2 = 2,   /* transposed 2x2x2 stride 2 onto the finer level's set */
-    NPVS_CONV_HEAD1 = 3  /* 1x1x1 */
+    NPVS_CONV_HEAD1 = 3, /* 1x1x1 */
+    NPVS_CONV_DOWN3 = 4, /* 3x3x3 stride 2 padding 1: output q gets input 2q + k - 1 through tap k;
+                            output set = the dilated set of a DOWN3 rulebook */
+    NPVS_CONV_UP3 = 5    /* its transpose: output p gets input q with p = 2q + k - 1, onto the
+                            finer level's set */
 } npvs_conv_kind;
 
 /* One sparse convolution (Sec. 2.3; masked dense definition y[p] = b + sum_t W_t^T x[p + t]).
@@ -121,6 +130,10 @@ typedef enum {
  *        UP2   -> parent*8 + child-tap of each fine row [cap_out] (the "up map"); map2 -> the
  *                 child rows of each coarse row [cap_in][8] (the down map of the same level pair)
  *        HEAD1 -> NULL
+ *        DOWN3 -> input rows of the 27 taps of each output [cap_out][27] (the map of a DOWN3
+ *                 rulebook); UP3 -> the map2 of that rulebook, [cap_out][27] coarse rows
+ *        (DOWN3 / UP3: forward only, npvs_sparse_conv_bwd returns NPVS_ERR_UNSUPPORTED; n_in and
+ *        cap_in are required)
  *  n_out: device row count of the output level; cap_out its capacity (grid sizing).
  *  x: [cap_in][cin]; y: [cap_out][cout]; skip (nullable): [cap_out][cout] added after ReLU.
  *  dtype: F32 / F64 (SIMT FMA kernels, weights [taps][cin][cout]) or BF16 (tcgen05 kernels,
@@ -279,7 +292,13 @@ size_t npvs_rulebook_workspace_bytes(npvs_dims dims);
  * sites {floor(p/2)} in linear order (out->dims must be in->dims halved; all even), map
  * [out->capacity][8] = rows of each parent's children (tap (cz*2+cy)*2+cx, -1 if absent), and
  * map2 [in->capacity] = parent_row*8 + tap of every fine row (the up map). Overflow of
- * out->capacity sets NPVS_ERR_CAPACITY in status. */
+ * out->capacity sets NPVS_ERR_CAPACITY in status.
+ * DOWN3 (Sec. 2.3: a sparse convolution whose outputs dilate onto the neighbours of active sites;
+ * here a 3x3x3 kernel, stride 2, padding 1): the same
+ * from in->table for the dilated output set {q : some 2q + k - 1 active, k in {0,1,2}^3} in linear
+ * order (out->dims = in->dims halved), map [out->capacity][27] = the input row of 2q + k - 1 for tap
+ * k = (kz*3 + ky)*3 + kx (-1 if absent) and map2 [in->capacity][27] = for every fine row p and tap
+ * k the output row q with p = 2q + k - 1 (-1 if none): the map of the transposed convolution. */
 npvs_status npvs_build_rulebook(int32_t kind, const npvs_level* in, const npvs_level* out,
                                 int32_t* map, int32_t* map2, int32_t* status, void* workspace,
                                 size_t workspace_bytes, void* stream);
@@ -287,8 +306,8 @@ npvs_status npvs_build_rulebook(int32_t kind, const npvs_level* in, const npvs_l
 /* ---- a5/a6: sparse convolution ------------------------------------------------------------- */
 
 /* Bytes of the BF16 convolution workspace for this convolution (split-K region, plus for SUBM3 /
- * DOWN2 / UP2 the FP32 product tiles T of cap_in x taps x cout, taps 27 / 8 / 8). NULL: the
- * split-K region only. */
+ * DOWN2 / UP2 / DOWN3 / UP3 the FP32 product tiles T of cap_in x taps x cout, taps 27 / 8 / 8 / 27
+ * / 27). NULL: the split-K region only. */
 size_t npvs_conv_workspace_bytes(const npvs_conv_desc* desc);
 
 /* Bytes of a packed BF16 weight tensor for a forward conv of this shape. */

@@ -181,14 +181,15 @@ def gt_candidate_offsets(seed: int, vc: Viewcell, n: int) -> np.ndarray:
 @dataclasses.dataclass(frozen=True)
 class Layer:
     name: str
-    kind: str        # "subm3" (27 taps), "down2" (8 taps, stride 2), "up2" (8 taps, inverse), "head1" (1 tap)
+    kind: str        # "subm3" (27 taps), "down2" (8 taps, stride 2), "up2" (8 taps, inverse), "head1" (1 tap),
+                     # "down3" (27 taps, stride 2, padding 1), "up3" (27 taps, its inverse)
     cin: int
     cout: int
     relu: bool
 
     @property
     def taps(self) -> int:
-        return {"subm3": 27, "down2": 8, "up2": 8, "head1": 1}[self.kind]
+        return {"subm3": 27, "down2": 8, "up2": 8, "head1": 1, "down3": 27, "up3": 27}[self.kind]
 
 
 def plain_layers(channels: Sequence[int]) -> List[Layer]:

@@ -9,10 +9,11 @@ Modules, each citing the paper passage it restates:
   camera      viewcell -> enclosing frustum and slice table (Sec. 3.2, first paragraph)
   froxel      froxelization (FP32 mirror and FP64) and ray-cast ground truth (Sec. 3.2) in C
   interleave  g_d, g_d^-1, active coarse sites (Sec. 3.3, "3D volume-preserving interleaving")
-  network     sparse convolutions as masked dense convolutions, the networks (Sec. 3.3, Sec. 2.3)
-  loss        weighted Dice + repulsive visibility loss (Sec. 3.3)
-  adam        Adam update on FP32 master weights (Sec. 4.2 hyper-parameters)
-  metrics     FNR / FPR (Sec. 5.1)
+  network     sparse convolutions as masked dense convolutions (SubM3, 2x2x2 and 3x3x3 stride 2 and
+              their transposes, 1x1), the networks (Sec. 3.3, Sec. 2.3)
+  rulebook    neighbour maps and the stride-2 output sets by dict lookups (Sec. 2.3)
+  loss        weighted Dice + repulsive visibility loss (Sec. 3.3), the Adam update on FP32 master
+              weights (Sec. 4.2 hyper-parameters), FNR / FPR (Sec. 5.1)
 
 Where the paper is silent or inconsistent, the reading taken is stated in the function's
 docstring.

@@ -14,6 +14,9 @@ active output sites only, which is what the sparse variants compute:
   up2       transposed stride-2 conv: out[2P + c] = b + W_c^T z[P], read at the finer level's
             active set (the encoder set of that level)
   head1     y[p] = b + W_0^T x[p]
+  down3     k = 3, stride 2, padding 1: y[q] = b + sum_{k in {0,1,2}^3} W_k^T x[2q + k - 1] at the
+            dilated output set {q : some 2q + k - 1 active}; tap (kz*3 + ky)*3 + kx
+  up3       its transpose: out[2q + k - 1] += W_k^T z[q], read at the finer level's active set
 Inactive inputs are zero, which is the "masked dense convolution" reading.
 
 Readings (the workloads name channel widths only): ReLU after every layer except the head;
@@ -29,6 +32,7 @@ import numpy as np
 import torch
 
 OFFS27 = [(dz, dy, dx) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+K27 = [(kz, ky, kx) for kz in range(3) for ky in range(3) for kx in range(3)]
 CHILD8 = [(cz, cy, cx) for cz in (0, 1) for cy in (0, 1) for cx in (0, 1)]
 
 F64 = torch.float64
@@ -56,6 +60,18 @@ class Level:
         Wp, Hp, Dp = pd[3], pd[2], pd[1]
         pc = torch.stack([u // (Dp * Hp * Wp), (u // (Hp * Wp)) % Dp, (u // Wp) % Hp, u % Wp], 1)
         return Level(pc, pd)
+
+    def strided3(self) -> "Level":
+        """The output set of a k = 3, stride 2, padding 1 convolution: the halved-grid sites whose
+        3^3 input window {2q - 1, 2q, 2q + 1}^3 holds an active site (max-pooling of the indicator)."""
+        B, Dz, Hy, Wx = self.dims
+        assert Dz % 2 == 0 and Hy % 2 == 0 and Wx % 2 == 0
+        ind = torch.zeros((B, 1, Dz, Hy, Wx), dtype=F64)
+        c = self.coords
+        ind[c[:, 0], 0, c[:, 1], c[:, 2], c[:, 3]] = 1.0
+        pooled = torch.nn.functional.max_pool3d(ind, kernel_size=3, stride=2, padding=1)[:, 0]
+        assert pooled.shape[1:] == (Dz // 2, Hy // 2, Wx // 2)
+        return Level(torch.nonzero(pooled > 0), (B, Dz // 2, Hy // 2, Wx // 2))
 
 
 def _dense(level: Level, x: torch.Tensor, halo: int) -> torch.Tensor:
@@ -94,6 +110,25 @@ def up2(coarse: Level, fine: Level, z, W, b):
     out = t.permute(3, 4, 0, 5, 1, 6, 2, 7).reshape(B, 2 * Dc, 2 * Hc, 2 * Wc, cout)
     c = fine.coords
     return b + out[c[:, 0], c[:, 1], c[:, 2], c[:, 3]]
+
+
+def down3(fine: Level, coarse: Level, x, W, b):
+    g = _dense(fine, x, 1)                                  # dense index = site + 1
+    Q = coarse.coords
+    y = b.expand(coarse.n, W.shape[2])
+    for k, (kz, ky, kx) in enumerate(K27):                  # input 2q + k - 1 at dense index 2q + k
+        y = y + g[Q[:, 0], 2 * Q[:, 1] + kz, 2 * Q[:, 2] + ky, 2 * Q[:, 3] + kx] @ W[k]
+    return y
+
+
+def up3(coarse: Level, fine: Level, z, W, b):
+    zd = _dense(coarse, z, 0)                               # B, Dc, Hc, Wc, Cin
+    B, Dc, Hc, Wc, _ = zd.shape
+    out = torch.zeros((B, 2 * Dc + 1, 2 * Hc + 1, 2 * Wc + 1, W.shape[2]), dtype=zd.dtype)
+    for k, (kz, ky, kx) in enumerate(K27):                  # output 2q + k - 1 at dense index 2q + k
+        out[:, kz:kz + 2 * Dc:2, ky:ky + 2 * Hc:2, kx:kx + 2 * Wc:2] += zd @ W[k]
+    c = fine.coords
+    return b + out[c[:, 0], c[:, 1] + 1, c[:, 2] + 1, c[:, 3] + 1]
 
 
 def head1(level: Level, x, W, b):

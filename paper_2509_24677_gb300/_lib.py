@@ -14,8 +14,8 @@ NPVS_MAX_SLICES = 256
 
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CAPACITY, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT = range(7)
 F32, BF16, F64 = 0, 1, 2
-RB_SUBM3, RB_DOWN2, RB_SUBM3_TABLE = 0, 1, 2
-CONV_SUBM3, CONV_DOWN2, CONV_UP2, CONV_HEAD1 = 0, 1, 2, 3
+RB_SUBM3, RB_DOWN2, RB_SUBM3_TABLE, RB_DOWN3 = 0, 1, 2, 3
+CONV_SUBM3, CONV_DOWN2, CONV_UP2, CONV_HEAD1, CONV_DOWN3, CONV_UP3 = 0, 1, 2, 3, 4, 5
 
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "CAPACITY", 4: "WORKSPACE",
                 5: "CUDA", 6: "TIMEOUT"}

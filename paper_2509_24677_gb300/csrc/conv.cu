@@ -377,7 +377,7 @@ npvs_status launch_narrow_rows(const npvs_conv_desc& d, const void* x, const voi
 
 npvs_status conv_narrow_bf16(const npvs_conv_desc& d, const void* x, const void* w, const float* bias,
                              const void* skip, void* y, cudaStream_t st) {
-    const int taps = d.kind == NPVS_CONV_SUBM3 ? 27 : (d.kind == NPVS_CONV_HEAD1 ? 1 : 8);
+    const int taps = conv_taps(d.kind);
     const size_t smem = (size_t)taps * d.cin * d.cout * sizeof(float);
     if (d.cin <= kNarrowMaxCin && d.cout >= 16 && d.cout <= 256 && smem <= 48 * 1024) {
         if (d.cout <= 32) return launch_narrow_rows<1>(d, x, w, bias, skip, y, smem, st);
@@ -408,12 +408,12 @@ npvs_status conv_f32_product(const npvs_conv_desc& d, const float* x, const floa
     if (T == nullptr || d.n_in == nullptr || d.cap_in <= 0) return NPVS_ERR_UNSUPPORTED;
     const long long work = (long long)d.cap_out * (d.cout / 4);
     if (work >= (1LL << 31)) return NPVS_ERR_UNSUPPORTED;  // the gather kernel handles any size
-    const int J = d.kind == NPVS_CONV_SUBM3 ? 27 : 8;
+    const int J = map27(d.kind) ? 27 : 8;
     const int N = J * d.cout;
     dim3 grid(ceil_div(d.cap_in, GM), ceil_div(N, GN));
     launch_k(gemm_f32_kernel, grid, 256, 0, st, x, d.n_in, d.cap_in, d.cin, w, d.cout, N, T, 0, nullptr, 0, nullptr);
     NPVS_TRY(check_launch("gemm_f32_kernel"));
-    const int taps = d.kind == NPVS_CONV_SUBM3 ? 27 : (d.kind == NPVS_CONV_DOWN2 ? 8 : 0);
+    const int taps = d.kind == NPVS_CONV_UP2 ? 0 : conv_taps(d.kind);
     const int rg = (int)std::max<long long>(1, std::min<long long>(ceil_div(work, 256), kNumSMs * 8));
     launch_k(reduce_f32_kernel, rg, 256, 0, st, T, N, d.map, taps, d.n_out, d.cap_out, d.cout, bias, d.relu, skip, y);
     return check_launch("reduce_f32_kernel");
@@ -427,8 +427,9 @@ using namespace npvs;
 extern "C" npvs_status npvs_sparse_conv_fwd(const npvs_conv_desc* dsc, const void* x, const void* w,
                                             const void* bias, const void* skip, void* y, void* stream) {
     NPVS_REQUIRE(dsc && x && w && y && dsc->n_out, NPVS_ERR_INVALID_ARG, "npvs_sparse_conv_fwd: NULL argument");
-    NPVS_REQUIRE(dsc->kind >= NPVS_CONV_SUBM3 && dsc->kind <= NPVS_CONV_HEAD1, NPVS_ERR_UNSUPPORTED,
-                 "npvs_sparse_conv_fwd: unknown kind");
+    NPVS_REQUIRE(valid_conv_kind(dsc->kind), NPVS_ERR_UNSUPPORTED, "npvs_sparse_conv_fwd: unknown kind");
+    NPVS_REQUIRE(!(dsc->kind == NPVS_CONV_DOWN3 || dsc->kind == NPVS_CONV_UP3) || (dsc->n_in && dsc->cap_in > 0),
+                 NPVS_ERR_INVALID_ARG, "npvs_sparse_conv_fwd: DOWN3 / UP3 need n_in and cap_in");
     NPVS_REQUIRE(dsc->kind == NPVS_CONV_HEAD1 || dsc->map, NPVS_ERR_INVALID_ARG, "npvs_sparse_conv_fwd: map is NULL");
     NPVS_REQUIRE(dsc->cin > 0 && dsc->cout > 0 && dsc->cap_out >= 0, NPVS_ERR_INVALID_ARG,
                  "npvs_sparse_conv_fwd: bad sizes");

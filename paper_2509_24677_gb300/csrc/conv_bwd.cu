@@ -400,7 +400,7 @@ size_t bwd_bytes(const BwdPlan& p) {
 using namespace npvs;
 
 extern "C" size_t npvs_conv_bwd_workspace_bytes(const npvs_conv_desc* desc) {
-    if (!desc) return 0;
+    if (!desc || desc->kind < NPVS_CONV_SUBM3 || desc->kind > NPVS_CONV_HEAD1) return 0;
     BwdPlan p = plan_bwd(*desc);
     return bwd_bytes(p);
 }
@@ -411,7 +411,7 @@ extern "C" npvs_status npvs_sparse_conv_bwd(const npvs_conv_desc* desc, const vo
     NPVS_REQUIRE(desc && x && w && dy && dw && desc->n_out, NPVS_ERR_INVALID_ARG, "npvs_sparse_conv_bwd: NULL argument");
     const npvs_conv_desc& d = *desc;
     NPVS_REQUIRE(d.kind >= NPVS_CONV_SUBM3 && d.kind <= NPVS_CONV_HEAD1, NPVS_ERR_UNSUPPORTED,
-                 "npvs_sparse_conv_bwd: unknown kind");
+                 "npvs_sparse_conv_bwd: unknown kind (DOWN3 / UP3 have a forward only)");
     NPVS_REQUIRE(d.cin > 0 && d.cout > 0 && d.cap_out >= 0, NPVS_ERR_INVALID_ARG, "npvs_sparse_conv_bwd: bad sizes");
     NPVS_REQUIRE(d.kind == NPVS_CONV_HEAD1 || d.map, NPVS_ERR_INVALID_ARG, "npvs_sparse_conv_bwd: map is NULL");
     NPVS_REQUIRE(d.dtype != NPVS_BF16 || !bf16_narrow(d.cin, d.cout), NPVS_ERR_UNSUPPORTED,

@@ -854,7 +854,7 @@ __global__ void pack_plain_kernel(size_t total, const float* __restrict__ w, __n
         out[e] = __float2bfloat16_rn(w[e]);
 }
 
-int conv_taps_host(int kind) { return kind == NPVS_CONV_SUBM3 ? 27 : (kind == NPVS_CONV_HEAD1 ? 1 : 8); }
+int conv_taps_host(int kind) { return conv_taps(kind); }
 
 constexpr int kMaxStages = 12;
 constexpr size_t kMaxSmem = 227 * 1024;
@@ -931,7 +931,7 @@ size_t packed_image_bytes(int kind, int cin, int cout, int form) {
     return Arena::round((size_t)sh.KB * sh.Npad * sh.BKE * sizeof(__nv_bfloat16));
 }
 
-bool has_product_form(int kind) { return kind == NPVS_CONV_SUBM3 || kind == NPVS_CONV_DOWN2; }
+bool has_product_form(int kind) { return map27(kind) || kind == NPVS_CONV_DOWN2; }
 
 size_t split_region_bytes() {
     return Arena::round(4 * kSplitSlots * sizeof(int)) + Arena::round((size_t)kSplitSlots * kBM * 256 * sizeof(float));
@@ -940,7 +940,7 @@ size_t split_region_bytes() {
 size_t product_region_bytes(const npvs_conv_desc& d) {
     if (!has_product_form(d.kind) && d.kind != NPVS_CONV_UP2) return 0;
     if (d.dtype == NPVS_BF16 && bf16_narrow(d.cin, d.cout)) return 0;
-    const int J = d.kind == NPVS_CONV_SUBM3 ? 27 : 8;
+    const int J = map27(d.kind) ? 27 : 8;
     const int rows = d.cap_in > 0 ? d.cap_in : d.cap_out;
     return Arena::round((size_t)rows * J * d.cout * sizeof(float));
 }
@@ -1019,8 +1019,8 @@ float* conv_product_tiles(const npvs_conv_desc& d) {
 TcShape tc_shape(int kind, int cin, int cout, int form) {
     TcShape s;
     s.form = form;
-    if (form == 1) {  // product form of SUBM3 / DOWN2: T = x [W_0 | W_1 | ...]
-        s.J = kind == NPVS_CONV_SUBM3 ? 27 : 8;
+    if (form == 1) {  // product form of SUBM3 / DOWN2 / DOWN3 / UP3: T = x [W_0 | W_1 | ...]
+        s.J = map27(kind) ? 27 : 8;
         s.taps_eff = 1;
         s.Ntot = s.J * cout;
     } else if (kind == NPVS_CONV_UP2) {
@@ -1029,7 +1029,7 @@ TcShape tc_shape(int kind, int cin, int cout, int form) {
         s.Ntot = 8 * cout;
     } else {
         s.J = 1;
-        s.taps_eff = kind == NPVS_CONV_SUBM3 ? 27 : (kind == NPVS_CONV_HEAD1 ? 1 : 8);
+        s.taps_eff = conv_taps(kind);
         s.Ntot = cout;
     }
     s.tma = cin % 32 == 0;
@@ -1114,7 +1114,7 @@ npvs_status conv_tc_fwd(const npvs_conv_desc& d, const void* x, const void* w, c
         p.cap_rows = rows_x;
         p.gmode = sh.tma ? 2 : 0;
         NPVS_TRY(run_gemm(p, sh, d, x, lag, st));
-        const int taps = d.kind == NPVS_CONV_SUBM3 ? 27 : (up ? 0 : 8);
+        const int taps = up ? 0 : conv_taps(d.kind);
         const long long work = (long long)d.cap_out * (d.cout / 4);
         NPVS_REQUIRE(work < (1LL << 31), NPVS_ERR_UNSUPPORTED, "BF16 conv: more than 2^31 output groups");
         const int grid = (int)std::max<long long>(1, std::min<long long>(ceil_div(work, 256), kNumSMs * 8));
@@ -1131,7 +1131,7 @@ npvs_status conv_tc_fwd(const npvs_conv_desc& d, const void* x, const void* w, c
     TcShape sh = tc_shape(d.kind, d.cin, d.cout, 0);
     p.w = (const __nv_bfloat16*)w;
     p.scatter = up;
-    p.taps = (d.kind == NPVS_CONV_SUBM3) ? 27 : (d.kind == NPVS_CONV_DOWN2 ? 8 : 0);
+    p.taps = (map27(d.kind) || d.kind == NPVS_CONV_DOWN2) ? conv_taps(d.kind) : 0;
     p.map = d.map;
     p.map2 = d.map2;
     p.n_rows = up ? d.n_in : d.n_out;
@@ -1154,7 +1154,7 @@ extern "C" size_t npvs_conv_workspace_bytes(const npvs_conv_desc* d) {
 }
 
 extern "C" size_t npvs_packed_weight_bytes(int32_t kind, int32_t cin, int32_t cout) {
-    if (kind < NPVS_CONV_SUBM3 || kind > NPVS_CONV_HEAD1 || cin <= 0 || cout <= 0) return 0;
+    if (!valid_conv_kind(kind) || cin <= 0 || cout <= 0) return 0;
     if (bf16_narrow(cin, cout)) {
         return Arena::round((size_t)conv_taps_host(kind) * cin * cout * sizeof(__nv_bfloat16));
     }
@@ -1167,8 +1167,7 @@ namespace npvs {
 
 npvs_status pack_weights_mode(int kind, int cin, int cout, const float* w, void* packed, int mode, cudaStream_t st) {
     NPVS_REQUIRE(w && packed && cin > 0 && cout > 0, NPVS_ERR_INVALID_ARG, "npvs_pack_weights: bad arguments");
-    NPVS_REQUIRE(kind >= NPVS_CONV_SUBM3 && kind <= NPVS_CONV_HEAD1, NPVS_ERR_UNSUPPORTED,
-                 "npvs_pack_weights: unknown kind");
+    NPVS_REQUIRE(valid_conv_kind(kind), NPVS_ERR_UNSUPPORTED, "npvs_pack_weights: unknown kind");
     if (bf16_narrow(cin, cout)) {
         NPVS_REQUIRE(mode == 0, NPVS_ERR_UNSUPPORTED, "BF16 conv: transposed packing needs cin and cout multiples of 8");
         const size_t total = (size_t)conv_taps_host(kind) * cin * cout;

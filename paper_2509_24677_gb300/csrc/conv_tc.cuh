@@ -4,14 +4,23 @@
 
 namespace npvs {
 
-__device__ __forceinline__ int conv_taps(int kind) {
-    return kind == NPVS_CONV_SUBM3 ? 27 : (kind == NPVS_CONV_HEAD1 ? 1 : 8);
+// Convolutions whose map lists the input row of each of 27 taps per output row ([rows][27]).
+__host__ __device__ __forceinline__ bool map27(int kind) {
+    return kind == NPVS_CONV_SUBM3 || kind == NPVS_CONV_DOWN3 || kind == NPVS_CONV_UP3;
 }
+
+__host__ __device__ __forceinline__ int conv_taps(int kind) {
+    return map27(kind) ? 27 : (kind == NPVS_CONV_HEAD1 ? 1 : 8);
+}
+
+inline bool valid_conv_kind(int kind) { return kind >= NPVS_CONV_SUBM3 && kind <= NPVS_CONV_UP3; }
 
 // Input row feeding output row n through tap t (-1: none).
 __device__ __forceinline__ int gather_row(int kind, const int32_t* __restrict__ map, int n, int t) {
     switch (kind) {
-        case NPVS_CONV_SUBM3: return map[(size_t)n * 27 + t];
+        case NPVS_CONV_SUBM3:
+        case NPVS_CONV_DOWN3:
+        case NPVS_CONV_UP3: return map[(size_t)n * 27 + t];
         case NPVS_CONV_DOWN2: return map[(size_t)n * 8 + t];
         case NPVS_CONV_UP2: {
             int u = map[n];

@@ -18,7 +18,8 @@ from . import _lib as L
 from . import ops
 
 TORCH_DT = {L.F32: torch.float32, L.BF16: torch.bfloat16, L.F64: torch.float64}
-KIND = {"subm3": L.CONV_SUBM3, "down2": L.CONV_DOWN2, "up2": L.CONV_UP2, "head1": L.CONV_HEAD1}
+KIND = {"subm3": L.CONV_SUBM3, "down2": L.CONV_DOWN2, "up2": L.CONV_UP2, "head1": L.CONV_HEAD1,
+        "down3": L.CONV_DOWN3, "up3": L.CONV_UP3}
 
 
 @dataclasses.dataclass

@@ -89,7 +89,8 @@ def test_packed_weight_and_workspace_sizes_of_narrow_bf16_convs():
     from paper_2509_24677_gb300 import _lib as L
     from paper_2509_24677_gb300 import ops
     rnd = lambda b: (b + 255) // 256 * 256
-    for kind, taps in ((L.CONV_SUBM3, 27), (L.CONV_DOWN2, 8), (L.CONV_UP2, 8), (L.CONV_HEAD1, 1)):
+    for kind, taps in ((L.CONV_SUBM3, 27), (L.CONV_DOWN2, 8), (L.CONV_UP2, 8), (L.CONV_HEAD1, 1), (L.CONV_DOWN3, 27),
+                       (L.CONV_UP3, 27)):
         for cin, cout in ((1, 16), (2, 192), (3, 5), (192, 1), (16, 1)):
             assert ops.npvs_packed_weight_bytes(kind, cin, cout) == rnd(taps * cin * cout * 2), (kind, cin, cout)
         assert ops.npvs_packed_weight_bytes(kind, 16, 16) >= taps * 16 * 16 * 2
@@ -98,3 +99,17 @@ def test_packed_weight_and_workspace_sizes_of_narrow_bf16_convs():
     wide = ops.conv_desc(L.CONV_SUBM3, L.BF16, 16, 192, True, None, None, 1000)
     assert ops.npvs_conv_workspace_bytes(narrow) == base
     assert ops.npvs_conv_workspace_bytes(wide) >= base + 1000 * 27 * 192 * 4
+
+
+def test_strided3_sizes_on_host():
+    """DOWN3 / UP3 keep product tiles of 27 taps and a tiled BF16 image at least as large as the
+    plain one; they have no backward (no backward workspace)."""
+    from paper_2509_24677_gb300 import _lib as L
+    from paper_2509_24677_gb300 import ops
+    base = ops.npvs_conv_workspace_bytes(None)
+    for kind in (L.CONV_DOWN3, L.CONV_UP3):
+        d = ops.conv_desc(kind, L.BF16, 32, 64, True, None, None, 500, cap_in=700)
+        assert ops.npvs_conv_workspace_bytes(d) >= base + 700 * 27 * 64 * 4
+        assert ops.npvs_packed_weight_bytes(kind, 32, 64) >= 2 * 27 * 32 * 64 * 2
+        assert ops.npvs_conv_bwd_workspace_bytes(d) == 0
+    assert ops.npvs_packed_weight_bytes(6, 32, 64) == 0

@@ -153,3 +153,73 @@ def test_rulebook_oracle_by_brute_force():
     for n in range(len(c)):
         assert down[up[n] // 8, up[n] % 8] == n
     assert (down >= 0).sum() == len(c)
+
+
+def test_down3_and_up3_equal_strided_convs_with_padding():
+    """k = 3, stride 2, padding 1 and its transpose equal conv3d / conv_transpose3d (output_padding
+    1 restores the even fine size) read at the active sites; the dilated output set is exactly the
+    support of the dense strided conv of a positive input with positive weights."""
+    rng = np.random.default_rng(5)
+    fine, _ = random_level(rng, (2, 6, 4, 8), 0.15)
+    coarse = fine.strided3()
+    cin, cout = 3, 4
+    x = torch.tensor(rng.normal(size=(fine.n, cin)))
+    W = torch.tensor(rng.normal(size=(27, cin, cout)))
+    b = torch.tensor(rng.normal(size=cout))
+    y = N.down3(fine, coarse, x, W, b)
+    wt = W.reshape(3, 3, 3, cin, cout).permute(4, 3, 0, 1, 2)        # out, in, kz, ky, kx
+    ref = F.conv3d(dense_of(fine, x), wt, b, stride=2, padding=1)
+    Q = coarse.coords
+    torch.testing.assert_close(y, ref[Q[:, 0], :, Q[:, 1], Q[:, 2], Q[:, 3]], rtol=1e-12, atol=1e-12)
+    pos = F.conv3d(dense_of(fine, torch.ones(fine.n, 1)), torch.ones(1, 1, 3, 3, 3), stride=2, padding=1)[:, 0]
+    np.testing.assert_array_equal(Q.numpy(), torch.nonzero(pos > 0).numpy())
+    # the dilated set holds the parent set and, where an odd coordinate p has p + 1 < the fine size,
+    # the site (p + 1) / 2 as well
+    assert {tuple(p) for p in fine.parent().coords.tolist()} <= {tuple(q) for q in Q.tolist()}
+    assert coarse.n > fine.parent().n
+    z = torch.tensor(rng.normal(size=(coarse.n, cout)))
+    Wu = torch.tensor(rng.normal(size=(27, cout, cin)))
+    bu = torch.tensor(rng.normal(size=cin))
+    yu = N.up3(coarse, fine, z, Wu, bu)
+    wtu = Wu.reshape(3, 3, 3, cout, cin).permute(3, 4, 0, 1, 2)      # in, out, kz, ky, kx
+    refu = F.conv_transpose3d(dense_of(coarse, z), wtu, bu, stride=2, padding=1, output_padding=1)
+    c = fine.coords
+    torch.testing.assert_close(yu, refu[c[:, 0], :, c[:, 1], c[:, 2], c[:, 3]], rtol=1e-12, atol=1e-12)
+
+
+def test_strided3_rulebook_oracle_by_brute_force():
+    """The dict-built output set equals the max-pool one; down[q][k] and up[p][k] are the rows of
+    every (q, p, k) with p = 2q + k - 1 found by a search over all pairs, and gathering through
+    them reproduces down3 / up3."""
+    from oracle import rulebook as RB
+    rng = np.random.default_rng(6)
+    fine, _ = random_level(rng, (2, 4, 6, 4), 0.2)
+    c = fine.coords.numpy()
+    outs, down, up = RB.strided3_level(c, fine.dims)
+    coarse = fine.strided3()
+    np.testing.assert_array_equal(outs, coarse.coords.numpy())
+    exp_d = np.full_like(down, -1)
+    exp_u = np.full_like(up, -1)
+    for i, q in enumerate(outs):
+        for n, p in enumerate(c):
+            if q[0] != p[0]:
+                continue
+            k = p[1:] - 2 * q[1:] + 1
+            if np.all((k >= 0) & (k <= 2)):
+                t = (k[0] * 3 + k[1]) * 3 + k[2]
+                exp_d[i, t] = n
+                exp_u[n, t] = i
+    np.testing.assert_array_equal(down, exp_d)
+    np.testing.assert_array_equal(up, exp_u)
+    cin, cout = 2, 3
+    x = torch.tensor(rng.normal(size=(fine.n, cin)))
+    W = torch.tensor(rng.normal(size=(27, cin, cout)))
+    b = torch.tensor(rng.normal(size=cout))
+    xz = torch.cat([x, torch.zeros(1, cin)])                            # row -1 -> zeros
+    y = b + sum(xz[torch.tensor(down[:, k])] @ W[k] for k in range(27))
+    torch.testing.assert_close(y, N.down3(fine, coarse, x, W, b), rtol=1e-12, atol=1e-12)
+    z = torch.tensor(rng.normal(size=(coarse.n, cout)))
+    Wu = torch.tensor(rng.normal(size=(27, cout, cin)))
+    zz = torch.cat([z, torch.zeros(1, cout)])
+    yu = b[:cin] + sum(zz[torch.tensor(up[:, k])] @ Wu[k] for k in range(27))
+    torch.testing.assert_close(yu, N.up3(coarse, fine, z, Wu, b[:cin]), rtol=1e-12, atol=1e-12)
