@@ -216,11 +216,13 @@ def make_frame_inputs(device):
 def cpu_oracle_frame_estimate(budget_s: float):
     """Times the FP64 oracle on a bounded sample of one frame of the same workload: the
     froxelization of a random sample of froxel columns (scaled to the whole grid) plus interleave,
-    network and de-interleave of the full frame (on G from a one-ray-per-column raster). Returns
-    (ms per frame, description, cores, seconds spent, ms per stage)."""
+    network and de-interleave of the full frame (on G from a one-ray-per-column raster), and, apart
+    from the frame, the training loss on the frame's logits (G standing in for the ground truth).
+    Returns (ms per frame, description, cores, seconds spent, ms per stage)."""
     from oracle import camera as ocam
     from oracle import froxel as ofx
     from oracle import interleave as oil
+    from oracle import loss as oloss
     from oracle import network as onet
     wl = I.workload(WORKLOAD)
     boxes = I.city_boxes(0)
@@ -240,6 +242,9 @@ def cpu_oracle_frame_estimate(budget_s: float):
     t3 = time.perf_counter()
     oil.pvs_from_logits(coords, logits, G1, wl.W, wl.d)
     t4 = time.perf_counter()
+    with torch.no_grad():
+        oloss.loss_terms(torch.from_numpy(logits), coords, G1, G1, wl.W, wl.d)
+    t_loss = time.perf_counter() - t4
     t_rest = t4 - t1
     # froxel columns at full supersampling, sized to the remaining budget
     probe = 256
@@ -257,8 +262,36 @@ def cpu_oracle_frame_estimate(budget_s: float):
     desc = (f"FP64/binary32-mirror oracle: froxelization of {n_cols} of {wl.W * wl.H} froxel columns "
             f"(s=8, scaled to the grid) + interleave, U-Net and de-interleave of one full frame")
     stages = {"froxelize": 1e3 * t_frox, "interleave": 1e3 * (t2 - t1), "rulebooks+network": 1e3 * (t3 - t2),
-              "deinterleave": 1e3 * (t4 - t3)}
-    return ms, desc, os.cpu_count(), t_cols + t_rest + (t1 - t0), {k: round(v, 1) for k, v in stages.items()}
+              "deinterleave": 1e3 * (t4 - t3), "loss (training, not in the frame)": 1e3 * t_loss}
+    return ms, desc, os.cpu_count(), t_cols + t_rest + (t1 - t0) + t_loss, {k: round(v, 1) for k, v in stages.items()}
+
+
+def cpu_oracle_single_thread(budget_s: float):
+    """cpu_oracle_frame_estimate with one thread (OMP_NUM_THREADS=1 for the C oracle, one torch
+    thread) in a child process. Returns (ms per frame, ms per stage), or None if the child fails."""
+    code = ("import json, torch; torch.set_num_threads(1); import bench; "
+            f"r = bench.cpu_oracle_frame_estimate({float(budget_s)!r}); print(json.dumps([r[0], r[4]]))")
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                             timeout=max(120.0, 10 * budget_s))
+        ms, stages = json.loads(out.stdout.strip().splitlines()[-1])
+        return float(ms), stages
+    except Exception:
+        return None
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), else the machine type."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
 
 
 def run_reference(args):
@@ -770,7 +803,12 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cms, desc, cores, spent, cstages = cpu_oracle_frame_estimate(args.cpu_seconds)
         line["cpu_baseline"] = {"value": round(1000.0 / cms, 5), "unit": "frames/s", "cores": cores, "kind": "oracle",
-                                "sample": desc, "seconds": round(spent, 1), "stage_ms": cstages}
+                                "sample": desc, "seconds": round(spent, 1), "stage_ms": cstages,
+                                "cpu_model": cpu_model()}
+        single = cpu_oracle_single_thread(max(4.0, args.cpu_seconds / 2))
+        if single is not None:
+            line["cpu_baseline"]["single_thread"] = {"value": round(1000.0 / single[0], 5), "unit": "frames/s",
+                                                     "threads": 1, "stage_ms": single[1]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
