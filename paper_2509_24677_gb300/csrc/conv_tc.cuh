@@ -35,7 +35,7 @@ __device__ __forceinline__ int gather_row(int kind, const int32_t* __restrict__ 
 inline bool bf16_narrow(int cin, int cout) { return cin % 8 != 0 || cout % 8 != 0; }
 
 // GEMM view of a convolution: rows x (Kflat = taps_eff * cin) x Ntot.
-//   G-form (SUBM3, DOWN2, HEAD1): row = output row, k = tap * cin + ci, n = co.
+//   G-form (SUBM3, DOWN2, HEAD1, DOWN3, UP3): row = output row, k = tap * cin + ci, n = co.
 //   S-form (UP2): row = coarse input row, k = ci, n = child_tap * cout + co; the epilogue scatters
 //   column block child_tap to the child's row (down map).
 struct TcShape {
