@@ -66,6 +66,43 @@ class Params:
         return [buf[ob:ob + l.cout] for l, (_, _, ob) in zip(self.layers, self.offsets)]
 
 
+CHECKPOINT_FORMAT = "npvs-trainer-1"
+
+
+def _layer_key(layers):
+    return [(l.name, l.kind, int(l.cin), int(l.cout), bool(l.relu)) for l in layers]
+
+
+def trainer_state(tr) -> dict:
+    """Checkpoint of a Trainer as host tensors (for torch.save): the layer list and dtype (checked
+    on load), the master parameters, Adam's moments and its device counters, and the forward's
+    tuned kernel forms. With the data sampler's state kept by the caller, a resumed run repeats
+    the uninterrupted one bit for bit (every step is deterministic)."""
+    return {"format": CHECKPOINT_FORMAT, "layers": _layer_key(tr.layers), "dtype": int(tr.dtype),
+            "theta": tr.params.theta.detach().cpu().clone(), "m": tr.m.detach().cpu().clone(),
+            "v": tr.v.detach().cpu().clone(), "adam_state": tr.adam_state.detach().cpu().clone(),
+            "tuned": tr.pipe.tuned_configs()}
+
+
+def load_trainer_state(tr, sd: dict):
+    """Restores trainer_state() into `tr` in place (every buffer keeps its address, so a graph of
+    tr captured earlier replays with the restored parameters; capture again if the tuned forms
+    differ) and rebuilds the BF16 weight images. Raises ValueError for another network or dtype."""
+    if sd.get("format") != CHECKPOINT_FORMAT:
+        raise ValueError(f"not a trainer checkpoint ({sd.get('format')!r})")
+    if [tuple(x) for x in sd["layers"]] != _layer_key(tr.layers) or int(sd["dtype"]) != int(tr.dtype):
+        raise ValueError("checkpoint of another network or dtype")
+    for name, dst in (("theta", tr.params.theta), ("m", tr.m), ("v", tr.v), ("adam_state", tr.adam_state)):
+        src = sd[name]
+        if tuple(src.shape) != tuple(dst.shape) or src.dtype != dst.dtype:
+            raise ValueError(f"checkpoint tensor {name}: {tuple(src.shape)} {src.dtype}, "
+                             f"expected {tuple(dst.shape)} {dst.dtype}")
+        dst.copy_(src)
+    tr.pipe.apply_tuned(sd["tuned"])
+    if tr.dtype == L.BF16:
+        tr.repack()
+
+
 class Trainer:
     """Buffers and launch sequence of one training step of `layers` on batches of `batch`
     viewcells of workload `wl`."""
@@ -113,6 +150,12 @@ class Trainer:
                 self.packed.append(torch.empty(ops.npvs_packed_weight_bytes(KIND[l.kind], l.cin, l.cout),
                                                dtype=torch.uint8, device=device))
             self.repack()
+
+    def state_dict(self) -> dict:
+        return trainer_state(self)
+
+    def load_state_dict(self, sd: dict):
+        load_trainer_state(self, sd)
 
     def autotune(self, boxes, box_offsets, cams_dev, reps: int = 3):
         """Per-layer kernel configurations of the forward convolutions, timed on this batch (see

@@ -8,6 +8,13 @@ Data (seeded, synthetic): 4 cities, 64 training and 16 held-out street viewcells
 city; ground truth from 256 viewpoints per cell by GPU ray casting, ANDed with G. Batches of 8 cells
 are drawn with a seeded sampler; every step is one replay of the captured training step (BF16
 forward/backward, FP32 master weights, Adam). Prints one JSON line.
+
+    --log steps.jsonl            one JSON line per --log-every steps (loss and its mean terms)
+    --save ck.pt                 checkpoint at the end: trainer state, sampler state, step count
+    --resume ck.pt --steps N     continue to N steps in all, with the checkpoint's parameters, Adam
+                                 state, sampler state and kernel forms (same data flags); every step
+                                 is deterministic, so this repeats the uninterrupted run's steps
+                                 whenever that run used the same kernel forms
 """
 from __future__ import annotations
 
@@ -43,6 +50,10 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--w-bce", type=float, default=1.0)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--log", default=None, help="append one JSON line per logged step to this file")
+    ap.add_argument("--log-every", type=int, default=100)
+    ap.add_argument("--save", default=None, help="write a checkpoint here after the last step")
+    ap.add_argument("--resume", default=None, help="continue from a checkpoint written by --save")
     a = ap.parse_args(argv)
     dev = "cuda"
     wl = I.workload("city256")
@@ -85,18 +96,43 @@ def main(argv=None):
         cams.view(B, -1).copy_(cams_all[ids])
         tr.gt.view(B, -1).copy_(gts[ids])
 
+    done = 0                           # steps taken before this run
+    if a.resume:
+        ck = torch.load(a.resume, map_location="cpu", weights_only=False)
+        tr.load_state_dict(ck["trainer"])  # parameters, Adam state and the tuned kernel forms
+        rng.bit_generator.state = ck["rng"]
+        done = int(ck["step"])
+        if done >= a.steps:
+            raise SystemExit(f"the checkpoint is at step {done}; ask for more --steps")
     load(list(rng.choice(train_idx, B, replace=False)))
-    tr.autotune(boxes, offs, cams)     # forward kernel forms for this batch size (no parameter update)
-    g = tr.capture(boxes, offs, cams)
+    if not a.resume:
+        tr.autotune(boxes, offs, cams)  # forward kernel forms for this batch size (no parameter update)
+    g = tr.capture(boxes, offs, cams)  # its warm-up is step done + 1
     torch.cuda.synchronize()
+    log_f = open(a.log, "a") if a.log else None
+
+    def log_step(n):
+        t = tr.terms.double().mean(0).tolist()
+        log_f.write(json.dumps({"step": n, "loss": float(tr.loss.item()), "dice": t[L.LT_DICE],
+                                "attr": t[L.LT_ATTR], "rep": t[L.LT_REP], "bce": t[L.LT_BCE]}) + "\n")
+
+    if log_f and (done + 1) % a.log_every == 0:
+        log_step(done + 1)
     losses = []
     t1 = time.perf_counter()
-    for step in range(1, a.steps):
+    for step in range(done + 1, a.steps):
         load(list(rng.choice(train_idx, B, replace=False)))
         g.replay()
         if step % 100 == 0 or step == a.steps - 1:
             losses.append((step + 1, round(float(tr.loss.item()), 5)))
+        if log_f and ((step + 1) % a.log_every == 0 or step == a.steps - 1):
+            log_step(step + 1)
     torch.cuda.synchronize()
+    if log_f:
+        log_f.close()
+    if a.save:
+        torch.save({"trainer": tr.state_dict(), "rng": rng.bit_generator.state, "step": a.steps, "args": vars(a)},
+                   a.save)
     t_train = time.perf_counter() - t1
     if ops.npvs_check_status(tr.pipe.status) != 0:
         raise RuntimeError("device status set during training")
@@ -114,9 +150,9 @@ def main(argv=None):
         fp += _popcount(nf.pvs & ~gt)
         gtp += _popcount(gt)
         occ += _popcount(nf.occ)
-    out = {"steps": a.steps, "batch": B, "train_cells": len(train_idx), "eval_cells": len(eval_idx),
+    out = {"steps": a.steps, "resumed_at": done, "batch": B, "train_cells": len(train_idx), "eval_cells": len(eval_idx),
            "gt_points": a.points, "lr": a.lr, "w_bce": a.w_bce, "data_seconds": round(t_data, 1),
-           "train_seconds": round(t_train, 1), "steps_per_s": round((a.steps - 1) / t_train, 1),
+           "train_seconds": round(t_train, 1), "steps_per_s": round((a.steps - 1 - done) / max(t_train, 1e-9), 1),
            "loss_curve": losses, "eval": {"FNR": round(fn / max(gtp, 1), 5), "FPR": round(fp / max(gtp, 1), 5),
                                           "GTP": gtp, "G_froxels": occ,
                                           "G_over_GT": round(occ / max(gtp, 1), 3)}}

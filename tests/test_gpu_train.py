@@ -636,3 +636,54 @@ def test_train_eval_runs_small(capsys):
     out = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert out["eval_cells"] == 4 and out["eval"]["GTP"] > 0
     assert 0.0 <= out["eval"]["FNR"] <= 1.0
+
+
+def test_checkpoint_resume_is_bit_identical(tmp_path):
+    """A trainer saved after 3 steps and loaded into another trainer (other parameters, fresh Adam
+    state) continues, 3 steps later, bitwise as the uninterrupted trainer after 6 steps."""
+    L, ops, P = lib()
+    wl = I.workload("plain64")
+    tr1, inp, _, _, _, _ = make_trainer(wl, L.F32)
+    for _ in range(3):
+        tr1.step(*inp)
+    path = tmp_path / "ck.pt"
+    torch.save({"trainer": tr1.state_dict()}, path)
+    for _ in range(3):
+        tr1.step(*inp)
+    tr2, inp2, _, _, _, _ = make_trainer(wl, L.F32)
+    tr2.params.theta.add_(0.25)
+    sd = torch.load(path, map_location="cpu", weights_only=False)["trainer"]
+    tr2.load_state_dict(sd)
+    assert tr2.adam_state[0].item() == 3
+    for _ in range(3):
+        tr2.step(*inp2)
+    torch.cuda.synchronize()
+    assert torch.equal(tr1.params.theta, tr2.params.theta)
+    assert torch.equal(tr1.m, tr2.m) and torch.equal(tr1.v, tr2.v)
+    assert torch.equal(tr1.adam_state, tr2.adam_state)
+    bad = dict(sd, layers=sd["layers"][:-1])
+    with pytest.raises(ValueError):
+        tr2.load_state_dict(bad)
+
+
+def test_train_eval_save_resume_and_log(tmp_path, capsys):
+    """The training driver writes a checkpoint and a JSONL log, and resumes from the checkpoint to
+    the requested step count."""
+    import json
+    from paper_2509_24677_gb300 import train_eval
+    small = ["--train-per-scene", "2", "--eval-per-scene", "1", "--points", "16", "--log-every", "1"]
+    ck, ck2, log = tmp_path / "a.pt", tmp_path / "b.pt", tmp_path / "steps.jsonl"
+    train_eval.main(["--steps", "2", "--save", str(ck), "--log", str(log)] + small)
+    capsys.readouterr()
+    train_eval.main(["--steps", "4", "--resume", str(ck), "--save", str(ck2), "--log", str(log)] + small)
+    out = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert out["resumed_at"] == 2 and out["steps"] == 4
+    a = torch.load(ck, map_location="cpu", weights_only=False)
+    b = torch.load(ck2, map_location="cpu", weights_only=False)
+    assert a["step"] == 2 and b["step"] == 4
+    assert int(a["trainer"]["adam_state"][0]) == 2 and int(b["trainer"]["adam_state"][0]) == 4
+    assert b["trainer"]["tuned"] == a["trainer"]["tuned"]
+    assert not torch.equal(a["trainer"]["theta"], b["trainer"]["theta"])
+    recs = [json.loads(x) for x in log.read_text().splitlines()]
+    assert [r["step"] for r in recs] == [1, 2, 3, 4]
+    assert all(np.isfinite(r["loss"]) for r in recs)
