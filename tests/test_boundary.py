@@ -113,3 +113,36 @@ def test_strided3_sizes_on_host():
         assert ops.npvs_packed_weight_bytes(kind, 32, 64) >= 2 * 27 * 32 * 64 * 2
         assert ops.npvs_conv_bwd_workspace_bytes(d) == 0
     assert ops.npvs_packed_weight_bytes(6, 32, 64) == 0
+
+
+def test_argument_errors_of_the_strided3_entry_points_on_host():
+    """The DOWN3 rulebook and the DOWN3 / UP3 convolutions validate their arguments before touching
+    the device: the documented status comes back (with a message) on a machine without a GPU. The
+    pointers are placeholders that the library must not dereference on these paths."""
+    import ctypes
+    from paper_2509_24677_gb300 import _lib as L
+    lib = L.load()
+    fake = ctypes.c_void_p(256)
+
+    def level(X, Y, Z, B, cap):
+        return L.Level(L.Dims(X, Y, Z, B), cap, fake, fake, fake)
+
+    fine, coarse = level(8, 6, 4, 1, 192), level(4, 3, 2, 1, 24)
+    ws = lib.npvs_rulebook_workspace_bytes(coarse.dims)
+    rb = lambda kind, a, b, m2, nbytes: lib.npvs_build_rulebook(kind, ctypes.byref(a), ctypes.byref(b), fake, m2,
+                                                                  None, fake, nbytes, None)
+    assert rb(L.RB_DOWN3, fine, coarse, None, ws) == L.ERR_INVALID_ARG          # no transposed map
+    assert lib.npvs_last_error().decode().startswith("npvs_build_rulebook")
+    assert rb(L.RB_DOWN3, fine, level(4, 3, 3, 1, 36), fake, ws) == L.ERR_UNSUPPORTED   # not halved
+    assert rb(L.RB_DOWN3, fine, coarse, fake, ws - 1) == L.ERR_WORKSPACE
+    assert rb(7, fine, coarse, fake, ws) == L.ERR_UNSUPPORTED
+    n = ctypes.c_void_p(512)
+    for kind in (L.CONV_DOWN3, L.CONV_UP3):
+        d = L.ConvDesc(kind, L.F32, 16, 16, 1, 0, fake, None, n, 24, None, 0)   # no n_in / cap_in
+        assert lib.npvs_sparse_conv_fwd(ctypes.byref(d), fake, fake, None, None, fake, None) == L.ERR_INVALID_ARG
+        d.n_in, d.cap_in = n, 192
+        assert lib.npvs_sparse_conv_bwd(ctypes.byref(d), fake, fake, fake, fake, None, None, fake, None, fake,
+                                        1 << 20, None) == L.ERR_UNSUPPORTED
+        assert "forward only" in lib.npvs_last_error().decode()
+    d = L.ConvDesc(9, L.F32, 16, 16, 1, 0, fake, None, n, 24, n, 24)
+    assert lib.npvs_sparse_conv_fwd(ctypes.byref(d), fake, fake, None, None, fake, None) == L.ERR_UNSUPPORTED
