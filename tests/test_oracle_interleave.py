@@ -17,7 +17,7 @@ def test_bit_layout():
     np.testing.assert_array_equal(IL.unpack_bits(bits, 64), dense)
 
 
-@pytest.mark.parametrize("d", [1, 2, 4])
+@pytest.mark.parametrize("d", [1, 2, 4, 8, 32])
 def test_roundtrip_and_bijection(d):
     rng = np.random.default_rng(d)
     B, D, H, W = 2, 2 * d, 3 * d, 2 * d
