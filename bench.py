@@ -77,6 +77,15 @@ def max_over_ranks(x: float, device) -> float:
     return float(t.item())
 
 
+def step_quantiles(times_ms) -> dict:
+    """Median and 99th percentile (nearest rank) of per-step times in milliseconds."""
+    t = sorted(float(x) for x in times_ms)
+    if not t:
+        return {"p50": None, "p99": None}
+    p99 = t[min(len(t) - 1, max(0, -(-99 * len(t) // 100) - 1))]
+    return {"p50": round(statistics.median(t), 4), "p99": round(p99, 4)}
+
+
 def replica_rate(world: int, units_per_rank: float, ms_per_step: float) -> float:
     """Whole-job throughput of `world` replicas that each process `units_per_rank` units per step
     in `ms_per_step` milliseconds (the slowest rank's time)."""
@@ -765,6 +774,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": round(replica_rate(world, 1, ms), 3), "unit": "frames/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
+        "ms_per_step_quantiles": step_quantiles(t_bf16),
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {"workload": "city256: 256x256x128 froxels (s=8), 2,001-box procedural city seed 0, "
                                f"{N_VIEWCELLS} street viewcells cycled, d=4 (128 ch), sparse U-Net 32/64/128/256",

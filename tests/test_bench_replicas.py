@@ -73,3 +73,10 @@ def test_tuned_labels_and_traffic_selection():
     assert bench.conv_frame_traffic({k: (win3, 1.0) for k in l1}) is None
     mixed = {k: (prod if k == "enc1a" else win, 1.0) for k in l1}
     assert bench.conv_frame_traffic(mixed) is None
+
+
+def test_step_quantiles_nearest_rank():
+    import bench
+    assert bench.step_quantiles([1.0] * 98 + [2.0, 3.0]) == {"p50": 1.0, "p99": 2.0}
+    assert bench.step_quantiles(range(1, 51)) == {"p50": 25.5, "p99": 50.0}
+    assert bench.step_quantiles([]) == {"p50": None, "p99": None}
