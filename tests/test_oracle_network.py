@@ -223,3 +223,88 @@ def test_strided3_rulebook_oracle_by_brute_force():
     zz = torch.cat([z, torch.zeros(1, cout)])
     yu = b[:cin] + sum(zz[torch.tensor(up[:, k])] @ Wu[k] for k in range(27))
     torch.testing.assert_close(yu, N.up3(coarse, fine, z, Wu, b[:cin]), rtol=1e-12, atol=1e-12)
+
+
+def test_unet_wiring_equals_dense_straight_line_composition():
+    """Pin of the U-Net composition in `forward` (Sec. 3.3 f_theta on the interleaved grid; the
+    U-Net reading: stem, per level two SubM3 then a stride-2 down conv, per decoder level the
+    transposed up conv with ReLU, the encoder level's output added after that ReLU, two SubM3, a
+    1x1 head without ReLU). The same network is written out a second way: dense conv3d /
+    conv_transpose3d on the zero-filled grid, every layer's output multiplied by its level's
+    active mask, the level masks from max-pooling the level-0 indicator (not from Level.parent),
+    and the skip wiring as straight-line code. Every layer output kept by `forward` must equal
+    the dense one at the active sites. A skip taken one layer early, a level pairing off by one
+    or a ReLU on the head would fail here."""
+    rng = np.random.default_rng(11)
+    dims = (2, 8, 8, 8)
+    lv0, m = random_level(rng, dims, 0.3)
+    layers = I.unet_layers(5, [4, 6, 8], 8)
+    ws, bs = I.kaiming_uniform(layers, seed=3, bias_scale=0.2)
+    W, B = N.to_torch_params(ws, bs)
+    x = torch.tensor(rng.normal(size=(lv0.n, 5)))
+    levels = N.build_levels(lv0.coords.numpy(), dims, 3)
+    keep = {}
+    out = N.forward(layers, W, B, levels, x, keep=keep)
+
+    P = {l.name: (W[i], B[i]) for i, l in enumerate(layers)}
+    m0 = torch.tensor(m, dtype=torch.float64).unsqueeze(1)                  # B, 1, D, H, W
+    m1 = F.max_pool3d(m0, kernel_size=2, stride=2)
+    m2 = F.max_pool3d(m1, kernel_size=2, stride=2)
+
+    def k3(name):
+        w, b = P[name]
+        return w.reshape(3, 3, 3, w.shape[1], w.shape[2]).permute(4, 3, 0, 1, 2), b
+
+    def sub(name, a, mask, relu=True):
+        w, b = k3(name)
+        y = F.conv3d(a, w, b, padding=1)
+        return (torch.relu(y) if relu else y) * mask
+
+    def down(name, a, mask):
+        w, b = P[name]
+        wt = w.reshape(2, 2, 2, w.shape[1], w.shape[2]).permute(4, 3, 0, 1, 2)
+        return torch.relu(F.conv3d(a, wt, b, stride=2)) * mask
+
+    def up(name, a, mask):
+        w, b = P[name]
+        wt = w.reshape(2, 2, 2, w.shape[1], w.shape[2]).permute(3, 4, 0, 1, 2)
+        return torch.relu(F.conv_transpose3d(a, wt, b, stride=2)) * mask
+
+    x0 = dense_of(lv0, x)
+    D = {}
+    D["stem"] = sub("stem", x0, m0)
+    D["enc0a"] = sub("enc0a", D["stem"], m0)
+    D["enc0b"] = sub("enc0b", D["enc0a"], m0)
+    D["down0"] = down("down0", D["enc0b"], m1)
+    D["enc1a"] = sub("enc1a", D["down0"], m1)
+    D["enc1b"] = sub("enc1b", D["enc1a"], m1)
+    D["down1"] = down("down1", D["enc1b"], m2)
+    D["enc2a"] = sub("enc2a", D["down1"], m2)
+    D["enc2b"] = sub("enc2b", D["enc2a"], m2)
+    D["up1"] = up("up1", D["enc2b"], m1)
+    D["up1+skip"] = D["up1"] + D["enc1b"]
+    D["dec1a"] = sub("dec1a", D["up1+skip"], m1)
+    D["dec1b"] = sub("dec1b", D["dec1a"], m1)
+    D["up0"] = up("up0", D["dec1b"], m0)
+    D["up0+skip"] = D["up0"] + D["enc0b"]
+    D["dec0a"] = sub("dec0a", D["up0+skip"], m0)
+    D["dec0b"] = sub("dec0b", D["dec0a"], m0)
+    wh, bh = P["head"]
+    D["head"] = F.conv3d(D["dec0b"], wh.reshape(1, 1, 1, wh.shape[1], wh.shape[2]).permute(4, 3, 0, 1, 2), bh) * m0
+
+    lvl = {n: 0 for n in ("stem", "enc0a", "enc0b", "up0", "up0+skip", "dec0a", "dec0b", "head")}
+    lvl.update({n: 1 for n in ("down0", "enc1a", "enc1b", "up1", "up1+skip", "dec1a", "dec1b")})
+    lvl.update({n: 2 for n in ("down1", "enc2a", "enc2b")})
+    assert set(keep) == set(D) == set(lvl)
+    for i, mk in enumerate((m0, m1, m2)):          # the level sets themselves
+        np.testing.assert_array_equal(levels[i].coords.numpy(), torch.nonzero(mk[:, 0] > 0).numpy())
+    for name, dense in D.items():
+        c = levels[lvl[name]].coords
+        ref = dense[c[:, 0], :, c[:, 1], c[:, 2], c[:, 3]]
+        assert keep[name].shape == ref.shape, name
+        assert float(ref.abs().max()) > 0, name
+        torch.testing.assert_close(keep[name], ref, rtol=1e-12, atol=1e-12, msg=name)
+    torch.testing.assert_close(out, D["head"][lv0.coords[:, 0], :, lv0.coords[:, 1], lv0.coords[:, 2],
+                                              lv0.coords[:, 3]], rtol=1e-12, atol=1e-12)
+    # the dense composition gives zero outside the level-0 set
+    assert float((D["head"] * (1 - m0)).abs().max()) == 0.0
