@@ -193,6 +193,19 @@ unsigned long long npvs_launch_count(void);
  * NPVS_OK if it was 0, else the lowest status whose bit was set. */
 npvs_status npvs_check_status(int32_t* status, void* stream);
 
+/* Bound of the waits inside the tensor-core kernels (the BF16 convolutions of npvs_sparse_conv_fwd /
+ * npvs_forward and the BF16 weight gradient of npvs_sparse_conv_bwd), in SM clock cycles, for every
+ * kernel launched after the call (a CUDA graph keeps the bound it was captured with); the paper has
+ * no counterpart. cycles = 0 restores the default (4e9 cycles, about 2 s at the maximum SM clock);
+ * the previous bound is stored in *previous (nullable). A wait that outlasts the bound makes its CTA
+ * stop issuing copies and MMAs, wait (at most ~1e7 SM cycles more per outstanding stage, whatever the
+ * bound) for those already in flight, free its tensor memory and return; NPVS_ERR_TIMEOUT is OR-ed
+ * into the convolution's status word. The outputs of a timed-out call are undefined, and a
+ * convolution workspace it used must be zero-filled again before its next use. A small bound
+ * (hundreds of cycles) makes ordinary waits expire: that is how the timeout path is tested.
+ * Returns NPVS_ERR_INVALID_ARG for cycles < 0. */
+npvs_status npvs_set_wait_limit(int64_t cycles, int64_t* previous);
+
 /* ---- a1: frustum setup (host) --------------------------------------------------------------- */
 
 /* Sec. 3.2 first paragraph: c' = c - fwd * (h / tan(theta/2) + h) for a cube viewcell of
@@ -262,7 +275,10 @@ npvs_status npvs_interleave(const uint32_t* occ_bits, npvs_grid grid, int32_t d,
  *  - Limit: B * (W/d) * (H/d) * (D/d) <= 4,194,304 coarse sites; larger grids return
  *    NPVS_ERR_UNSUPPORTED with a message (use npvs_interleave and a workspace).
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
- *    device current; make that first call before any stream capture on the device.
+ *    device current; make that first call before any stream capture on the device. The address is
+ *    cached per device and per CUDA context: after a device reset (cudaDeviceReset, which replaces
+ *    the primary context) the next call looks it up again, so that call too belongs before any
+ *    capture.
  *  - All calls on a device share the one array and it keeps the last call's contents; no part of it
  *    needs to start at zero (each call rewrites what it reads), but calls that overlap on the GPU (e.g.
  *    from two streams at once) race on it and must be serialised by the caller. */

@@ -89,6 +89,7 @@ SIGNATURES = {
     "npvs_version": (ctypes.c_char_p, []),
     "npvs_launch_count": (ctypes.c_ulonglong, []),
     "npvs_check_status": (I32, [P, P]),
+    "npvs_set_wait_limit": (I32, [ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "npvs_camera_setup": (I32, [ctypes.POINTER(Viewcell), I32, ctypes.POINTER(Camera)]),
     "npvs_froxelize_workspace_bytes": (SZ, [I32]),
     "npvs_froxelize": (I32, [P, P, I32, P, Grid, I32, P, P, SZ, P]),

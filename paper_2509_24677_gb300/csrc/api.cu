@@ -1,4 +1,6 @@
 // Status/error entry points, the host-side frustum setup (a1) and the shared scan kernel.
+#include <cuda.h>
+
 #include <atomic>
 #include <cmath>
 #include <cstdlib>
@@ -10,6 +12,9 @@ namespace npvs {
 
 static thread_local char g_err[512] = "";
 static std::atomic<unsigned long long> g_launches{0};
+static std::atomic<long long> g_wait_limit{kDefaultWaitCycles};
+
+long long wait_limit_cycles() { return g_wait_limit.load(std::memory_order_relaxed); }
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
@@ -26,6 +31,53 @@ void set_error(const char* fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(g_err, sizeof(g_err), fmt, ap);
     va_end(ap);
+}
+
+namespace {
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+template <typename Fn>
+Fn driver_fn(const char* name) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(name, &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+        return reinterpret_cast<Fn>(f);
+    return nullptr;
+}
+}  // namespace
+
+unsigned long long current_context_id() {
+    static const CtxGetCurrentFn get_current = driver_fn<CtxGetCurrentFn>("cuCtxGetCurrent");
+    static const CtxGetIdFn get_id = driver_fn<CtxGetIdFn>("cuCtxGetId");
+    if (!get_current || !get_id) return 0;
+    CUcontext c = nullptr;
+    if (get_current(&c) != CUDA_SUCCESS || c == nullptr) return 0;
+    unsigned long long id = 0;
+    if (get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+npvs_status ensure_dynamic_smem(const void* kernel, int bytes, std::atomic<unsigned long long>* seen,
+                                const char* what) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        set_error("%s: cudaGetDevice: %s", what, cudaGetErrorString(e));
+        return NPVS_ERR_CUDA;
+    }
+    const bool slot = dev >= 0 && dev < kMaxDevices;
+    unsigned long long id = current_context_id();
+    if (slot && id != 0 && seen[dev].load(std::memory_order_acquire) == id) return NPVS_OK;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) {
+        set_error("%s: cudaFuncSetAttribute: %s", what, cudaGetErrorString(e));
+        return NPVS_ERR_CUDA;
+    }
+    if (id == 0) id = current_context_id();  // the runtime call above made the primary context current
+    if (slot) seen[dev].store(id, std::memory_order_release);
+    return NPVS_OK;
 }
 
 // One CTA of 1024 threads scans n block counts in chunks of 1024.
@@ -67,6 +119,13 @@ extern "C" const char* npvs_last_error(void) { return g_err; }
 extern "C" const char* npvs_version(void) { return "npvs 0.1 (sm_103a)"; }
 
 extern "C" unsigned long long npvs_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+extern "C" npvs_status npvs_set_wait_limit(int64_t cycles, int64_t* previous) {
+    NPVS_REQUIRE(cycles >= 0, NPVS_ERR_INVALID_ARG, "npvs_set_wait_limit: cycles < 0");
+    const long long old = g_wait_limit.exchange(cycles > 0 ? (long long)cycles : kDefaultWaitCycles);
+    if (previous) *previous = old;
+    return NPVS_OK;
+}
 
 extern "C" npvs_status npvs_check_status(int32_t* status, void* stream) {
     NPVS_REQUIRE(status != nullptr, NPVS_ERR_INVALID_ARG, "npvs_check_status: status is NULL");

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 #include <utility>
 #include <cstdarg>
 #include <cstdio>
@@ -48,6 +49,25 @@ inline npvs_status check_launch(const char* what) {
     } while (0)
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Identifier of the CUDA context current on the calling thread, 0 if there is none or the driver
+// cannot say (cuCtxGetCurrent / cuCtxGetId, reached through the runtime's entry-point query so that
+// the library does not link libcuda). Ids are unique within a process and never reused: a cache
+// keyed on one is refreshed after a device reset, which replaces the primary context.
+unsigned long long current_context_id();
+
+constexpr int kMaxDevices = 64;
+
+// Bound, in SM clock cycles, of every mbarrier wait in the tensor-core kernels launched from now on
+// (npvs_set_wait_limit; default kDefaultWaitCycles, about 2 s at the maximum SM clock).
+constexpr long long kDefaultWaitCycles = 4000000000ll;
+long long wait_limit_cycles();
+
+// Raises `kernel`'s dynamic shared-memory limit to `bytes` in the current context. `seen` (one
+// slot per device ordinal, kMaxDevices) remembers the context in which it was last raised, so the
+// attribute is set once per context; concurrent first calls may both set it, which is harmless.
+npvs_status ensure_dynamic_smem(const void* kernel, int bytes, std::atomic<unsigned long long>* seen,
+                                const char* what);
 
 // Every kernel of the library is launched with programmatic stream serialisation: the next kernel
 // on the stream may be launched and scheduled while this one finishes. Each kernel therefore

@@ -72,6 +72,7 @@ struct TcParams {
     int max_split;   // upper bound of the k-split factor
     float* part;     // split-K partial tiles [kSplitSlots][128][BN] (nullable: no split)
     int* counters;   // split-K arrival counters [4 * kSplitSlots], zero between launches
+    long long wait_limit;  // bound of every mbarrier wait, SM cycles (npvs_set_wait_limit)
 };
 
 // Shared-memory matrix descriptor of a K-major operand with rows of RB bytes (128: 128-byte
@@ -100,6 +101,28 @@ __host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
 }
 
 // ---- the kernel -----------------------------------------------------------------------------
+
+// Teardown of the gather warps in the modes where several warps issue copies that complete on one
+// stage barrier (TMA gather4, window gather). After a timeout the warps may have stopped at
+// different iterations, so the drain must cover the last S stages of the furthest one: every
+// warp publishes its iteration count, the gather warps meet at hardware named barrier 1 (each of
+// them reaches it: their loops hold bounded waits only), and thread 0 waits for those stages. A
+// stage that a stopped warp never armed completely gives up after kDrainCycles (~10 ms), long
+// after any copy issued before the named barrier has landed. Without a timeout every warp ran
+// the same iterations and this is the plain wait for the last S stages.
+__device__ __forceinline__ void gather_teardown(uint32_t it, volatile int* warp_its, int PW, int warp, int lane,
+                                                uint32_t full0, int S, volatile int* abort_flag, long long limit) {
+    if (lane == 0) warp_its[warp] = (int)it;
+    __syncwarp();
+    asm volatile("bar.sync 1, %0;" ::"r"(PW * 32) : "memory");
+    if (warp == 0 && lane == 0) {
+        uint32_t hi = 0;
+        for (int w = 0; w < PW; ++w) hi = max(hi, (uint32_t)warp_its[w]);
+        for (uint32_t j = hi >= (uint32_t)S ? hi - S : 0; j < hi; ++j)
+            mbar_wait(full0 + 8 * (j % S), (j / S) & 1, abort_flag, limit);
+    }
+    __syncwarp();
+}
 
 __device__ __forceinline__ void tma_tile2d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, uint32_t bar) {
     asm volatile(
@@ -233,6 +256,7 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
     uint64_t* bars = reinterpret_cast<uint64_t*>(s_bias + 4 * 256);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * S + 8);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    volatile int* warp_its = reinterpret_cast<volatile int*>(tmem_slot + 4);  // [PW] gather teardown
     const uint32_t full0 = smem_u32(bars), bfull0 = smem_u32(bars + S), empty0 = smem_u32(bars + 2 * S);
     const uint32_t tfull0 = smem_u32(bars + 3 * S), tempty0 = smem_u32(bars + 3 * S + 2);
     const uint32_t mdone = smem_u32(bars + 3 * S + 4);
@@ -292,7 +316,7 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
                 const int kb0 = kc * kbc, kb1 = min(p.KB, kb0 + kbc);
                 for (int kb = kb0; kb < kb1; ++kb, ++it) {
                     const int s = (int)(it % S);
-                    mbar_wait(empty0 + 8 * s, ((it / S) & 1) ^ 1, abort_flag);
+                    mbar_wait(empty0 + 8 * s, ((it / S) & 1) ^ 1, abort_flag, p.wait_limit);
                     if (__any_sync(0xffffffffu, *abort_flag)) {
                         stop = true;
                         break;
@@ -310,7 +334,7 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
             }
             if (lane == 0)  // nothing the TMA engine writes may still be landing when the CTA leaves
                 for (uint32_t j = it >= (uint32_t)S ? it - S : 0; j < it; ++j)
-                    mbar_wait(full0 + 8 * (j % S), (j / S) & 1, abort_flag);
+                    mbar_wait(full0 + 8 * (j % S), (j / S) & 1, abort_flag, p.wait_limit);
             __syncwarp();
         }
     } else if (warp < PW && p.gmode == 1) {
@@ -337,7 +361,7 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
             }
             for (int kb = kb0; kb < kb1; ++kb, ++it) {
                 const int s = (int)(it % S);
-                mbar_wait(empty0 + 8 * s, ((it / S) & 1) ^ 1, abort_flag);
+                mbar_wait(empty0 + 8 * s, ((it / S) & 1) ^ 1, abort_flag, p.wait_limit);
                 if (__any_sync(0xffffffffu, *abort_flag)) {
                     stop = true;
                     break;
@@ -364,10 +388,8 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
                                 rows[2], rows[3], full0 + 8 * s);
             }
         }
-        if (warp == 0 && lane == 0)  // nothing the TMA engine writes may still be landing when the CTA leaves
-            for (uint32_t j = it >= (uint32_t)S ? it - S : 0; j < it; ++j)
-                mbar_wait(full0 + 8 * (j % S), (j / S) & 1, abort_flag);
-        __syncwarp();
+        // nothing the TMA engine writes may still be landing when the CTA leaves
+        gather_teardown(it, warp_its, PW, warp, lane, full0, S, abort_flag, p.wait_limit);
     } else if (warp < PW && p.gmode == 3) {
         // ------------------------------------------------------------------ window gather (SUBM3)
         // Rows are in linear site order, so the neighbours of a 128-row tile through the 9 taps of
@@ -387,7 +409,7 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
         auto rendezvous = [&]() {
             __syncwarp();
             if (lane == 0) mbar_arrive(rdv);
-            mbar_wait(rdv, rdv_ph & 1, abort_flag);
+            mbar_wait(rdv, rdv_ph & 1, abort_flag, p.wait_limit);
             ++rdv_ph;
             return __any_sync(0xffffffffu, *abort_flag) != 0;
         };
@@ -410,7 +432,7 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
                              : "memory");
                 if (rows4 > 0) bulk_g2s(smem_u32(map_s), p.map + (size_t)m0 * 27, (uint32_t)rows4 * 108u, mfull);
             }
-            mbar_wait(mfull, mf_ph & 1, abort_flag);
+            mbar_wait(mfull, mf_ph & 1, abort_flag, p.wait_limit);
             ++mf_ph;
             const int rvalid = n_rows - m0;  // rows of the tile that exist (map rows past it are stale)
             // every warp finds the window starts (smallest neighbour row per dz plane) of the whole tile
@@ -466,7 +488,7 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
                         for (int j = 0; j < 3; ++j)
                             if (need[j]) tma_tile2d(smem_u32(win + j * win1), &tmap, cb * p.BKE, lo[j], wfull);
                     }
-                    mbar_wait(wfull, wf_ph & 1, abort_flag);
+                    mbar_wait(wfull, wf_ph & 1, abort_flag, p.wait_limit);
                     ++wf_ph;
                     if (__any_sync(0xffffffffu, *abort_flag)) {
                         stop = true;
@@ -478,7 +500,7 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
                 // overlap. NB <= S keeps every wait within one phase of its barrier: the warp's
                 // previous stage (it - NB) waited for the release of it - NB - S >= it - 2S.
                 if (own != warp) continue;
-                mbar_wait(empty0 + 8 * s, ph ^ 1u, abort_flag);
+                mbar_wait(empty0 + 8 * s, ph ^ 1u, abort_flag, p.wait_limit);
                 if (__any_sync(0xffffffffu, *abort_flag)) {
                     stop = true;
                     break;
@@ -511,12 +533,10 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
             }
         }
         if (tid == 0) {  // nothing the TMA engine writes may still be landing when the CTA leaves
-            if (wf_ph > 0) mbar_wait(wfull, (wf_ph - 1) & 1, abort_flag);
-            if (mf_ph > 0) mbar_wait(mfull, (mf_ph - 1) & 1, abort_flag);
-            for (uint32_t j = it >= (uint32_t)S ? it - S : 0; j < it; ++j)
-                mbar_wait(full0 + 8 * (j % S), (j / S) & 1, abort_flag);
+            if (wf_ph > 0) mbar_wait(wfull, (wf_ph - 1) & 1, abort_flag, p.wait_limit);
+            if (mf_ph > 0) mbar_wait(mfull, (mf_ph - 1) & 1, abort_flag, p.wait_limit);
         }
-        __syncwarp();
+        gather_teardown(it, warp_its, PW, warp, lane, full0, S, abort_flag, p.wait_limit);
     } else if (warp < PW) {
         // ------------------------------------------------------------------ cp.async gather
         // thread (warp w, lane): 16-byte chunk c = lane & 7 of rows r0 + 4 PW q, r0 = 4 w + lane / 8
@@ -540,7 +560,7 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
             }
             for (int kb = kb0; kb < kb1; ++kb, ++it) {
                 const int s = (int)(it % S);
-                mbar_wait(empty0 + 8 * s, ((it / S) & 1) ^ 1, abort_flag);
+                mbar_wait(empty0 + 8 * s, ((it / S) & 1) ^ 1, abort_flag, p.wait_limit);
                 if (__any_sync(0xffffffffu, *abort_flag)) {
                     stop = true;
                     break;
@@ -581,7 +601,7 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
             for (uint32_t j = it >= (uint32_t)LAG ? it - LAG : 0; j < it; ++j) mbar_arrive(full0 + 8 * (j % S));
         if (tid == 0)  // no weight copy may still be landing when the CTA leaves
             for (uint32_t j = it >= (uint32_t)S ? it - S : 0; j < it; ++j)
-                mbar_wait(bfull0 + 8 * (j % S), (j / S) & 1, abort_flag);
+                mbar_wait(bfull0 + 8 * (j % S), (j / S) & 1, abort_flag, p.wait_limit);
     } else if (warp < PW + 4) {
         // ------------------------------------------------------------------ epilogue
         const int ew = warp - PW, r = ew * 32 + lane;
@@ -602,7 +622,7 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
                 }
                 __syncwarp();
             }
-            mbar_wait(tfull0 + 8 * buf, (tc >> 1) & 1, abort_flag);
+            mbar_wait(tfull0 + 8 * buf, (tc >> 1) & 1, abort_flag, p.wait_limit);
             if (__any_sync(0xffffffffu, *abort_flag)) break;
             tc_fence_after();
             if (p.tout) {
@@ -700,12 +720,12 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
                 const int kb0 = kc * kbc, kb1 = min(p.KB, kb0 + kbc);
                 const uint32_t buf = tc & 1;
                 const uint32_t acc = tmem + buf * p.acc_cols;
-                mbar_wait(tempty0 + 8 * buf, ((tc >> 1) & 1) ^ 1, abort_flag);
+                mbar_wait(tempty0 + 8 * buf, ((tc >> 1) & 1) ^ 1, abort_flag, p.wait_limit);
                 if (*abort_flag) break;
                 tc_fence_after();
                 for (int kb = kb0; kb < kb1; ++kb) {
-                    mbar_wait(full0 + 8 * s, ph, abort_flag);
-                    if (p.gmode == 0) mbar_wait(bfull0 + 8 * s, ph, abort_flag);
+                    mbar_wait(full0 + 8 * s, ph, abort_flag, p.wait_limit);
+                    if (p.gmode == 0) mbar_wait(bfull0 + 8 * s, ph, abort_flag, p.wait_limit);
                     if (*abort_flag) {
                         stop = true;
                         break;
@@ -726,7 +746,7 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
             }
             // every MMA this CTA issued has completed before TMEM is released
             tc_commit(mdone);
-            mbar_wait(mdone, 0, abort_flag);
+            mbar_wait(mdone, 0, abort_flag, p.wait_limit);
         }
         __syncwarp();
     }
@@ -904,11 +924,8 @@ EncodeTiledFn encode_tiled() {
 
 template <int LAG, int PW>
 npvs_status launch_tc(const TcParams& p, const CUtensorMap& tm, int grid, size_t smem, cudaStream_t st) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(conv_tc_kernel<LAG, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> seen[kMaxDevices];
+    NPVS_TRY(ensure_dynamic_smem((const void*)conv_tc_kernel<LAG, PW>, (int)kMaxSmem, seen, "conv_tc_kernel"));
     launch_k(conv_tc_kernel<LAG, PW>, grid, threads_for(PW), smem, st, p, tm);
     return check_launch("conv_tc_kernel");
 }
@@ -1097,6 +1114,7 @@ npvs_status conv_tc_fwd(const npvs_conv_desc& d, const void* x, const void* w, c
     p.skip = (const __nv_bfloat16*)skip;
     p.y = y;
     p.status = d.status;
+    p.wait_limit = wait_limit_cycles();
     p.rows_x = rows_x;
     p.max_split = d.tune_max_split > 0 ? d.tune_max_split : 8;
     const int lag = d.tune_lag > 0 ? d.tune_lag : 2;

@@ -336,9 +336,13 @@ extern "C" npvs_status npvs_deinterleave(const float* logits, const int32_t* tab
 namespace {
 constexpr long long kNoAllocMaxSites = 1ll << 22;  // 4,194,304 coarse sites per call (all batches)
 constexpr int kNoAllocMaxCtas = (int)(kNoAllocMaxSites / npvs::kSitesPerCta);
-constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mutex;
-int* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+// per device ordinal: the context in which the array's address was looked up, and the address
+struct NoAllocSlot {
+    unsigned long long ctx;
+    int* ptr;
+};
+NoAllocSlot g_noalloc[npvs::kMaxDevices] = {};
 }  // namespace
 
 // counts [kNoAllocMaxCtas + 1] then offsets [kNoAllocMaxCtas + 1] (128 KiB per device)
@@ -365,24 +369,28 @@ extern "C" npvs_status npvs_interleave_noalloc(const uint32_t* occ_bits, npvs_gr
         return NPVS_ERR_UNSUPPORTED;
     }
     int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         set_error("npvs_interleave_noalloc: no usable current device");
         return NPVS_ERR_CUDA;
     }
     int* scratch;
     {
-        // the device address of the array, looked up once per device (with that device current)
+        // The device address of the array, looked up with the device current, once per device
+        // and context: a device reset makes a new primary context (a new id), and the address of
+        // the old one must not be reused, so the look-up is repeated then.
         std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-        if (g_noalloc_ptr[dev] == nullptr) {
+        const unsigned long long ctx = current_context_id();
+        if (ctx == 0 || g_noalloc[dev].ctx != ctx || g_noalloc[dev].ptr == nullptr) {
             void* ptr = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&ptr, npvs_interleave_scratch);
             if (e != cudaSuccess || ptr == nullptr) {
                 set_error("npvs_interleave_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
                 return NPVS_ERR_CUDA;
             }
-            g_noalloc_ptr[dev] = static_cast<int*>(ptr);
+            g_noalloc[dev].ctx = current_context_id();  // the look-up made the primary context current
+            g_noalloc[dev].ptr = static_cast<int*>(ptr);
         }
-        scratch = g_noalloc_ptr[dev];
+        scratch = g_noalloc[dev].ptr;
     }
     cudaStream_t st = as_stream(stream);
     ILParams p;

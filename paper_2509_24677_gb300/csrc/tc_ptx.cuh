@@ -29,13 +29,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 // Wait for phase `parity` of an mbarrier. The bound is kept with the SM cycle counter (cheap to
-// read on every poll): ~4e9 cycles, about 2 s at the maximum clock, and 2e7 cycles once the CTA
-// has already timed out. On expiry the CTA records the timeout and carries on without waiting.
-__device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+// read on every poll): `limit` cycles (npvs_set_wait_limit; by default ~4e9, about 2 s at the
+// maximum clock), and kDrainCycles once the CTA has already timed out, whatever `limit` is, so that
+// the teardown's waits for copies and MMAs still in flight are not cut short by a small limit. On
+// expiry the CTA records the timeout and carries on without waiting.
+constexpr long long kDrainCycles = 20000000ll;  // ~10 ms at the maximum clock
+__device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, long long limit) {
     if (mbar_try_wait(bar, parity)) return;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        const long long lim = *abort_flag ? 20000000ll : 4000000000ll;
+        const long long lim = *abort_flag ? kDrainCycles : limit;
         if (clock64() - t0 > lim) {
             *abort_flag = 1;
             return;

@@ -97,6 +97,7 @@ struct WgParams {
     const __nv_bfloat16* g;
     float* part;  // [units][128][Ntile]
     int32_t* status;
+    long long wait_limit;  // bound of every mbarrier wait, SM cycles (npvs_set_wait_limit)
 };
 
 // Shared-memory descriptor of an MN-major operand in 128-byte swizzle atoms: LBO = bytes between
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_tc_kernel(const WgParams 
                 const int jn = w.j0 + (kb + 1) * 64 + row;
                 next = (kb + 1 < w.nkb && jn < w.j1) ? list[jn] : -1;
                 const int s = (int)(it % S);
-                mbar_wait(empty0 + 8 * s, ((it / S) & 1) ^ 1, abort_flag);
+                mbar_wait(empty0 + 8 * s, ((it / S) & 1) ^ 1, abort_flag, p.wait_limit);
                 if (__any_sync(0xffffffffu, *abort_flag)) {
                     stop = true;
                     break;
@@ -236,7 +237,7 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_tc_kernel(const WgParams 
                 continue;
             }
             const uint32_t buf = tc & 1;
-            mbar_wait(tfull0 + 8 * buf, (tc >> 1) & 1, abort_flag);
+            mbar_wait(tfull0 + 8 * buf, (tc >> 1) & 1, abort_flag, p.wait_limit);
             if (__any_sync(0xffffffffu, *abort_flag)) break;
             tc_fence_after();
             const uint32_t taddr = tmem + buf * p.acc_cols + ((uint32_t)(ew * 32) << 16);
@@ -265,12 +266,12 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_tc_kernel(const WgParams 
                 if (w.nkb == 0) continue;
                 const uint32_t buf = tc & 1;
                 const uint32_t acc = tmem + buf * p.acc_cols;
-                mbar_wait(tempty0 + 8 * buf, ((tc >> 1) & 1) ^ 1, abort_flag);
+                mbar_wait(tempty0 + 8 * buf, ((tc >> 1) & 1) ^ 1, abort_flag, p.wait_limit);
                 if (*abort_flag) break;
                 tc_fence_after();
                 for (int kb = 0; kb < w.nkb; ++kb, ++it) {
                     const int s = (int)(it % S);
-                    mbar_wait(full0 + 8 * s, (it / S) & 1, abort_flag);
+                    mbar_wait(full0 + 8 * s, (it / S) & 1, abort_flag, p.wait_limit);
                     if (*abort_flag) {
                         stop = true;
                         break;
@@ -287,7 +288,7 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_tc_kernel(const WgParams 
                 ++tc;
             }
             tc_commit(mdone);
-            mbar_wait(mdone, 0, abort_flag);
+            mbar_wait(mdone, 0, abort_flag, p.wait_limit);
         }
         __syncwarp();
     }
@@ -396,14 +397,9 @@ npvs_status wgrad_tc(const npvs_conv_desc& d, const __nv_bfloat16* x, const __nv
     p.g = g;
     p.part = part;
     p.status = d.status;
-    static bool attr_set[64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        if (cudaFuncSetAttribute(wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess)
-            return check_launch("wgrad_tc_kernel attribute");
-        attr_set[dev] = true;
-    }
+    p.wait_limit = wait_limit_cycles();
+    static std::atomic<unsigned long long> seen[kMaxDevices];
+    NPVS_TRY(ensure_dynamic_smem((const void*)wgrad_tc_kernel, 227 * 1024, seen, "wgrad_tc_kernel"));
     const int units = w.taps * w.MT * w.NT * w.ksplit;
     launch_k(wgrad_tc_kernel, std::min(units, kNumSMs), kWgThreads, w.smem, st, p);
     NPVS_TRY(check_launch("wgrad_tc_kernel"));

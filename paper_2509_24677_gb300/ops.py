@@ -91,6 +91,14 @@ def npvs_last_error() -> str:
     return _lib().npvs_last_error().decode()
 
 
+def npvs_set_wait_limit(cycles: int) -> int:
+    """Sets the bound (SM cycles; 0 = the default) of the tensor-core kernels' waits for kernels
+    launched from now on; returns the previous bound."""
+    prev = ctypes.c_int64()
+    check(_lib().npvs_set_wait_limit(int(cycles), ctypes.byref(prev)), "npvs_set_wait_limit")
+    return int(prev.value)
+
+
 def npvs_check_status(status: torch.Tensor, stream=None) -> int:
     """Synchronises, returns and clears the device status word (0 = OK)."""
     _need_cuda(status)

@@ -146,3 +146,17 @@ def test_argument_errors_of_the_strided3_entry_points_on_host():
         assert "forward only" in lib.npvs_last_error().decode()
     d = L.ConvDesc(9, L.F32, 16, 16, 1, 0, fake, None, n, 24, n, 24)
     assert lib.npvs_sparse_conv_fwd(ctypes.byref(d), fake, fake, None, None, fake, None) == L.ERR_UNSUPPORTED
+
+
+def test_wait_limit_setter_is_host_only_and_checks_its_argument():
+    """npvs_set_wait_limit changes a host-side setting only (no GPU needed): it returns the previous
+    bound, 0 restores the default of 4e9 SM cycles, and a negative bound is refused."""
+    from paper_2509_24677_gb300 import _lib as L
+    from paper_2509_24677_gb300 import ops
+    assert ops.npvs_set_wait_limit(0) == 4_000_000_000
+    assert ops.npvs_set_wait_limit(12345) == 4_000_000_000
+    assert ops.npvs_set_wait_limit(0) == 12345
+    with pytest.raises(L.NpvsError) as e:
+        ops.npvs_set_wait_limit(-1)
+    assert e.value.status == L.ERR_INVALID_ARG
+    assert ops.npvs_set_wait_limit(0) == 4_000_000_000
