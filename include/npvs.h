@@ -399,7 +399,11 @@ npvs_status npvs_forward_layer_output(const npvs_net_desc* net, int32_t layer, v
  * (s_gt H) raster of cams[e]'s directions (as npvs_froxelize), the nearest box hit t > 0 of
  * p_m + t dir is reprojected into cams[e]'s frame; a hit inside the frustum sets its froxel in
  * gt_bits [B][D][H][W/32] (zeroed here). With g_bits (nullable) the result is ANDed with the
- * geometry grid. Binary32 arithmetic. n_points * s_gt^2 * W * H must be a multiple of 256. */
+ * geometry grid. Binary32 arithmetic, each step rounded to nearest in a fixed order (slab entry
+ * t* = max(0, max_i min(t0_i, t1_i)) with t_i = (bound_i - p_i) * (1 / dir_i); v_i = (p_i + t* dir_i)
+ * - c'_i; x_c = (v_0 r_0 + v_1 r_1) + v_2 r_2 and likewise y_c, z_c; x = min(floor((((x_c / z_c) /
+ * tan) + 1) * 0.5 * W), W - 1)), so the bits are reproducible exactly by a binary32 program.
+ * n_points * s_gt^2 * W * H must be a multiple of 256. */
 npvs_status npvs_gt_raycast(const float* boxes, const int32_t* box_offsets, const npvs_camera* cams,
                             const float* points, int32_t n_points, npvs_grid grid, int32_t s_gt,
                             const uint32_t* g_bits, uint32_t* gt_bits, void* stream);

@@ -28,7 +28,12 @@
  * Ground truth (Sec. 3.2, last paragraph): from each of M viewpoints p_m in the viewcell, one
  * ray per supersampled pixel of p_m's own frustum (same basis and tan(phi)) finds the nearest
  * face hit t* > 0; the hit point p_m + t* dir is reprojected into the c' frame and its froxel is
- * marked. All of it in binary64.
+ * marked. Two precisions again: binary64 (the nearest hit over every face rectangle), and a
+ * binary32 mirror that fixes one sequence of binary32 operations, each rounded to nearest: the
+ * nearest entry t* = max_i min(t0_i, t1_i) over the boxes whose slab intervals overlap after the
+ * origin (the Kay-Kajiya slab method, t_i = (bound_i - p_i) * (1 / dir_i)), then the reprojection.
+ * The slab entry of a ray that starts outside a box is its first face hit, so the two agree up
+ * to rounding; the mirror's sequence is what fixes every integer decision bit for bit.
  */
 #include <math.h>
 #include <stdint.h>
@@ -266,6 +271,95 @@ long long oracle_gt_raycast(const float *cam, const float *z, int W, int H, int 
         int k = slice_of_d(z, D, zc);
         __atomic_fetch_or(&bits[((size_t)k * H + y) * WW + x / 32], 1u << (x & 31),
                           __ATOMIC_RELAXED);
+    }
+    return nhit;
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* ground truth: binary32 mirror                                                             */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Nearest slab entry t* > 0 of the ray p + t dir over all boxes (inv = 1 / dir per axis, +-inf
+ * where dir is 0); +inf if none. A box is entered at tn = max(0, max_i min(t0_i, t1_i)) and left
+ * at tf = min(best, min_i max(t0_i, t1_i)); it is hit first if tn <= tf, tn > 0 and tn < best. */
+static float first_hit_f(const float p[3], const float dir[3], const float inv[3], const float *boxes,
+                         int nb) {
+    float best = INFINITY;
+    for (int j = 0; j < nb; ++j) {
+        const float *bx = boxes + 6 * (size_t)j;
+        float tn = 0.0f, tf = best;
+        for (int i = 0; i < 3; ++i) {
+            float lo = bx[i], hi = bx[3 + i];
+            if (dir[i] == 0.0f) {
+                if (p[i] < lo || p[i] > hi) tf = -1.0f;   /* parallel to the slab, outside it */
+            } else {
+                float d0 = lo - p[i];
+                float t0 = d0 * inv[i];
+                float d1 = hi - p[i];
+                float t1 = d1 * inv[i];
+                tn = fmaxf(tn, fminf(t0, t1));
+                tf = fminf(tf, fmaxf(t0, t1));
+            }
+        }
+        if (tn <= tf && tn > 0.0f && tn < best) best = tn;
+    }
+    return best;
+}
+
+/*
+ * Binary32 mirror of oracle_gt_raycast. pts: [M][3] float viewpoints. Per ray (a, b) of
+ * viewpoint m: dir as the froxelization's ray_dir_f, inv_i = 1 / dir_i, t* from first_hit_f,
+ * v_i = (p_i + t* dir_i) - c'_i, x_c = (v_0 r_0 + v_1 r_1) + v_2 r_2 (likewise y_c with u, z_c
+ * with f), inside iff z[0] <= z_c < z[D] and |(x_c / z_c) / tan| <= 1 and |(y_c / z_c) / tan| <= 1,
+ * froxel x = min(floor(((x_c / z_c / tan) + 1) * 0.5 * W), W - 1) (likewise y), slice k of z_c.
+ * bits: [D][H][W/32] raw ground truth, zeroed here. Returns the number of rays that hit.
+ */
+long long oracle_gt_raycast_f32(const float *cam, const float *z, int W, int H, int D, int s_gt,
+                                const float *pts, int M, const float *boxes, int nb, uint32_t *bits) {
+    const int WW = W / 32, sW = s_gt * W, sH = s_gt * H;
+    const float tp = cam[12];
+    memset(bits, 0, sizeof(uint32_t) * (size_t)D * H * WW);
+    long long nhit = 0;
+    const long long nrays = (long long)M * sW * sH;
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : nhit)
+    for (long long ray = 0; ray < nrays; ++ray) {
+        int m = (int)(ray / ((long long)sW * sH));
+        int rem = (int)(ray % ((long long)sW * sH));
+        int b = rem / sW, a = rem % sW;
+        const float *p = pts + 3 * (size_t)m;
+        float dir[3], inv[3];
+        ray_dir_f(cam, a, b, sW, sH, dir);
+        for (int i = 0; i < 3; ++i) inv[i] = 1.0f / dir[i];
+        float t = first_hit_f(p, dir, inv, boxes, nb);
+        if (!(t < INFINITY)) continue;
+        ++nhit;
+        float v[3];
+        for (int i = 0; i < 3; ++i) {
+            float step = t * dir[i];
+            float q = p[i] + step;
+            v[i] = q - cam[i];
+        }
+        float c[3];
+        for (int axis = 0; axis < 3; ++axis) {          /* 0: right (x_c), 1: up (y_c), 2: fwd (z_c) */
+            const float *e = cam + 3 + 3 * axis;
+            float s0 = v[0] * e[0];
+            float s1 = v[1] * e[1];
+            float s2 = v[2] * e[2];
+            float acc = s0 + s1;
+            c[axis] = acc + s2;
+        }
+        float xc = c[0], yc = c[1], zc = c[2];
+        if (!(zc >= z[0] && zc < z[D])) continue;
+        float qx = xc / zc, qy = yc / zc;
+        float ux = qx / tp, uy = qy / tp;
+        if (!(fabsf(ux) <= 1.0f && fabsf(uy) <= 1.0f)) continue;
+        float hx = (ux + 1.0f) * 0.5f, hy = (uy + 1.0f) * 0.5f;
+        float fx = hx * (float)W, fy = hy * (float)H;
+        int x = (int)floorf(fx), y = (int)floorf(fy);
+        if (x > W - 1) x = W - 1;
+        if (y > H - 1) y = H - 1;
+        int k = slice_of_f(z, D, zc);
+        __atomic_fetch_or(&bits[((size_t)k * H + y) * WW + x / 32], 1u << (x & 31), __ATOMIC_RELAXED);
     }
     return nhit;
 }

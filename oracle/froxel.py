@@ -50,6 +50,8 @@ def _load():
             lib.oracle_ray_dir_f32.restype = None
             lib.oracle_gt_raycast.argtypes = [P, P, I, I, I, I, P, I, P, I, P]
             lib.oracle_gt_raycast.restype = ctypes.c_longlong
+            lib.oracle_gt_raycast_f32.argtypes = [P, P, I, I, I, I, P, I, P, I, P]
+            lib.oracle_gt_raycast_f32.restype = ctypes.c_longlong
             _lib = lib
     return _lib
 
@@ -124,17 +126,23 @@ def points_outside_boxes(pts: np.ndarray, boxes: np.ndarray) -> np.ndarray:
     return ~inside
 
 
-def gt_raycast(cam, boxes, W, H, D, s_gt: int, pts: np.ndarray):
+def gt_raycast(cam, boxes, W, H, D, s_gt: int, pts: np.ndarray, precision: int = 64):
     """Raw ground truth [D][H][W/32] from the given viewpoints (not yet ANDed with G).
-    Returns (bits, number of rays that hit geometry)."""
+    precision 64: binary64 nearest face hit (viewpoints taken as float64); 32: the binary32
+    mirror (viewpoints rounded to float32). Returns (bits, number of rays that hit geometry)."""
     lib = _load()
     cv = _cam_vec(cam)
     z = np.ascontiguousarray(cam.slices, dtype=np.float32)
     bx = np.ascontiguousarray(boxes, dtype=np.float32)
-    p = np.ascontiguousarray(pts, dtype=np.float64)
     bits = np.zeros((D, H, W // 32), dtype=np.uint32)
-    nhit = lib.oracle_gt_raycast(_ptr(cv), _ptr(z), W, H, D, s_gt, _ptr(p), len(p), _ptr(bx),
-                                 len(bx), _ptr(bits))
+    if precision == 32:
+        p = np.ascontiguousarray(pts, dtype=np.float32)
+        nhit = lib.oracle_gt_raycast_f32(_ptr(cv), _ptr(z), W, H, D, s_gt, _ptr(p), len(p), _ptr(bx),
+                                         len(bx), _ptr(bits))
+    else:
+        p = np.ascontiguousarray(pts, dtype=np.float64)
+        nhit = lib.oracle_gt_raycast(_ptr(cv), _ptr(z), W, H, D, s_gt, _ptr(p), len(p), _ptr(bx),
+                                     len(bx), _ptr(bits))
     return bits, int(nhit)
 
 
@@ -147,7 +155,8 @@ def viewpoints(vc, cam, offsets: np.ndarray) -> np.ndarray:
     return c[None, :] + np.asarray(offsets, dtype=np.float64) @ R
 
 
-def ground_truth(vc, cam, boxes, W, H, D, s_gt, offsets: np.ndarray, M: int, G: np.ndarray):
+def ground_truth(vc, cam, boxes, W, H, D, s_gt, offsets: np.ndarray, M: int, G: np.ndarray,
+                 precision: int = 64):
     """GT := raw ray-cast PVS from the first M candidate viewpoints outside every box, ANDed with
     the geometry grid G. Reading of Sec. 3.2's occlusion-culling property (supp of the PVS lies
     inside supp(G)). Returns (gt_bits, raw_bits)."""
@@ -156,5 +165,5 @@ def ground_truth(vc, cam, boxes, W, H, D, s_gt, offsets: np.ndarray, M: int, G: 
     pts = cand[ok][:M]
     if len(pts) < M:
         raise ValueError("not enough viewpoints outside the geometry")
-    raw, _ = gt_raycast(cam, boxes, W, H, D, s_gt, pts)
+    raw, _ = gt_raycast(cam, boxes, W, H, D, s_gt, pts, precision)
     return raw & G, raw

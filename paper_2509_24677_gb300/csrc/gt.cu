@@ -10,8 +10,15 @@
 // (floor((x_c / (z_c tan) + 1) / 2 W), floor((y_c / (z_c tan) + 1) / 2 H), slice(z_c)) is set.
 // Optionally the result is ANDed with the geometry grid G (supp(PVS) within supp(G), Sec. 3.2).
 //
-// One thread per ray, binary32 arithmetic; the boxes of the batch element are streamed through
-// shared memory in tiles that every thread of the CTA tests its ray against (slab test).
+// One thread per ray; the boxes of the batch element are streamed through shared memory in tiles
+// that every thread of the CTA tests its ray against (slab test: a box is entered at
+// tn = max(0, max_i min(t0_i, t1_i)), t_i = (bound_i - p_i) * (1 / dir_i), and hit first if it is
+// left after that and before the best hit so far). Every floating-point step is one binary32
+// operation rounded to nearest (__fadd_rn / __fmul_rn / __fdiv_rn, so nothing is contracted into
+// an FMA) in a fixed order: dir_i = (f_i + (n_x tan) r_i) + (n_y tan) u_i as in the froxelization,
+// v_i = (p_i + t* dir_i) - c'_i, x_c = (v_0 r_0 + v_1 r_1) + v_2 r_2 (y_c with u, z_c with f),
+// x = floor((((x_c / z_c) / tan) + 1) * 0.5 * W). The minimum over boxes does not depend on their
+// order, so the result is bit-for-bit the same whatever the tiling.
 #include "common.cuh"
 
 namespace npvs {
@@ -49,17 +56,19 @@ __global__ void __launch_bounds__(kGtCta) gt_raycast_kernel(const float* __restr
         const int m = (int)(ray / ((long long)sW * sH));
         const int rem = (int)(ray - (long long)m * sW * sH);
         const int b = rem / sW, a = rem - b * sW;
-        const float nx = (float)(2 * a + 1 - sW) / (float)sW, ny = (float)(2 * b + 1 - sH) / (float)sH;
+        const float nx = __fdiv_rn((float)(2 * a + 1 - sW), (float)sW);
+        const float ny = __fdiv_rn((float)(2 * b + 1 - sH), (float)sH);
+        const float sx = __fmul_rn(nx, cam.tan_half), sy = __fmul_rn(ny, cam.tan_half);
         const float* pm = points + ((size_t)e * M + m) * 3;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             p[i] = pm[i];
-            dir[i] = cam.fwd[i] + nx * cam.tan_half * cam.right[i] + ny * cam.tan_half * cam.up[i];
+            dir[i] = __fadd_rn(__fadd_rn(cam.fwd[i], __fmul_rn(sx, cam.right[i])), __fmul_rn(sy, cam.up[i]));
         }
     }
     float inv[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) inv[i] = 1.0f / dir[i];  // +-inf on an axis-parallel ray
+    for (int i = 0; i < 3; ++i) inv[i] = __fdiv_rn(1.0f, dir[i]);  // +-inf on an axis-parallel ray
     float best = INFINITY;
     const int j0 = box_offsets[e], j1 = box_offsets[e + 1];
     for (int base = j0; base < j1; base += kBoxTile) {
@@ -76,7 +85,8 @@ __global__ void __launch_bounds__(kGtCta) gt_raycast_kernel(const float* __restr
                 if (dir[i] == 0.0f) {
                     if (p[i] < lo || p[i] > hi) tf = -1.0f;
                 } else {
-                    const float t0 = (lo - p[i]) * inv[i], t1 = (hi - p[i]) * inv[i];
+                    const float t0 = __fmul_rn(__fsub_rn(lo, p[i]), inv[i]);
+                    const float t1 = __fmul_rn(__fsub_rn(hi, p[i]), inv[i]);
                     tn = fmaxf(tn, fminf(t0, t1));
                     tf = fminf(tf, fmaxf(t0, t1));
                 }
@@ -87,15 +97,16 @@ __global__ void __launch_bounds__(kGtCta) gt_raycast_kernel(const float* __restr
     if (!live || !(best < INFINITY)) return;
     float v[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) v[i] = p[i] + best * dir[i] - cam.origin[i];
-    const float xc = v[0] * cam.right[0] + v[1] * cam.right[1] + v[2] * cam.right[2];
-    const float yc = v[0] * cam.up[0] + v[1] * cam.up[1] + v[2] * cam.up[2];
-    const float zc = v[0] * cam.fwd[0] + v[1] * cam.fwd[1] + v[2] * cam.fwd[2];
+    for (int i = 0; i < 3; ++i) v[i] = __fsub_rn(__fadd_rn(p[i], __fmul_rn(best, dir[i])), cam.origin[i]);
+    auto dot = [&](const float* e) {
+        return __fadd_rn(__fadd_rn(__fmul_rn(v[0], e[0]), __fmul_rn(v[1], e[1])), __fmul_rn(v[2], e[2]));
+    };
+    const float xc = dot(cam.right), yc = dot(cam.up), zc = dot(cam.fwd);
     if (!(zc >= cam.slices[0] && zc < cam.slices[g.D])) return;
-    const float ux = xc / zc / cam.tan_half, uy = yc / zc / cam.tan_half;
+    const float ux = __fdiv_rn(__fdiv_rn(xc, zc), cam.tan_half), uy = __fdiv_rn(__fdiv_rn(yc, zc), cam.tan_half);
     if (!(fabsf(ux) <= 1.0f && fabsf(uy) <= 1.0f)) return;
-    const int x = min((int)floorf((ux + 1.0f) * 0.5f * g.W), g.W - 1);
-    const int y = min((int)floorf((uy + 1.0f) * 0.5f * g.H), g.H - 1);
+    const int x = min((int)floorf(__fmul_rn(__fmul_rn(__fadd_rn(ux, 1.0f), 0.5f), (float)g.W)), g.W - 1);
+    const int y = min((int)floorf(__fmul_rn(__fmul_rn(__fadd_rn(uy, 1.0f), 0.5f), (float)g.H)), g.H - 1);
     const int k = slice_index(cam.slices, g.D, zc);
     atomicOr(bits + (((size_t)e * g.D + k) * g.H + y) * (g.W / 32) + (x >> 5), 1u << (x & 31));
 }

@@ -28,18 +28,35 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// Non-blocking probe of the same phase (returns at once).
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 // Wait for phase `parity` of an mbarrier. The bound is kept with the SM cycle counter (cheap to
 // read on every poll): `limit` cycles (npvs_set_wait_limit; by default ~4e9, about 2 s at the
 // maximum clock), and kDrainCycles once the CTA has already timed out, whatever `limit` is, so that
 // the teardown's waits for copies and MMAs still in flight are not cut short by a small limit. On
-// expiry the CTA records the timeout and carries on without waiting.
-constexpr long long kDrainCycles = 20000000ll;  // ~10 ms at the maximum clock
+// expiry the CTA records the timeout and carries on without waiting. try_wait may itself suspend
+// the thread for a hardware-defined interval before it reports an incomplete phase; a bound below
+// kPollBelowCycles is kept by polling with test_wait instead, which returns at once.
+constexpr long long kDrainCycles = 20000000ll;    // ~10 ms at the maximum clock
+constexpr long long kPollBelowCycles = 1000000ll;
 __device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, long long limit) {
-    if (mbar_try_wait(bar, parity)) return;
+    const bool poll = limit < kPollBelowCycles;
+    if (poll ? mbar_test_wait(bar, parity) : mbar_try_wait(bar, parity)) return;
     const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        const long long lim = *abort_flag ? kDrainCycles : limit;
-        if (clock64() - t0 > lim) {
+    for (;;) {
+        const bool aborted = *abort_flag != 0;
+        if ((poll && !aborted) ? mbar_test_wait(bar, parity) : mbar_try_wait(bar, parity)) return;
+        if (clock64() - t0 > (aborted ? kDrainCycles : limit)) {
             *abort_flag = 1;
             return;
         }

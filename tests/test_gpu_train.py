@@ -554,14 +554,16 @@ def test_autograd_functions_match_trainer():
 # training targets: ground-truth ray casting
 # ------------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("case", ["plain64", "city-small"])
+@pytest.mark.parametrize("case", ["plain64", "city-small", "city-s2"])
 def test_gt_raycast_matches_oracle(case):
-    """Binary32 GPU ray casting against the FP64 oracle: identical viewpoints; froxels may differ
-    only where a ray grazes an edge or two hits tie (a small fraction)."""
+    """GPU ray casting is bit-exact against the oracle's binary32 mirror on the same float32
+    viewpoints (raw and ANDed with G), and within a small fraction (grazing rays, ties) of the
+    oracle's binary64 nearest face hits."""
     from oracle import camera as ocam
     from oracle import froxel as ofx
     from paper_2509_24677_gb300 import data as Dm
     L, ops, P = lib()
+    s_gt = 2 if case == "city-s2" else 1
     if case == "plain64":
         wl = I.workload("plain64")
         boxes, vc = I.plain64_scene()
@@ -575,7 +577,8 @@ def test_gt_raycast_matches_oracle(case):
     cam_o = ocam.frustum(vc, wl.D)
     offs = I.gt_candidate_offsets(3, vc, max(4 * M, M + 64))
     G_o = ofx.froxelize(cam_o, boxes, wl.W, wl.H, wl.D, wl.supersample)
-    gt_o, raw_o = ofx.ground_truth(vc, cam_o, boxes, wl.W, wl.H, wl.D, 1, offs, M, G_o)
+    gt_o, raw_o = ofx.ground_truth(vc, cam_o, boxes, wl.W, wl.H, wl.D, s_gt, offs, M, G_o)
+    raw_m, _ = ofx.gt_raycast(cam_o, boxes, wl.W, wl.H, wl.D, s_gt, pts, precision=32)
     pts_o = ofx.viewpoints(vc, cam_o, offs)
     pts_o = pts_o[ofx.points_outside_boxes(pts_o, boxes)][:M]
     np.testing.assert_allclose(pts, pts_o, rtol=0, atol=1e-4)
@@ -585,13 +588,15 @@ def test_gt_raycast_matches_oracle(case):
     cd = ops.cameras_to_device([cam])
     words = wl.D * wl.H * (wl.W // 32)
     raw = torch.full((words,), -1, dtype=torch.int32, device=DEV)
-    ops.npvs_gt_raycast(bx, of, cd, torch.from_numpy(pts[None]).to(DEV), g, 1, raw)
+    ops.npvs_gt_raycast(bx, of, cd, torch.from_numpy(pts[None]).to(DEV), g, s_gt, raw)
     occ = torch.empty(words, dtype=torch.int32, device=DEV)
     ops.npvs_froxelize(bx, of, cd, g, wl.supersample, occ)
     gt = torch.empty(words, dtype=torch.int32, device=DEV)
-    ops.npvs_gt_raycast(bx, of, cd, torch.from_numpy(pts[None]).to(DEV), g, 1, gt, g_bits=occ)
+    ops.npvs_gt_raycast(bx, of, cd, torch.from_numpy(pts[None]).to(DEV), g, s_gt, gt, g_bits=occ)
     raw_h = u32(raw).reshape(raw_o.shape)
     gt_h = u32(gt).reshape(gt_o.shape)
+    np.testing.assert_array_equal(raw_h, raw_m)                   # bit-exact against the mirror
+    np.testing.assert_array_equal(gt_h, raw_m & G_o)
     n_ref = int(oil.unpack_bits(raw_o, wl.W).sum())
     d_raw = int(oil.unpack_bits(raw_h ^ raw_o, wl.W).sum())
     d_gt = int(oil.unpack_bits(gt_h ^ gt_o, wl.W).sum())

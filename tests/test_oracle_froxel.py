@@ -186,14 +186,16 @@ def test_plain64_scene_occupancy():
 # ground truth (Sec. 3.2, last paragraph)
 # ------------------------------------------------------------------------------------------
 
-def test_point_viewcell_is_zbuffer_visibility():
-    """h = 0, M = 1: the PVS is the froxel of each pixel ray's first hit (z-buffer)."""
+@pytest.mark.parametrize("precision", [64, 32])
+def test_point_viewcell_is_zbuffer_visibility(precision):
+    """h = 0, M = 1: the PVS is the froxel of each pixel ray's first hit (z-buffer), in binary64 and
+    in the binary32 mirror."""
     W = H = 32
     D, s = 16, 2
     vc = I.Viewcell(centre=(50.0, 8.0, 20.0), half=0.0, yaw=0.3)
     cam = camera.frustum(vc, D)
     boxes = I.random_boxes(seed=7, n=50)
-    raw, _ = froxel.gt_raycast(cam, boxes, W, H, D, s, froxel.viewpoints(vc, cam, np.zeros((1, 3))))
+    raw, _ = froxel.gt_raycast(cam, boxes, W, H, D, s, froxel.viewpoints(vc, cam, np.zeros((1, 3))), precision)
     # z-buffer by slab intersection: nearest positive entry over boxes
     sW, sH = s * W, s * H
     nx = (2 * np.arange(sW) + 1 - sW) / sW
@@ -222,7 +224,8 @@ def test_point_viewcell_is_zbuffer_visibility():
     assert popcount(exp ^ raw) <= 2
 
 
-def test_full_occlusion():
+@pytest.mark.parametrize("precision", [64, 32])
+def test_full_occlusion(precision):
     """A wall spanning the whole frustum between the viewcell and a box hides the box."""
     W = H = 32
     D, s = 16, 2
@@ -234,13 +237,14 @@ def test_full_occlusion():
     G = froxel.froxelize(cam, boxes, W, H, D, s)
     G_target = froxel.froxelize(cam, np.array([target], np.float32), W, H, D, s)
     offs = I.gt_candidate_offsets(0, vc, 64)
-    gt, raw = froxel.ground_truth(vc, cam, boxes, W, H, D, s, offs, 16, G)
+    gt, raw = froxel.ground_truth(vc, cam, boxes, W, H, D, s, offs, 16, G, precision)
     assert popcount(G_target) > 0
     assert popcount(raw & G_target) == 0 and popcount(gt & G_target) == 0
     assert popcount(gt) > 0
 
 
-def test_monotone_in_viewpoints():
+@pytest.mark.parametrize("precision", [64, 32])
+def test_monotone_in_viewpoints(precision):
     """Viewpoints of A a prefix of those of B (same frustum) => GT(A) within GT(B)."""
     W = H = 32
     D, s = 16, 2
@@ -248,8 +252,29 @@ def test_monotone_in_viewpoints():
     cam = camera.frustum(vc, D)
     G = froxel.froxelize(cam, boxes, W, H, D, 4)
     offs = I.gt_candidate_offsets(1, vc, 64)
-    gA, _ = froxel.ground_truth(vc, cam, boxes, W, H, D, s, offs, 3, G)
-    gB, _ = froxel.ground_truth(vc, cam, boxes, W, H, D, s, offs, 12, G)
+    gA, _ = froxel.ground_truth(vc, cam, boxes, W, H, D, s, offs, 3, G, precision)
+    gB, _ = froxel.ground_truth(vc, cam, boxes, W, H, D, s, offs, 12, G, precision)
     assert popcount(gA) > 0
     assert popcount(gA & ~gB) == 0
     assert popcount(gB & ~G) == 0
+
+
+def test_gt_binary32_mirror_agrees_with_binary64_face_hits():
+    """The binary32 mirror (slab entries, float32 viewpoints) against the binary64 nearest face hit
+    on a city street viewcell: the same froxels up to ties at edges and slice bounds, and an empty
+    scene or viewpoints facing away from every box give nothing."""
+    W = H = 64
+    D, s, M = 32, 1, 6
+    boxes = I.city_boxes(1)
+    vc = I.city_viewcells(1, 1, half=1.0)[0]
+    cam = camera.frustum(vc, D)
+    cand = froxel.viewpoints(vc, cam, I.gt_candidate_offsets(3, vc, 64))
+    pts = cand[froxel.points_outside_boxes(cand, boxes)][:M]
+    pts32 = pts.astype(np.float32).astype(np.float64)          # both sides from the same points
+    r64, n64 = froxel.gt_raycast(cam, boxes, W, H, D, s, pts32, 64)
+    r32, n32 = froxel.gt_raycast(cam, boxes, W, H, D, s, pts32, 32)
+    n = popcount(r64)
+    assert n > 500 and abs(n64 - n32) <= max(2, n64 // 1000)
+    assert popcount(r64 ^ r32) <= max(3, n // 200), (popcount(r64 ^ r32), n)
+    empty, nh = froxel.gt_raycast(cam, boxes[:0], W, H, D, s, pts32, 32)
+    assert nh == 0 and popcount(empty) == 0
