@@ -44,7 +44,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle sample")
+    ap.add_argument("--no-single-thread", action="store_true", help="skip the one-thread CPU-oracle estimate")
+    ap.add_argument("--frames-per-step", type=int, default=0,
+                    help="frames timed per step (0: enough for about 1 s of timed frames over all steps)")
     ap.add_argument("--no-train", action="store_true", help="skip the training-step measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-viewcell batched measurement")
     ap.add_argument("--no-highres", action="store_true", help="skip the 512x512x192 measurement")
@@ -78,12 +80,22 @@ def max_over_ranks(x: float, device) -> float:
 
 
 def step_quantiles(times_ms) -> dict:
-    """Median and 99th percentile (nearest rank) of per-step times in milliseconds."""
+    """Median and 99th percentile (nearest rank) of per-frame times in milliseconds; with fewer than
+    100 samples the 99th percentile is not defined by them and the maximum is given instead."""
     t = sorted(float(x) for x in times_ms)
     if not t:
-        return {"p50": None, "p99": None}
-    p99 = t[min(len(t) - 1, max(0, -(-99 * len(t) // 100) - 1))]
-    return {"p50": round(statistics.median(t), 4), "p99": round(p99, 4)}
+        return {"p50": None, "n": 0}
+    out = {"p50": round(statistics.median(t), 4), "n": len(t)}
+    if len(t) >= 100:
+        out["p99"] = round(t[min(len(t) - 1, max(0, -(-99 * len(t) // 100) - 1))], 4)
+    else:
+        out["max"] = round(t[-1], 4)
+    return out
+
+
+def frames_per_step(steps: int, est_ms: float, target_s: float = 1.0) -> int:
+    """Frames timed per step so that the timed frames add up to about target_s (at least one)."""
+    return max(1, int(np.ceil(target_s * 1e3 / max(steps, 1) / max(est_ms, 1e-3))))
 
 
 def replica_rate(world: int, units_per_rank: float, ms_per_step: float) -> float:
@@ -157,6 +169,17 @@ class Clocks:
 CONV_FRAME_DRAM_BYTES = {"level1-window": 65_664_000, "level1-product": 68_955_648}
 
 
+# Measured DRAM traffic (reads + writes) of every kernel of one city256 frame in the bench's launch
+# configuration; None until it is measured for the kernels as they are.
+FRAME_DRAM_BYTES = {}
+
+
+def frame_traffic(tuned: dict):
+    """Measured DRAM bytes of one whole frame for the tuned configuration, or None."""
+    lvl1 = {tuned_label(tuned[k][0]).split("-")[0] for k in ("enc1a", "enc1b", "dec1a", "dec1b")}
+    return FRAME_DRAM_BYTES.get("level1-" + lvl1.pop()) if len(lvl1) == 1 else None
+
+
 def conv_frame_traffic(tuned: dict):
     """Measured convolution DRAM bytes per frame for the tuned configuration `tuned` ({layer:
     (config, us)}), or None when its level-1 form was not captured."""
@@ -222,72 +245,86 @@ def make_frame_inputs(device):
     return wl, boxes, vcs, cams
 
 
-def cpu_oracle_frame_estimate(budget_s: float):
-    """Times the FP64 oracle on a bounded sample of one frame of the same workload: the
-    froxelization of a random sample of froxel columns (scaled to the whole grid) plus interleave,
-    network and de-interleave of the full frame (on G from a one-ray-per-column raster), and, apart
-    from the frame, the training loss on the frame's logits (G standing in for the ground truth).
-    Returns (ms per frame, description, cores, seconds spent, ms per stage)."""
+def cpu_oracle_frame(vc_index: int = 0, G=None):
+    """One whole frame of the FP64 / binary32-mirror oracle on the host cores, nothing sampled:
+    froxelization of the full 256x256x128 grid at s = 8 (binary32 mirror, OpenMP over rows),
+    interleave, the four levels and the U-Net (float64 torch), de-interleave + threshold + G mask
+    (viewcell `vc_index` of the bench's cycle). With G given the froxelization is skipped (its time
+    is then not in the result). Returns (ms per frame, ms per stage, G, logits, coords)."""
     from oracle import camera as ocam
     from oracle import froxel as ofx
     from oracle import interleave as oil
-    from oracle import loss as oloss
     from oracle import network as onet
     wl = I.workload(WORKLOAD)
     boxes = I.city_boxes(0)
-    vc = I.city_viewcells(0, 1)[0]
+    vc = I.city_viewcells(0, N_VIEWCELLS)[vc_index % N_VIEWCELLS]
     cam = ocam.frustum(vc, wl.D)
     ws, bs = I.kaiming_uniform(wl.layers, seed=0)
     W_, B_ = onet.to_torch_params(ws, bs)
-    rng = np.random.default_rng(0)
     t0 = time.perf_counter()
-    G1 = ofx.froxelize(cam, boxes, wl.W, wl.H, wl.D, 1)[None]
+    if G is None:
+        G = ofx.froxelize(cam, boxes, wl.W, wl.H, wl.D, wl.supersample)[None]
     t1 = time.perf_counter()
-    coords, feats, _ = oil.interleave(G1, wl.W, wl.d, wl.in_ch)
+    coords, feats, _ = oil.interleave(G, wl.W, wl.d, wl.in_ch)
     t2 = time.perf_counter()
     levels = onet.build_levels(coords, (1, wl.D // wl.d, wl.H // wl.d, wl.W // wl.d), 4)
     with torch.no_grad():
         logits = onet.forward(list(wl.layers), W_, B_, levels, torch.tensor(feats)).numpy()
     t3 = time.perf_counter()
-    oil.pvs_from_logits(coords, logits, G1, wl.W, wl.d)
+    oil.pvs_from_logits(coords, logits, G, wl.W, wl.d)
     t4 = time.perf_counter()
-    with torch.no_grad():
-        oloss.loss_terms(torch.from_numpy(logits), coords, G1, G1, wl.W, wl.d)
-    t_loss = time.perf_counter() - t4
-    t_rest = t4 - t1
-    # froxel columns at full supersampling, sized to the remaining budget
-    probe = 256
-    cols = np.stack([rng.integers(0, wl.W, probe), rng.integers(0, wl.H, probe)], 1)
+    stages = {"froxelize": 1e3 * (t1 - t0), "interleave": 1e3 * (t2 - t1), "rulebooks+network": 1e3 * (t3 - t2),
+              "deinterleave": 1e3 * (t4 - t3)}
+    return 1e3 * (t4 - t0), {k: round(v, 1) for k, v in stages.items()}, G, logits, coords
+
+
+def cpu_oracle_loss_ms(G, logits, coords) -> float:
+    """The oracle's training loss on a frame's logits (G standing in for the ground truth), ms."""
+    from oracle import loss as oloss
+    wl = I.workload(WORKLOAD)
     t0 = time.perf_counter()
-    ofx.froxel_columns(cam, boxes, wl.W, wl.H, wl.D, wl.supersample, cols)
-    per_col = (time.perf_counter() - t0) / probe
-    n_cols = int(max(probe, min(wl.W * wl.H, (budget_s - t_rest) / max(per_col, 1e-9))))
+    with torch.no_grad():
+        oloss.loss_terms(torch.from_numpy(logits), coords, G, G, wl.W, wl.d)
+    return 1e3 * (time.perf_counter() - t0)
+
+
+def cpu_oracle_single_thread_estimate(G_path: str, n_cols: int = 2048):
+    """The oracle with one thread: froxelization of `n_cols` random froxel columns at s = 8 scaled
+    to the grid's 65,536 columns, plus interleave, U-Net and de-interleave of the whole frame on the
+    oracle's own G (read from G_path). Returns (ms per frame, ms per stage)."""
+    from oracle import camera as ocam
+    from oracle import froxel as ofx
+    wl = I.workload(WORKLOAD)
+    G = np.load(G_path)
+    ms_rest, stages, _, _, _ = cpu_oracle_frame(0, G=G)
+    cam = ocam.frustum(I.city_viewcells(0, N_VIEWCELLS)[0], wl.D)
+    rng = np.random.default_rng(0)
     cols = np.stack([rng.integers(0, wl.W, n_cols), rng.integers(0, wl.H, n_cols)], 1)
     t0 = time.perf_counter()
-    ofx.froxel_columns(cam, boxes, wl.W, wl.H, wl.D, wl.supersample, cols)
-    t_cols = time.perf_counter() - t0
-    t_frox = t_cols * (wl.W * wl.H) / n_cols
-    ms = 1e3 * (t_frox + t_rest)
-    desc = (f"FP64/binary32-mirror oracle: froxelization of {n_cols} of {wl.W * wl.H} froxel columns "
-            f"(s=8, scaled to the grid) + interleave, U-Net and de-interleave of one full frame")
-    stages = {"froxelize": 1e3 * t_frox, "interleave": 1e3 * (t2 - t1), "rulebooks+network": 1e3 * (t3 - t2),
-              "deinterleave": 1e3 * (t4 - t3), "loss (training, not in the frame)": 1e3 * t_loss}
-    return ms, desc, os.cpu_count(), t_cols + t_rest + (t1 - t0) + t_loss, {k: round(v, 1) for k, v in stages.items()}
+    ofx.froxel_columns(cam, I.city_boxes(0), wl.W, wl.H, wl.D, wl.supersample, cols)
+    t_frox = (time.perf_counter() - t0) * (wl.W * wl.H) / n_cols
+    stages["froxelize"] = round(1e3 * t_frox, 1)
+    return ms_rest + 1e3 * t_frox, stages
 
 
-def cpu_oracle_single_thread(budget_s: float):
-    """cpu_oracle_frame_estimate with one thread (OMP_NUM_THREADS=1 for the C oracle, one torch
-    thread) in a child process. Returns (ms per frame, ms per stage), or None if the child fails."""
+def cpu_oracle_single_thread(G):
+    """cpu_oracle_single_thread_estimate in a child process with OMP_NUM_THREADS=1 and one torch
+    thread. Returns (ms per frame, ms per stage), or None if the child fails."""
+    fd, path = tempfile.mkstemp(suffix=".npy")
+    os.close(fd)
+    np.save(path, G)
     code = ("import json, torch; torch.set_num_threads(1); import bench; "
-            f"r = bench.cpu_oracle_frame_estimate({float(budget_s)!r}); print(json.dumps([r[0], r[4]]))")
+            f"r = bench.cpu_oracle_single_thread_estimate({path!r}); print(json.dumps([r[0], r[1]]))")
     env = dict(os.environ, OMP_NUM_THREADS="1")
     try:
         out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
-                             timeout=max(120.0, 10 * budget_s))
+                             timeout=600)
         ms, stages = json.loads(out.stdout.strip().splitlines()[-1])
         return float(ms), stages
     except Exception:
         return None
+    finally:
+        os.unlink(path)
 
 
 def cpu_model() -> str:
@@ -303,26 +340,53 @@ def cpu_model() -> str:
     return platform.machine()
 
 
+def bench_config(world: int) -> dict:
+    """The workload both arms measure (the same dict in the reference arm's line)."""
+    return {"workload": "city256: 256x256x128 froxels (s=8), 2,001-box procedural city seed 0, "
+                        f"{N_VIEWCELLS} street viewcells cycled, d=4 (128 ch), sparse U-Net 32/64/128/256",
+            "batch": 1, "parallelism": "replicas" if world > 1 else "single"}
+
+
+REFERENCE_BUDGET_S = 150.0
+
+
 def run_reference(args):
+    """The reference arm: the oracle (the paper has no code) running whole frames of the same
+    workload on the host cores, nothing sampled or scaled: each step is one full frame. A full
+    frame takes seconds, so the steps run are capped by a wall-clock budget and the line declares
+    the steps and warm-up frames that actually ran."""
     ws_, rank, _ = dist_env()
     if rank != 0:
         return
-    steps = []
-    per_step = max(2.0, min(12.0, 150.0 / max(1, args.steps + args.warmup)))
-    for i in range(args.warmup + args.steps):
-        ms, desc, cores, _, _ = cpu_oracle_frame_estimate(per_step)
-        if i >= args.warmup:
-            steps.append(ms)
-    ms = statistics.mean(steps)
+    warm = min(args.warmup, 1)
+    t0 = time.perf_counter()
+    for i in range(warm):
+        cpu_oracle_frame(i)
+    times, stages_acc = [], {}
+    per = None
+    for i in range(args.steps):
+        if per is not None and (time.perf_counter() - t0) + per > REFERENCE_BUDGET_S:
+            break
+        ms, stages, _, _, _ = cpu_oracle_frame(warm + i)
+        times.append(ms)
+        per = ms / 1e3
+        for k, v in stages.items():
+            stages_acc[k] = stages_acc.get(k, 0.0) + v
+    n = len(times)
+    ms = statistics.mean(times)
     fps = 1000.0 / ms
-    line = {"impl": "reference", "metric": METRIC, "value": round(fps, 4), "unit": "frames/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "city256: 256x256x128 froxels, 2,001-box city seed 0, d=4, U-Net 32/64/128/256",
-                       "batch": 1},
-            "cpu_baseline": {"value": round(fps, 4), "unit": "frames/s", "cores": cores, "kind": "oracle",
-                             "sample": desc},
-            "e2e": {"value": round(fps, 4), "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    cores = os.cpu_count()
+    desc = (f"{n} whole frames of the FP64 / binary32-mirror oracle (froxelization of all 65,536 columns at "
+            f"s=8, interleave, U-Net, de-interleave; nothing scaled), viewcells cycled as in the GPU arm")
+    line = {"impl": "reference", "metric": METRIC, "value": round(fps, 5), "unit": "frames/s", "n_gpus": args.gpus,
+            "steps": n, "warmup": warm, "steps_requested": args.steps, "warmup_requested": args.warmup,
+            "ms_per_step": round(ms, 2), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": bench_config(1),
+            "stage_ms": {k: round(v / n, 1) for k, v in stages_acc.items()},
+            "cpu_baseline": {"value": round(fps, 5), "unit": "frames/s", "cores": cores, "kind": "oracle",
+                             "sample": desc, "cpu_model": cpu_model()},
+            "e2e": {"value": round(fps, 5), "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": round(time.perf_counter() - t0, 1)}
     print(json.dumps(line), flush=True)
 
 
@@ -654,40 +718,47 @@ def run_ours(args):
     torch.cuda.synchronize()
     st = torch.cuda.current_stream()
 
-    def timed_replays(graph, steps, warmup, per_step=None, mark_last=False):
+    def timed_replays(graph, steps, warmup, per_step=None, mark_last=False, frames=1):
+        """Per step `frames` frames, each after an L2 flush and timed alone with CUDA events on the
+        launching stream; returns the per-frame times (ms) of the timed steps."""
         out = []
         for i in range(warmup + steps):
-            flush.zero_()
-            cam_buf.copy_(cams_d[i % len(cams_d)])
-            s = torch.cuda.Event(enable_timing=True)
-            e = torch.cuda.Event(enable_timing=True)
-            last = mark_last and i == warmup + steps - 1
-            if last:    # the last timed frame in an NVTX range "frame", for a profiler to select
-                torch.cuda.nvtx.range_push("frame")
-            s.record(st)
-            graph.replay()
-            e.record(st)
-            if last:
-                torch.cuda.nvtx.range_pop()
-            if per_step is not None:
-                torch.cuda.synchronize()
+            for f in range(frames):
+                flush.zero_()
+                cam_buf.copy_(cams_d[(i * frames + f) % len(cams_d)])
+                s = torch.cuda.Event(enable_timing=True)
+                e = torch.cuda.Event(enable_timing=True)
+                last = mark_last and i == warmup + steps - 1 and f == frames - 1
+                if last:    # the last timed frame in an NVTX range "frame", for a profiler to select
+                    torch.cuda.nvtx.range_push("frame")
+                s.record(st)
+                graph.replay()
+                e.record(st)
+                if last:
+                    torch.cuda.nvtx.range_pop()
+                if per_step is not None:
+                    torch.cuda.synchronize()
+                    if i >= warmup:
+                        per_step()
                 if i >= warmup:
-                    per_step()
-            if i >= warmup:
-                out.append((s, e))
+                    out.append((s, e))
         torch.cuda.synchronize()
         return [s.elapsed_time(e) for s, e in out]
 
     # ---- device-timed BF16 frames (the headline) ----------------------------------------------
+    # a few untimed frames give the frame time that sizes the timed region (about 1 s of frames)
+    est = statistics.median(timed_replays(g16, 5, 2))
+    fps_step = frames_per_step(args.steps, est) if args.frames_per_step <= 0 else args.frames_per_step
     clocks = Clocks(torch.cuda.current_device())
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    t_bf16 = timed_replays(g16, args.steps, args.warmup, mark_last=True)
+    t_bf16 = timed_replays(g16, args.steps, args.warmup, mark_last=True, frames=fps_step)
     clk = clocks.stop()
-    launches_timed = launches_per_frame * args.steps
-    ms = max_over_ranks(statistics.mean(t_bf16), dev)
+    launches_timed = launches_per_frame * args.steps * fps_step
+    ms_frame = max_over_ranks(statistics.mean(t_bf16), dev)
+    ms = ms_frame * fps_step
     if ops.npvs_check_status(nf.status) != 0:
         raise RuntimeError("device status set during the timed frames")
 
@@ -702,26 +773,42 @@ def run_ours(args):
     stage_ms = {k: v / args.steps for k, v in acc.items()}
 
     # ---- FP32 path, same inputs ------------------------------------------------------------------
-    t_f32 = timed_replays(g32, max(5, args.steps // 2), 2)
+    t_f32 = timed_replays(g32, max(5, args.steps // 2), 2, frames=max(1, fps_step // 2))
     ms32 = statistics.mean(t_f32)
 
     # ---- end to end through the public API with host buffers -------------------------------------
     boxes_h = torch.from_numpy(boxes).pin_memory()
     cams_h = [ops.cameras_to_device([c], "cpu").pin_memory() for c in cams]
     pvs_h = torch.empty(nf.pvs.numel(), dtype=torch.int32).pin_memory()
-    ev = []
-    for i in range(args.warmup + args.steps):
-        flush.zero_()
-        s = torch.cuda.Event(enable_timing=True)
-        e = torch.cuda.Event(enable_timing=True)
-        s.record(st)
-        boxes_d.copy_(boxes_h, non_blocking=True)
-        nf.frame_from_host(g16, cam_buf, cams_h[i % len(cams_h)], pvs_h)
-        e.record(st)
-        if i >= args.warmup:
-            ev.append((s, e))
-    torch.cuda.synchronize()
-    ms_e2e = max_over_ranks(statistics.mean(s.elapsed_time(e) for s, e in ev), dev)
+    def e2e_frames(run_one, steps, warmup, frames):
+        ev = []
+        for i in range(warmup + steps):
+            for f in range(frames):
+                flush.zero_()
+                s = torch.cuda.Event(enable_timing=True)
+                e = torch.cuda.Event(enable_timing=True)
+                s.record(st)
+                boxes_d.copy_(boxes_h, non_blocking=True)
+                run_one(cams_h[(i * frames + f) % len(cams_h)])
+                e.record(st)
+                if i >= warmup:
+                    ev.append((s, e))
+        torch.cuda.synchronize()
+        return statistics.mean(s.elapsed_time(e) for s, e in ev)
+
+    # (a) the captured graph of npvs_forward replayed per frame; (b) one npvs_forward call through
+    # the C ABI per frame (host-side argument checks and launches inside the timed region)
+    ms_e2e = max_over_ranks(e2e_frames(lambda c: nf.frame_from_host(g16, cam_buf, c, pvs_h), args.steps,
+                                       args.warmup, fps_step), dev)
+
+    def abi_call(c):
+        cam_buf.copy_(c, non_blocking=True)
+        nf.run(boxes_d, off_d, nb, cam_buf)
+        pvs_h.copy_(nf.pvs, non_blocking=True)
+
+    ms_e2e_abi = max_over_ranks(e2e_frames(abi_call, args.steps, args.warmup, max(1, fps_step // 2)), dev)
+    if ops.npvs_check_status(nf.status) != 0:
+        raise RuntimeError("device status set during the end-to-end frames")
     h2d = boxes_h.numel() * 4 + cams_h[0].numel()
     d2h = pvs_h.numel() * 4
 
@@ -747,49 +834,57 @@ def run_ours(args):
              "boxes_per_s": round(nb * 1000.0 / ms_prune, 1),
              "what": "npvs_prune of every scene box against the frame's PVS (one CUDA graph replay)"}
 
-    # ---- roofline of the dominant kernel: the sparse-convolution kernels (conv_tc + reduce) take
-    # most of the frame, so their algorithmic work over all layers is set against their summed time
+    # ---- roofline. The headline one is the whole frame's (the slower of its contraction FLOPs at
+    # the tensor peak and its algorithmic bytes at the HBM peak, against the measured ms per frame);
+    # the convolution kernels' own fraction (their algorithmic work against their summed stage
+    # times) is reported beside it.
     alg = layer_algorithmic(fp, wl)
     conv_keys = [k for k in alg if k.startswith("conv:") and k in stage_ms]
-    dom = "conv (all %d layers)" % len(conv_keys)
-    a = {"bytes": sum(alg[k]["bytes"] for k in conv_keys), "flops": sum(alg[k]["flops"] for k in conv_keys)}
-    t_s = sum(stage_ms[k] for k in conv_keys) * 1e-3
-    t_tensor = a["flops"] / (tf_bf16 * 1e12)
-    t_hbm = a["bytes"] / (hbm_gbs * 1e9)
-    if t_tensor > t_hbm:
-        roof = {"bound": "tensor", "achieved": round(a["flops"] / t_s / 1e12, 3), "peak": tf_bf16, "unit": "TFLOP/s"}
-    else:
-        roof = {"bound": "hbm", "achieved": round(a["bytes"] / t_s / 1e9, 2), "peak": hbm_gbs, "unit": "GB/s"}
-    roof["frac"] = round(roof["achieved"] / roof["peak"], 5)
-    # DRAM bytes of the 37 convolution launches of one timed frame (ncu, caches not flushed between
-    # kernels, L2 flushed before the frame as here): profiles/city256_bf16_frame_launches.md
-    roof["traffic"] = conv_frame_traffic(tuned)
-    roof["time_ms"] = round(t_s * 1e3, 4)
-    roof["kernel"] = dom
-    roof["peak_source"] = peak_src
+
+    def roof_of(byts, flops, t_s):
+        if flops / (tf_bf16 * 1e12) > byts / (hbm_gbs * 1e9):
+            r = {"bound": "tensor", "achieved": round(flops / t_s / 1e12, 3), "peak": tf_bf16, "unit": "TFLOP/s"}
+        else:
+            r = {"bound": "hbm", "achieved": round(byts / t_s / 1e9, 2), "peak": hbm_gbs, "unit": "GB/s"}
+        r["frac"] = round(r["achieved"] / r["peak"], 5)
+        r["algorithmic_bytes"], r["algorithmic_flops"] = int(byts), int(flops)
+        r["time_ms"] = round(t_s * 1e3, 4)
+        r["peak_source"] = peak_src + " (MEASURED_PEAKS.json: copy GB/s, cuBLAS BF16 burst TFLOP/s)"
+        return r
+
     frame_bytes = sum(v["bytes"] for v in alg.values())
     frame_flops = sum(v["flops"] for v in alg.values())
-    frame_roof_ms = max(frame_flops / (tf_bf16 * 1e12), frame_bytes / (hbm_gbs * 1e9)) * 1e3
+    roof = roof_of(frame_bytes, frame_flops, ms_frame * 1e-3)
+    roof["kernel"] = "frame (every kernel of npvs_forward, one graph replay)"
+    roof["traffic"] = frame_traffic(tuned)
+    conv_roof = roof_of(sum(alg[k]["bytes"] for k in conv_keys), sum(alg[k]["flops"] for k in conv_keys),
+                        sum(stage_ms[k] for k in conv_keys) * 1e-3)
+    conv_roof["kernel"] = "conv (all %d layers: tcgen05 GEMM + gather-reduce kernels)" % len(conv_keys)
+    conv_roof["traffic"] = conv_frame_traffic(tuned)
 
     line = {
-        "metric": METRIC, "value": round(replica_rate(world, 1, ms), 3), "unit": "frames/s", "n_gpus": world,
+        "metric": METRIC, "value": round(replica_rate(world, fps_step, ms), 3), "unit": "frames/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
-        "ms_per_step_quantiles": step_quantiles(t_bf16),
+        "frames_per_step": fps_step, "ms_per_frame": round(ms_frame, 5),
+        "ms_per_frame_quantiles": step_quantiles(t_bf16),
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": "city256: 256x256x128 froxels (s=8), 2,001-box procedural city seed 0, "
-                               f"{N_VIEWCELLS} street viewcells cycled, d=4 (128 ch), sparse U-Net 32/64/128/256",
-                   "batch": 1, "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "flushed (256 MB write) before every timed step",
-                   "launch": "one CUDA graph replay of npvs_forward per frame"},
-        "e2e": {"value": round(replica_rate(world, 1, ms_e2e), 3), "unit": "frames/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+        "config": bench_config(world),
+        "timing": {"l2": "flushed (256 MB write) before every timed frame",
+                   "launch": "one CUDA graph replay of npvs_forward per frame",
+                   "step": f"{fps_step} frames, each after an L2 flush and timed alone with CUDA events",
+                   "timed_frames": len(t_bf16), "timed_frame_s": round(sum(t_bf16) / 1e3, 3)},
+        "e2e": {"value": round(replica_rate(world, 1, ms_e2e), 3), "unit": "frames/s", "h2d_bytes_per_step": h2d * fps_step,
+                "d2h_bytes_per_step": d2h * fps_step, "h2d_bytes_per_frame": h2d, "d2h_bytes_per_frame": d2h,
+                "what": "pinned host boxes and camera up, PVS bits down, one graph replay of npvs_forward per frame"},
+        "e2e_abi_call": {"value": round(replica_rate(world, 1, ms_e2e_abi), 3), "unit": "frames/s",
+                         "what": "as e2e, with one npvs_forward call through the C ABI per frame (no graph)"},
         "gpu_launches": int(launches_timed),
         "launches_per_frame": int(launches_per_frame),
-        "fp32_path": {"ms_per_frame": round(ms32, 4), "frames_per_s": round(1000.0 / ms32, 3)},
+        "fp32_path": {"ms_per_frame": round(ms32, 4), "frames_per_s": round(1000.0 / ms32, 3),
+                      "bf16_speedup": round(ms32 / ms_frame, 3)},
         "stage_ms": {k: round(v, 4) for k, v in sorted(stage_ms.items(), key=lambda kv: -kv[1])},
         "roofline": roof,
-        "frame_roofline": {"bytes": frame_bytes, "flops": frame_flops, "roof_ms": round(frame_roof_ms, 5),
-                           "frac": round(frame_roof_ms / ms, 5)},
+        "conv_roofline": conv_roof,
         "active_sites": [int(lv.n_rows.item()) for lv in fp.levels],
         "autotuned": {k: [tuned_label(v[0]), round(v[1], 2) if v[1] == v[1] else None] for k, v in tuned.items()},
     }
@@ -811,14 +906,21 @@ def run_ours(args):
         del g16, g32, g16t
         line["train"] = run_train(args, dev, flush)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cms, desc, cores, spent, cstages = cpu_oracle_frame_estimate(args.cpu_seconds)
-        line["cpu_baseline"] = {"value": round(1000.0 / cms, 5), "unit": "frames/s", "cores": cores, "kind": "oracle",
-                                "sample": desc, "seconds": round(spent, 1), "stage_ms": cstages,
+        t0 = time.perf_counter()
+        cms, cstages, G, logits, coords = cpu_oracle_frame(0)
+        spent = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": round(1000.0 / cms, 5), "unit": "frames/s", "cores": os.cpu_count(),
+                                "kind": "oracle", "seconds": round(spent, 1), "stage_ms": cstages,
+                                "sample": "one whole frame of the FP64 / binary32-mirror oracle (froxelization of all "
+                                          "65,536 columns at s=8, interleave, U-Net, de-interleave; nothing scaled)",
+                                "loss_ms_not_in_frame": round(cpu_oracle_loss_ms(G, logits, coords), 1),
                                 "cpu_model": cpu_model()}
-        single = cpu_oracle_single_thread(max(4.0, args.cpu_seconds / 2))
-        if single is not None:
-            line["cpu_baseline"]["single_thread"] = {"value": round(1000.0 / single[0], 5), "unit": "frames/s",
-                                                     "threads": 1, "stage_ms": single[1]}
+        if not args.no_single_thread:
+            single = cpu_oracle_single_thread(G)
+            if single is not None:
+                line["cpu_baseline"]["single_thread"] = {
+                    "value": round(1000.0 / single[0], 5), "unit": "frames/s", "threads": 1, "stage_ms": single[1],
+                    "sample": "froxelization of 2,048 random columns scaled to 65,536; the rest of the frame whole"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

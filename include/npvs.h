@@ -201,8 +201,9 @@ npvs_status npvs_check_status(int32_t* status, void* stream);
  * stop issuing copies and MMAs, wait (at most ~1e7 SM cycles more per outstanding stage, whatever the
  * bound) for those already in flight, free its tensor memory and return; NPVS_ERR_TIMEOUT is OR-ed
  * into the convolution's status word. The outputs of a timed-out call are undefined, and a
- * convolution workspace it used must be zero-filled again before its next use. A small bound
- * (hundreds of cycles) makes ordinary waits expire: that is how the timeout path is tested.
+ * convolution workspace it used must be zero-filled again before its next use. A bound of a few
+ * cycles makes every wait that is not satisfied when first tested expire (bounds below 1e6 cycles
+ * are kept by polling; each poll costs a few hundred cycles): that is how the timeout path is tested.
  * Returns NPVS_ERR_INVALID_ARG for cycles < 0. */
 npvs_status npvs_set_wait_limit(int64_t cycles, int64_t* previous);
 

@@ -77,6 +77,14 @@ def test_tuned_labels_and_traffic_selection():
 
 def test_step_quantiles_nearest_rank():
     import bench
-    assert bench.step_quantiles([1.0] * 98 + [2.0, 3.0]) == {"p50": 1.0, "p99": 2.0}
-    assert bench.step_quantiles(range(1, 51)) == {"p50": 25.5, "p99": 50.0}
-    assert bench.step_quantiles([]) == {"p50": None, "p99": None}
+    assert bench.step_quantiles([1.0] * 98 + [2.0, 3.0]) == {"p50": 1.0, "n": 100, "p99": 2.0}
+    # fewer than 100 samples: no 99th percentile, the maximum is labelled as such
+    assert bench.step_quantiles(range(1, 51)) == {"p50": 25.5, "n": 50, "max": 50.0}
+    assert bench.step_quantiles([]) == {"p50": None, "n": 0}
+
+
+def test_frames_per_step_fills_about_a_second():
+    import bench
+    assert bench.frames_per_step(20, 0.5) == 100          # 20 steps x 100 frames x 0.5 ms = 1 s
+    assert bench.frames_per_step(50, 30.0) == 1
+    assert bench.frames_per_step(0, 0.0) >= 1
