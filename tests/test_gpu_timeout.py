@@ -46,12 +46,13 @@ def conv_case(cin, cout, form, seed):
                          n_in=lv.n_rows, cap_in=lv.capacity, status=status, form=form)
     wp = torch.empty(ops.npvs_packed_weight_bytes(P.KIND["subm3"], cin, cout), dtype=torch.uint8, device=DEV)
     ops.npvs_pack_weights(P.KIND["subm3"], cin, cout, torch.from_numpy(w).to(DEV), wp)
-    return desc, status, xin, wp, torch.from_numpy(b).to(DEV), ref, fine.n, lv.capacity
+    # the levels are returned too: the descriptor holds raw pointers into them
+    return desc, status, xin, wp, torch.from_numpy(b).to(DEV), ref, fine.n, lv.capacity, lvs
 
 
 def run_fwd(case, with_workspace):
     L, ops, _ = lib()
-    desc, status, xin, wp, b, ref, n, cap = case
+    desc, status, xin, wp, b, ref, n, cap, _ = case
     ws = None
     if with_workspace:   # a fresh zero-filled workspace each call
         ws = ops.conv_workspace(ops.npvs_conv_workspace_bytes(desc), DEV)
@@ -93,7 +94,7 @@ def test_wgrad_wait_timeout_is_reported(short_waits):
     """The BF16 backward (dgrad on the cp.async gather, weight gradient on tcgen05) under the short
     bound reports the timeout; the default bound is restored by the fixture."""
     L, ops, P = lib()
-    desc, status, xin, wp, b, ref, n, cap = conv_case(16, 16, 0, seed=3)
+    desc, status, xin, wp, b, ref, n, cap, lvs = conv_case(16, 16, 0, seed=3)
     cin = cout = 16
     w = torch.from_numpy(I.kaiming_uniform([I.Layer("t", "subm3", cin, cout, True)], seed=5)[0][0]).to(DEV)
     y = torch.zeros(cap, cout, dtype=torch.bfloat16, device=DEV)
