@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-single-thread", action="store_true", help="skip the one-thread CPU-oracle estimate")
+    ap.add_argument("--chain-level", type=int, default=-1,
+                    help="layer chain level of the headline frame (-1: the fastest of 0..levels-1 on this GPU)")
     ap.add_argument("--frames-per-step", type=int, default=0,
                     help="frames timed per step (0: enough for about 1 s of timed frames over all steps)")
     ap.add_argument("--no-train", action="store_true", help="skip the training-step measurement")
@@ -705,17 +707,6 @@ def run_ours(args):
     if args.save_tuned:
         with open(args.save_tuned, "w") as fh:
             json.dump(fp.tuned_configs(), fh)
-    # the timed frames go through the public single call npvs_forward (same kernels as fp)
-    nb = len(boxes)
-    nf = P.NativeFrame(wl, net, 1, L.BF16, max_boxes=nb, device=dev, tuned=fp.descs)
-    nf32 = P.NativeFrame(wl, net, 1, L.F32, max_boxes=nb, device=dev)
-    l0 = ops.npvs_launch_count()
-    g16 = nf.capture(boxes_d, off_d, nb, cam_buf)
-    launches_per_frame = (ops.npvs_launch_count() - l0) // 2      # warm-up run + captured run
-    g32 = nf32.capture(boxes_d, off_d, nb, cam_buf)
-    timer = P.StageTimer()
-    g16t = fp.capture(boxes_d, off_d, cam_buf, timer=timer)
-    torch.cuda.synchronize()
     st = torch.cuda.current_stream()
 
     def timed_replays(graph, steps, warmup, per_step=None, mark_last=False, frames=1):
@@ -744,6 +735,30 @@ def run_ours(args):
                     out.append((s, e))
         torch.cuda.synchronize()
         return [s.elapsed_time(e) for s, e in out]
+
+    # the timed frames go through the public single call npvs_forward (same kernels as fp). The
+    # layer chain (the coarse levels' layers in one persistent launch, npvs_net_desc.chain_level)
+    # is chosen by timing the captured frame at each level on this GPU (0: no chain)
+    nb = len(boxes)
+    chain_ms = {}
+    levels = [args.chain_level] if args.chain_level >= 0 else list(range(0, fp.n_levels))
+    for k in levels:
+        nfk = P.NativeFrame(wl, net, 1, L.BF16, max_boxes=nb, device=dev, tuned=fp.descs, chain_level=k)
+        gk = nfk.capture(boxes_d, off_d, nb, cam_buf)
+        chain_ms[k] = statistics.median(timed_replays(gk, 30, 3))
+        if ops.npvs_check_status(nfk.status) != 0:
+            raise RuntimeError(f"device status set with chain level {k}")
+        del gk, nfk
+    chain_level = min(chain_ms, key=chain_ms.get)
+    nf = P.NativeFrame(wl, net, 1, L.BF16, max_boxes=nb, device=dev, tuned=fp.descs, chain_level=chain_level)
+    nf32 = P.NativeFrame(wl, net, 1, L.F32, max_boxes=nb, device=dev)
+    l0 = ops.npvs_launch_count()
+    g16 = nf.capture(boxes_d, off_d, nb, cam_buf)
+    launches_per_frame = (ops.npvs_launch_count() - l0) // 2      # warm-up run + captured run
+    g32 = nf32.capture(boxes_d, off_d, nb, cam_buf)
+    timer = P.StageTimer()
+    g16t = fp.capture(boxes_d, off_d, cam_buf, timer=timer)
+    torch.cuda.synchronize()
 
     # ---- device-timed BF16 frames (the headline) ----------------------------------------------
     # a few untimed frames give the frame time that sizes the timed region (about 1 s of frames)
@@ -880,9 +895,15 @@ def run_ours(args):
                          "what": "as e2e, with one npvs_forward call through the C ABI per frame (no graph)"},
         "gpu_launches": int(launches_timed),
         "launches_per_frame": int(launches_per_frame),
+        "chain": {"level": chain_level, "layers": [wl.layers[i].name for i in P.chain_layer_indices(wl.layers, chain_level)],
+                  "ms_per_frame_by_level": {str(k): round(v, 4) for k, v in chain_ms.items()},
+                  "what": "layers of levels >= level run as one persistent cooperative kernel (0: every layer "
+                          "its own launch); the level is chosen by timing the captured frame at each level"},
         "fp32_path": {"ms_per_frame": round(ms32, 4), "frames_per_s": round(1000.0 / ms32, 3),
                       "bf16_speedup": round(ms32 / ms_frame, 3)},
         "stage_ms": {k: round(v, 4) for k, v in sorted(stage_ms.items(), key=lambda kv: -kv[1])},
+        "stage_ms_what": "stage events in a graph of the frame built entry point by entry point (no layer chain); "
+                         "the events break the launch overlap, so the stages add up to more than ms_per_frame",
         "roofline": roof,
         "conv_roofline": conv_roof,
         "active_sites": [int(lv.n_rows.item()) for lv in fp.levels],

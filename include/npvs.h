@@ -357,7 +357,15 @@ typedef struct {
 /* A frame plan: froxel grid (batch = number of viewcells), interleave factor d, input channels
  * (1 occupancy, 2 + depth), supersampling, dtype (BF16 or F32), threshold tau, the largest box
  * count of a call, level capacities in permille of each level's sites (0 = all sites: no overflow
- * possible), and the layers (host array). */
+ * possible), the layers (host array), and chain_level:
+ *  - 0: every layer is its own launch (npvs_sparse_conv_fwd with the layer's tune fields);
+ *  - k >= 1: the down conv into level k, every layer below it and the up conv out of it run as one
+ *    persistent cooperative launch (one CTA per SM, grid-wide barriers between phases) in the
+ *    product form (a tcgen05 GEMM T = x [W_0 | W_1 | ...], then the gather-reduce over existing
+ *    neighbours in fixed tap order), bitwise equal to those layers launched one by one in the
+ *    product form (tune_form 2). Their tune fields are not used. Needs BF16, cin % 32 == 0 and
+ *    cout % 16 == 0 for each of those layers and at most 24 of them (else NPVS_ERR_UNSUPPORTED).
+ *    A timed-out wait in it reports NPVS_ERR_TIMEOUT; the workspace must then be zero-filled again. */
 typedef struct {
     npvs_grid grid;
     int32_t d, in_ch, supersample, dtype;
@@ -366,9 +374,12 @@ typedef struct {
     int32_t capacity_permille;
     int32_t n_layers;
     const npvs_layer* layers;
+    int32_t chain_level;
 } npvs_net_desc;
 
-/* Bytes of the npvs_forward workspace of a plan (0 if the plan is invalid). */
+/* Bytes of the npvs_forward workspace of a plan (0 if the plan is invalid). The workspace must be
+ * zero-filled before its first use (it holds the convolutions' split-K counters and the layer
+ * chain's barrier words, which every call leaves at zero again). */
 size_t npvs_forward_workspace_bytes(const npvs_net_desc* net);
 
 /* The whole per-frame path (Sec. 3.1-3.3): npvs_froxelize -> npvs_interleave -> neighbour maps and

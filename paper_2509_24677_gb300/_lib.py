@@ -76,7 +76,7 @@ class NetLayer(ctypes.Structure):
 class NetDesc(ctypes.Structure):
     _fields_ = [("grid", Grid), ("d", I32), ("in_ch", I32), ("supersample", I32), ("dtype", I32),
                 ("tau", ctypes.c_float), ("max_boxes", I32), ("capacity_permille", I32), ("n_layers", I32),
-                ("layers", ctypes.POINTER(NetLayer))]
+                ("layers", ctypes.POINTER(NetLayer)), ("chain_level", I32)]
 
 
 LOSS_TERMS = 12

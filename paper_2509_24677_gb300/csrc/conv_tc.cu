@@ -75,17 +75,6 @@ struct TcParams {
     long long wait_limit;  // bound of every mbarrier wait, SM cycles (npvs_set_wait_limit)
 };
 
-// Shared-memory matrix descriptor of a K-major operand with rows of RB bytes (128: 128-byte
-// swizzle, 64: 64-byte swizzle); 8-row groups are 8 * RB bytes apart.
-__device__ __forceinline__ uint64_t make_sdesc(uint32_t saddr, int RB) {
-    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;                        // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)((8 * RB) >> 4) << 32;          // stride byte offset
-    d |= (uint64_t)1 << 46;                        // descriptor version
-    d |= (uint64_t)(RB == 128 ? 2 : 4) << 61;      // 128-byte or 64-byte swizzle
-    return d;
-}
-
 __device__ __forceinline__ void tma_gather4(uint32_t dst, const CUtensorMap* tm, int col, int r0, int r1, int r2,
                                             int r3, uint32_t bar) {
     asm volatile(
@@ -93,11 +82,6 @@ __device__ __forceinline__ void tma_gather4(uint32_t dst, const CUtensorMap* tm,
         " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
         "l"(reinterpret_cast<uint64_t>(tm)), "r"(col), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(bar)
         : "memory");
-}
-
-// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major.
-__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // ---- the kernel -----------------------------------------------------------------------------
@@ -122,13 +106,6 @@ __device__ __forceinline__ void gather_teardown(uint32_t it, volatile int* warp_
             mbar_wait(full0 + 8 * (j % S), (j / S) & 1, abort_flag, limit);
     }
     __syncwarp();
-}
-
-__device__ __forceinline__ void tma_tile2d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(bar)
-        : "memory");
 }
 
 // Epilogue for 16 consecutive GEMM columns (from ng; bias of those columns in sb) of GEMM row n:
@@ -903,23 +880,6 @@ int win_rows_for(int BN, int RB, int G, int* stages) {
             }
     }
     return 0;
-}
-
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_tiled() {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
-        void* f = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(f);
-    }
-    return fn;
 }
 
 template <int LAG, int PW>

@@ -14,7 +14,9 @@
 
 #include <mutex>
 
+#include "chain.cuh"
 #include "common.cuh"
+#include "conv_tc.cuh"
 
 namespace npvs {
 namespace {
@@ -31,6 +33,7 @@ struct FwdPlan {
     std::vector<int> skip_of;   // layer whose output is added after this layer's ReLU (-1: none)
     std::vector<size_t> act_off;
     size_t el = 2;
+    int chain_first = -1, chain_last = -1;  // layers run as one persistent launch (chain_level)
 };
 
 npvs_status plan_net(const npvs_net_desc& n, FwdPlan* P) {
@@ -79,6 +82,21 @@ npvs_status plan_net(const npvs_net_desc& n, FwdPlan* P) {
         Z /= 2;
     }
     P->el = n.dtype == NPVS_BF16 ? 2 : 4;
+    if (n.chain_level > 0) {
+        // the down conv into level chain_level ... the up conv out of it
+        NPVS_REQUIRE(n.dtype == NPVS_BF16 && n.chain_level < P->n_levels, NPVS_ERR_UNSUPPORTED,
+                     "npvs_forward: chain_level needs BF16 and a level below the top");
+        for (int i = 0; i < n.n_layers && P->chain_first < 0; ++i)
+            if (n.layers[i].kind == NPVS_CONV_DOWN2 && P->level_of[i] == n.chain_level) P->chain_first = i;
+        for (int i = P->chain_first + 1; P->chain_first >= 0 && i < n.n_layers && P->chain_last < 0; ++i)
+            if (n.layers[i].kind == NPVS_CONV_UP2 && P->level_of[i] == n.chain_level - 1) P->chain_last = i;
+        NPVS_REQUIRE(P->chain_first >= 0 && P->chain_last > P->chain_first &&
+                         P->chain_last - P->chain_first < kChainMaxLayers,
+                     NPVS_ERR_UNSUPPORTED, "npvs_forward: no chain of at most 24 layers at chain_level");
+        for (int i = P->chain_first; i <= P->chain_last; ++i)
+            NPVS_REQUIRE(chain_layer_supported(n.layers[i].kind, n.layers[i].cin, n.layers[i].cout),
+                         NPVS_ERR_UNSUPPORTED, "npvs_forward: a chained layer needs cin % 32 == 0 and cout % 16 == 0");
+    }
     return NPVS_OK;
 }
 
@@ -140,8 +158,11 @@ npvs_conv_desc layer_desc(const npvs_net_desc& n, const FwdPlan& P, const std::v
 
 // Carves the workspace; with base == nullptr only sizes it. Returns the bytes used.
 size_t carve(const npvs_net_desc& n, FwdPlan& P, void* base, size_t size, std::vector<FwdLevel>& L, void** feats,
-             std::vector<void*>& acts, void** conv_ws, size_t* conv_ws_bytes, void** scratch, size_t* scratch_bytes) {
+             std::vector<void*>& acts, void** conv_ws, size_t* conv_ws_bytes, void** scratch, size_t* scratch_bytes,
+             unsigned int** chain_bar = nullptr) {
     Arena ar(base, base ? size : 0);
+    unsigned int* cb = ar.take<unsigned int>(2);  // the layer chain's grid-barrier words
+    if (chain_bar) *chain_bar = cb;
     L.assign(P.n_levels, FwdLevel());
     for (int li = 0; li < P.n_levels; ++li) {
         FwdLevel& v = L[li];
@@ -244,7 +265,8 @@ extern "C" npvs_status npvs_forward(const npvs_net_desc* net, const float* boxes
     const size_t need = carve(n, P, nullptr, 0, L, &feats, acts, &cw, &cwb, &sc, &scb);
     NPVS_REQUIRE(workspace && workspace_bytes >= need, NPVS_ERR_WORKSPACE,
                  "npvs_forward: workspace smaller than npvs_forward_workspace_bytes()");
-    carve(n, P, workspace, workspace_bytes, L, &feats, acts, &cw, &cwb, &sc, &scb);
+    unsigned int* chain_bar = nullptr;
+    carve(n, P, workspace, workspace_bytes, L, &feats, acts, &cw, &cwb, &sc, &scb, &chain_bar);
     cudaStream_t st = as_stream(stream);
 
     NPVS_TRY(npvs_froxelize(boxes, box_offsets, n_boxes, cams, n.grid, n.supersample, occ_bits, sc, scb, st));
@@ -282,6 +304,37 @@ extern "C" npvs_status npvs_forward(const npvs_net_desc* net, const float* boxes
         if (!joined && !level0_only) {  // the first layer that reads a coarser level's rulebooks
             if (cudaStreamWaitEvent(st, side.join, 0) != cudaSuccess) return check_launch("npvs_forward: join");
             joined = true;
+        }
+        if (i == P.chain_first) {  // the chained layers, one persistent launch
+            ChainLayerHost cl[kChainMaxLayers];
+            float* T = nullptr;
+            for (int j = i; j <= P.chain_last; ++j) {
+                npvs_conv_desc d = layer_desc(n, P, L, j, status);
+                d.workspace = cw;
+                d.workspace_bytes = cwb;
+                if (!T) T = conv_product_tiles(d);
+                ChainLayerHost& h = cl[j - i];
+                h.kind = d.kind;
+                h.cin = d.cin;
+                h.cout = d.cout;
+                h.relu = d.relu;
+                h.x = a;
+                h.w = n.layers[j].w;
+                h.bias = n.layers[j].bias;
+                h.skip = P.skip_of[j] >= 0 ? acts[P.skip_of[j]] : nullptr;
+                h.y = acts[j];
+                h.map = d.map;
+                h.n_in = d.n_in;
+                h.n_out = d.n_out;
+                h.rows_x = d.cap_in;
+                h.cap_out = d.cap_out;
+                a = acts[j];
+            }
+            NPVS_REQUIRE(T != nullptr, NPVS_ERR_WORKSPACE, "npvs_forward: no product tiles for the layer chain");
+            const size_t T_bytes = (size_t)((const char*)cw + cwb - (const char*)T);
+            NPVS_TRY(chain_launch(cl, P.chain_last - i + 1, T, T_bytes, chain_bar, status, st));
+            i = P.chain_last;
+            continue;
         }
         npvs_conv_desc d = layer_desc(n, P, L, i, status);
         d.workspace = cw;

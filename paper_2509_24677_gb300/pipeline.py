@@ -119,6 +119,24 @@ class Net:
         return self.b32
 
 
+def chain_layer_indices(layers, chain_level: int) -> List[int]:
+    """Indices of the layers npvs_forward runs as one persistent launch for `chain_level` (0: none):
+    the down conv into that level through the up conv out of it."""
+    if chain_level <= 0:
+        return []
+    lv, first = 0, None
+    for i, l in enumerate(layers):
+        if l.kind == "down2":
+            lv += 1
+            if first is None and lv == chain_level:
+                first = i
+        elif l.kind == "up2":
+            lv -= 1
+            if first is not None and lv == chain_level - 1:
+                return list(range(first, i + 1))
+    return []
+
+
 class FramePipeline:
     """Buffers and launch sequence of one frame (batch of viewcells) for a workload."""
 
@@ -326,6 +344,12 @@ class FramePipeline:
         torch.cuda.synchronize()
         return chosen
 
+    def use_chain_forms(self, chain_level: int):
+        """Runs the layers that npvs_forward chains at `chain_level` in the product form, the form
+        the chain computes, so that this frame and NativeFrame(chain_level=...) agree bit for bit."""
+        for i in chain_layer_indices(self.net.layers, chain_level):
+            self._apply_cfg(i, dict(tune_form=2))
+
     def _apply_cfg(self, i: int, cfg: dict):
         for f in self.TUNE_FIELDS:
             setattr(self.descs[i], f, int(cfg.get(f, 0)))
@@ -405,8 +429,10 @@ class NativeFrame:
     FramePipeline's descriptors) copies per-layer kernel configurations chosen by its autotuner."""
 
     def __init__(self, wl, net: Net, batch: int = 1, dtype: int = L.BF16, tau: float = 0.5, max_boxes: int = 4096,
-                 device="cuda", capacity_frac: float = 1.0, tuned: Optional[Sequence[L.ConvDesc]] = None):
+                 device="cuda", capacity_frac: float = 1.0, tuned: Optional[Sequence[L.ConvDesc]] = None,
+                 chain_level: int = 0):
         self.wl, self.net, self.B, self.dtype = wl, net, batch, dtype
+        self.chain_level = chain_level
         W = net.operands(dtype)
         Bs = net.biases(dtype)
         self._keep = (W, Bs)
@@ -422,7 +448,7 @@ class NativeFrame:
         permille = 0 if capacity_frac >= 1.0 else max(1, int(round(capacity_frac * 1000)))
         self.grid = L.Grid(wl.W, wl.H, wl.D, batch)
         self.desc = L.NetDesc(self.grid, wl.d, wl.in_ch, wl.supersample, dtype, tau, max_boxes, permille, n,
-                              self.layers_c)
+                              self.layers_c, chain_level)
         nbytes = ops.npvs_forward_workspace_bytes(self.desc)
         if nbytes == 0:
             raise ValueError("npvs_forward: invalid network plan")

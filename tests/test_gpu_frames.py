@@ -60,7 +60,7 @@ def oracle_refs(wl, which):
     return _REFS[key]
 
 
-def check_frame(wl, which, dt, tune=False):
+def check_frame(wl, which, dt, tune=False, chain_level=0):
     L, ops, P = lib()
     els = batch_inputs(wl, which)
     dtype = L.F32 if dt == "f32" else L.BF16
@@ -76,7 +76,7 @@ def check_frame(wl, which, dt, tune=False):
         fp = P.FramePipeline(wl, net, B, dtype)
         fp.autotune(bx, off, cams, reps=2)
         tuned = fp.descs
-    nf = P.NativeFrame(wl, net, B, dtype, max_boxes=len(boxes), tuned=tuned)
+    nf = P.NativeFrame(wl, net, B, dtype, max_boxes=len(boxes), tuned=tuned, chain_level=chain_level)
     nf.run(bx, off, len(boxes), cams)
     assert ops.npvs_check_status(nf.status) == 0
     occ_all = u32(nf.occ).reshape(B, wl.D, wl.H, wl.W // 32)
@@ -118,12 +118,13 @@ def check_frame(wl, which, dt, tune=False):
     return occs
 
 
-@pytest.mark.parametrize("dt,tune", [("bf16", False), ("bf16", True), ("f32", False)])
-def test_batch4_frame_matches_oracle_per_viewcell(dt, tune):
-    occs = check_frame(CITY128, "mixed", dt, tune)
+@pytest.mark.parametrize("dt,tune,chain", [("bf16", False, 0), ("bf16", True, 0), ("f32", False, 0), ("bf16", False, 1),
+                                           ("bf16", True, 2)])
+def test_batch4_frame_matches_oracle_per_viewcell(dt, tune, chain):
+    occs = check_frame(CITY128, "mixed", dt, tune, chain)
     assert max(occs) > 2 * min(occs)           # the elements' occupancy differs widely
 
 
-@pytest.mark.parametrize("dt,tune", [("bf16", False), ("bf16", True), ("f32", False)])
-def test_512_grid_network_shape_matches_oracle(dt, tune):
-    check_frame(CITY512_SHAPE, "large", dt, tune)
+@pytest.mark.parametrize("dt,tune,chain", [("bf16", False, 0), ("bf16", True, 0), ("f32", False, 0), ("bf16", False, 1)])
+def test_512_grid_network_shape_matches_oracle(dt, tune, chain):
+    check_frame(CITY512_SHAPE, "large", dt, tune, chain)

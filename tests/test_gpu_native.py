@@ -86,3 +86,102 @@ def test_native_forward_argument_errors():
     with pytest.raises(L.NpvsError) as e:
         ops.npvs_forward(nf.desc, bx, off, 41, cams, nf.occ, nf.pvs, None, nf.status, nf.ws)
     assert e.value.status == L.ERR_INVALID_ARG
+
+
+# ------------------------------------------------------------------------------------------
+# the layer chain: the coarse levels' layers in one persistent launch (npvs_net_desc.chain_level)
+# ------------------------------------------------------------------------------------------
+
+def chained_frames(name, batch, chain_level, tune=False, capacity_frac=1.0):
+    """The same frame through the entry points (the chained layers in the product form, which the
+    chain computes) and through npvs_forward with chain_level."""
+    L, ops, P = lib()
+    wl = I.workload(name)
+    vcs = I.city_viewcells(0, batch)
+    boxes = np.concatenate([I.city_boxes(0)] * batch).astype(np.float32)
+    nb = len(boxes) // batch
+    off = torch.tensor([nb * i for i in range(batch + 1)], dtype=torch.int32, device=DEV)
+    bx = torch.from_numpy(boxes).to(DEV)
+    cams = ops.cameras_to_device([ops.npvs_camera_setup(v, wl.D) for v in vcs])
+    ws, bs = I.kaiming_uniform(wl.layers, seed=0, bias_scale=0.05)
+    net = P.Net(wl.layers, ws, bs, DEV)
+    fp = P.FramePipeline(wl, net, batch, L.BF16, capacity_frac=capacity_frac)
+    if tune:
+        fp.autotune(bx, off, cams, reps=2)
+    fp.use_chain_forms(chain_level)
+    fp.run(bx, off, cams)
+    nf = P.NativeFrame(wl, net, batch, L.BF16, max_boxes=len(boxes), tuned=fp.descs, chain_level=chain_level,
+                       capacity_frac=capacity_frac)
+    nf.run(bx, off, len(boxes), cams)
+    assert ops.npvs_check_status(fp.status) == 0 and ops.npvs_check_status(nf.status) == 0
+    return wl, fp, nf, (bx, off, cams, len(boxes))
+
+
+@pytest.mark.parametrize("batch,chain_level,tune", [(1, 1, True), (1, 2, False), (1, 3, False), (2, 1, False)])
+def test_chain_equals_product_form_layers(batch, chain_level, tune):
+    """Every layer's output and the PVS of the chained frame are bitwise those of the layers launched
+    one by one (the chained ones in the product form): same MMAs, same fixed-order reductions."""
+    L, ops, P = lib()
+    wl, fp, nf, _ = chained_frames("city256", batch, chain_level, tune)
+    chained = P.chain_layer_indices(wl.layers, chain_level)
+    assert len(chained) == {1: 16, 2: 10, 3: 4}[chain_level]
+    lv_of = fp._level_of_layers()
+    for i, l in enumerate(wl.layers):
+        rows, nr = nf.layer_output(i)
+        n = int(nr.item())
+        assert n == int(fp.levels[lv_of[l.name]].n_rows.item()) and n > 0
+        assert torch.equal(rows[:n], fp.acts[l.name][:n]), l.name
+    assert torch.equal(fp.pvs, nf.pvs)
+
+
+def test_chain_graph_replay_and_repeat_calls():
+    """The chained frame captured in a CUDA graph and replayed, and called again eagerly, gives the
+    same bits each time (the grid-barrier words go back to zero after every launch)."""
+    L, ops, P = lib()
+    wl, fp, nf, (bx, off, cams, n) = chained_frames("city256", 1, 1)
+    pvs0 = nf.pvs.clone()
+    out0 = nf.layer_output(len(wl.layers) - 2)[0].clone()
+    g = nf.capture(bx, off, n, cams)
+    for _ in range(3):
+        nf.pvs.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(nf.pvs, pvs0)
+    nf.run(bx, off, n, cams)
+    assert ops.npvs_check_status(nf.status) == 0
+    assert torch.equal(nf.pvs, pvs0) and torch.equal(nf.layer_output(len(wl.layers) - 2)[0], out0)
+
+
+def test_chain_wait_timeout_is_reported_and_recoverable():
+    """Under a one-cycle wait bound the chained frame returns with NPVS_ERR_TIMEOUT (its CTAs stop,
+    pay the arrivals they owe to the grid barriers, drain and free their tensor memory); with the
+    default bound and a zero-filled workspace the same frame is bitwise correct again. The frame's
+    other convolutions run in the product form, whose copies are all issued and drained by one
+    thread."""
+    L, ops, P = lib()
+    wl, fp, nf, (bx, off, cams, n) = chained_frames("city256", 1, 1)
+    pvs0 = nf.pvs.clone()
+    prev = ops.npvs_set_wait_limit(1)
+    try:
+        nf.pvs.zero_()
+        nf.run(bx, off, n, cams)
+        st = ops.npvs_check_status(nf.status)
+    finally:
+        ops.npvs_set_wait_limit(0)
+    assert prev == 4_000_000_000 and st == L.ERR_TIMEOUT
+    nf.ws.zero_()
+    nf.run(bx, off, n, cams)
+    assert ops.npvs_check_status(nf.status) == 0
+    assert torch.equal(nf.pvs, pvs0)
+
+
+def test_chain_level_argument_errors():
+    """A chain level without a level below it, or over layers off the tensor-core shapes, is refused."""
+    L, ops, P = lib()
+    wl = I.workload("city256")
+    ws, bs = I.kaiming_uniform(wl.layers, seed=0)
+    net = P.Net(wl.layers, ws, bs, DEV)
+    with pytest.raises((L.NpvsError, ValueError)):
+        P.NativeFrame(wl, net, 1, L.BF16, max_boxes=10, chain_level=4)
+    with pytest.raises((L.NpvsError, ValueError)):
+        P.NativeFrame(wl, net, 1, L.F32, max_boxes=10, chain_level=1)
