@@ -64,8 +64,11 @@ struct ChainParams {
     uint32_t acc_cols;
 };
 
+constexpr int kStageLd = 36;                   // floats per row of an epilogue warp's staging tile
+constexpr uint32_t kStageTile = 32 * kStageLd * 4;  // 32 rows x 32 columns (padded), one per epilogue warp
+
 size_t chain_smem_bytes() {
-    return 1024 + (size_t)kStages * (kAStride + kBStride) + (2 * kStages + 5) * 8 + 16;
+    return 1024 + (size_t)kStages * (kAStride + kBStride) + 4 * kStageTile + (2 * kStages + 5) * 8 + 16;
 }
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
@@ -82,7 +85,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv_chain_kernel(const __grid_co
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = smem;
     uint8_t* sB = smem + (size_t)kStages * kAStride;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + (size_t)kStages * kBStride);
+    float* stage_tiles = reinterpret_cast<float*>(sB + (size_t)kStages * kBStride);  // [4][32][kStageLd]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(stage_tiles) + 4 * kStageTile);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 5);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kStages);
@@ -124,10 +128,11 @@ __global__ void __launch_bounds__(kThreads, 1) conv_chain_kernel(const __grid_co
     const int total_bars = 2 * P.n_layers;
 
     // Grid-wide barrier: every thread's writes of the phase (T by the epilogue, y by the reduce)
-    // are ordered before it for the generic and the async proxy (TMA reads y next); thread 0 adds
-    // the CTA's arrival and waits, bounded, for all CTAs. Returns false once the CTA has timed out.
-    auto grid_barrier = [&]() -> bool {
-        fence_proxy_async_global();
+    // are ordered before it; after the reduce also for the async proxy (TMA reads y next). Thread 0
+    // adds the CTA's arrival and waits, bounded, for all CTAs. Returns false once the CTA has timed
+    // out.
+    auto grid_barrier = [&](bool async_readers) -> bool {
+        if (async_readers) fence_proxy_async_global();
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
@@ -213,34 +218,53 @@ __global__ void __launch_bounds__(kThreads, 1) conv_chain_kernel(const __grid_co
             }
             __syncwarp();
         } else if (warp >= 4) {
-            const int r = (warp - 4) * 32 + lane;  // warp % 4 is the TMEM lane quadrant it may read
+            // Each lane holds one accumulator row (TMEM lane); T is row-major, so the rows of a
+            // 32-column chunk go through a shared-memory tile and leave as whole 128-byte lines
+            // (8 lanes per row, 4 rows per store instruction) instead of 32 rows per instruction.
+            const int q = warp - 4;  // warp % 4: the TMEM lane quadrant it may read
+            float* tile = stage_tiles + q * 32 * kStageLd;
             for (int u = blockIdx.x; u < tiles; u += gridDim.x, ++tc) {
                 const int mt = u / L.n_tiles, nt = u - mt * L.n_tiles;
-                const int n = mt * kRows + r;
+                const int row0 = mt * kRows + q * 32;  // first T row of this warp's 32 rows
                 const uint32_t buf = tc & 1;
                 mbar_wait(tfull0 + 8 * buf, (tc >> 1) & 1, abort_flag, lim);
                 if (__any_sync(0xffffffffu, *abort_flag)) break;
                 tc_fence_after();
-                const uint32_t taddr = tmem + buf * P.acc_cols + ((uint32_t)((warp - 4) * 32) << 16);
-                for (int c0 = 0; c0 < L.BN; c0 += 16) {
-                    uint32_t v[16];
-                    tmem_ld16(taddr + (uint32_t)c0, v);
+                const uint32_t taddr = tmem + buf * P.acc_cols + ((uint32_t)(q * 32) << 16);
+                for (int c0 = 0; c0 < L.BN; c0 += 32) {
+                    const int cw = min(32, L.BN - c0);  // 32, or 16 at the end of a tile
+                    uint32_t v[32];
+                    tmem_ld16(taddr + (uint32_t)c0, *reinterpret_cast<uint32_t(*)[16]>(v));
+                    if (cw == 32) tmem_ld16(taddr + (uint32_t)c0 + 16, *reinterpret_cast<uint32_t(*)[16]>(v + 16));
                     tmem_ld_wait();
-                    const int ng = nt * L.BN + c0;
-                    if (n >= n_in || ng >= L.Ntot) continue;  // Ntot is a multiple of 16
-                    float* dst = P.T + (size_t)n * L.Ntot + ng;
+                    __syncwarp();  // the previous chunk's reads of the tile are done
 #pragma unroll
-                    for (int q = 0; q < 16; q += 4)
-                        *reinterpret_cast<float4*>(dst + q) = make_float4(
-                            __uint_as_float(v[q]), __uint_as_float(v[q + 1]), __uint_as_float(v[q + 2]),
-                            __uint_as_float(v[q + 3]));
+                    for (int k = 0; k < 32; k += 4)
+                        if (k < cw)
+                            *reinterpret_cast<float4*>(tile + lane * kStageLd + k) =
+                                make_float4(__uint_as_float(v[k]), __uint_as_float(v[k + 1]), __uint_as_float(v[k + 2]),
+                                            __uint_as_float(v[k + 3]));
+                    __syncwarp();
+                    const int ng = nt * L.BN + c0;
+                    if (ng < L.Ntot) {  // Ntot is a multiple of 16; a 32-wide chunk never straddles it
+                        const int lpr = cw / 4;                      // lanes per row: 8, or 4
+                        const int rr = lane / lpr, cc = (lane % lpr) * 4;
+                        const int rstep = 32 / lpr;                  // rows per store instruction
+#pragma unroll 4
+                        for (int r = rr; r < 32; r += rstep) {
+                            const int n = row0 + r;
+                            if (n < n_in)
+                                *reinterpret_cast<float4*>(P.T + (size_t)n * L.Ntot + ng + cc) =
+                                    *reinterpret_cast<const float4*>(tile + r * kStageLd + cc);
+                        }
+                    }
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
             }
         }
-        if (!grid_barrier()) {
+        if (!grid_barrier(false)) {
             ok = false;
             break;
         }
@@ -263,19 +287,25 @@ __global__ void __launch_bounds__(kThreads, 1) conv_chain_kernel(const __grid_co
                         acc.w += v.w;
                     }
                 } else {
+                    // every neighbour index first, then every product row, then the sums in tap
+                    // order (one memory round trip each instead of one per batch of taps)
                     const int32_t* mp = L.map + (size_t)m * L.taps;
-#pragma unroll 9
-                    for (int t = 0; t < L.taps; ++t) {
-                        const int nn = __ldg(mp + t);
-                        if (nn >= 0) {
-                            const float4 v =
-                                __ldcg(reinterpret_cast<const float4*>(P.T + (size_t)nn * L.Ntot + t * L.cout + o));
-                            acc.x += v.x;
-                            acc.y += v.y;
-                            acc.z += v.z;
-                            acc.w += v.w;
+                    int nb[27];
+#pragma unroll
+                    for (int t = 0; t < 27; ++t) nb[t] = t < L.taps ? __ldg(mp + t) : -1;
+                    float4 v[27];
+#pragma unroll
+                    for (int t = 0; t < 27; ++t)
+                        v[t] = nb[t] >= 0 ? __ldcg(reinterpret_cast<const float4*>(P.T + (size_t)nb[t] * L.Ntot + t * L.cout + o))
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int t = 0; t < 27; ++t)
+                        if (nb[t] >= 0) {
+                            acc.x += v[t].x;
+                            acc.y += v[t].y;
+                            acc.z += v[t].z;
+                            acc.w += v[t].w;
                         }
-                    }
                 }
                 if (L.relu) {
                     acc.x = fmaxf(acc.x, 0.f);
@@ -298,7 +328,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_chain_kernel(const __grid_co
                 *reinterpret_cast<uint2*>(L.y + off) = *reinterpret_cast<uint2*>(h);
             }
         }
-        if (!grid_barrier()) ok = false;
+        if (!grid_barrier(true)) ok = false;
     }
 
     // ---- teardown

@@ -763,18 +763,25 @@ __global__ void __launch_bounds__(256) conv_reduce_kernel(const float* __restric
                 acc.w += v.w;
             }
         } else {
+            // every neighbour index first, then every product row, then the sums in tap order (one
+            // memory round trip each instead of one per batch of taps); taps <= 27
             const int32_t* mp = map + (size_t)m * taps;
-#pragma unroll 9
-            for (int t = 0; t < taps; ++t) {
-                const int n = __ldg(mp + t);
-                if (n >= 0) {
-                    const float4 v = __ldcg(reinterpret_cast<const float4*>(T + (size_t)n * ldT + t * cout + o));
-                    acc.x += v.x;
-                    acc.y += v.y;
-                    acc.z += v.z;
-                    acc.w += v.w;
+            int nb[27];
+#pragma unroll
+            for (int t = 0; t < 27; ++t) nb[t] = t < taps ? __ldg(mp + t) : -1;
+            float4 v[27];
+#pragma unroll
+            for (int t = 0; t < 27; ++t)
+                v[t] = nb[t] >= 0 ? __ldcg(reinterpret_cast<const float4*>(T + (size_t)nb[t] * ldT + t * cout + o))
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int t = 0; t < 27; ++t)
+                if (nb[t] >= 0) {
+                    acc.x += v[t].x;
+                    acc.y += v[t].y;
+                    acc.z += v[t].z;
+                    acc.w += v[t].w;
                 }
-            }
         }
         if (relu) {
             acc.x = fmaxf(acc.x, 0.f);
