@@ -11,6 +11,10 @@
 //           the copies, warp 1 the MMAs, warps 4-7 move the accumulators to T);
 //   reduce  y[m] = act(b + sum_t T[map(m, t)][t*cout + o]) (+ skip), taps in fixed order
 //           (transposed conv: y[m] = act(b + T[parent][tap*cout + o]) through the up map),
+// where the GEMM's epilogue writes only the blocks T[n][t*cout ...] that the reduce reads: those
+// of an existing neighbour pair (row n is the tap-t neighbour of an output row exactly when the
+// opposite offset from n is active), of a fine row's own child tap (down conv: one block of eight)
+// and of a coarse row's existing children (up conv),
 // with exactly the operations, in the same order, of the two-kernel product form (conv_tc_kernel
 // with its T epilogue, then conv_reduce_kernel), so the results are bitwise those of the layers
 // launched one by one in that form.
@@ -47,9 +51,11 @@ struct ChainLayer {
     const __nv_bfloat16* skip;
     __nv_bfloat16* y;
     const int32_t* map;  // SUBM3 [cap_out][27] neighbours, DOWN2 [cap_out][8] children, UP2 [cap_out] up map
+    const int32_t* need;  // product block (row n, tap t) read by the reduce iff: SUBM3 need[n*27 + 26 - t] >= 0,
+                          // DOWN2 need[n] == parent*8 + t (the up map), UP2 need[n*8 + t] >= 0 (the down map)
     const int32_t* n_in;
     const int32_t* n_out;
-    int cout, relu, taps;  // taps: 27, 8, or 0 for the transposed conv (one parent per row)
+    int kind, cout, relu, taps;  // taps: 27, 8, or 0 for the transposed conv (one parent per row)
     int rows_x, cap_out;
     int KB, Ntot, Npad, BN, n_tiles, BKE, RB;
 };
@@ -231,8 +237,10 @@ __global__ void __launch_bounds__(kThreads, 1) conv_chain_kernel(const __grid_co
                 if (__any_sync(0xffffffffu, *abort_flag)) break;
                 tc_fence_after();
                 const uint32_t taddr = tmem + buf * P.acc_cols + ((uint32_t)(q * 32) << 16);
-                for (int c0 = 0; c0 < L.BN; c0 += 32) {
-                    const int cw = min(32, L.BN - c0);  // 32, or 16 at the end of a tile
+                // chunks start at multiples of their width, so they never straddle a tap block
+                const int cmax = (L.cout % 32 == 0 && L.BN % 32 == 0) ? 32 : 16;
+                for (int c0 = 0; c0 < L.BN; c0 += cmax) {
+                    const int cw = min(cmax, L.BN - c0);  // 32, or 16 (end of a tile, or 16-wide blocks)
                     uint32_t v[32];
                     tmem_ld16(taddr + (uint32_t)c0, *reinterpret_cast<uint32_t(*)[16]>(v));
                     if (cw == 32) tmem_ld16(taddr + (uint32_t)c0 + 16, *reinterpret_cast<uint32_t(*)[16]>(v + 16));
@@ -246,17 +254,24 @@ __global__ void __launch_bounds__(kThreads, 1) conv_chain_kernel(const __grid_co
                                             __uint_as_float(v[k + 3]));
                     __syncwarp();
                     const int ng = nt * L.BN + c0;
-                    if (ng < L.Ntot) {  // Ntot is a multiple of 16; a 32-wide chunk never straddles it
+                    if (ng < L.Ntot) {  // Ntot is a multiple of 16; a chunk never straddles it or a tap block
+                        // rows whose block of this tap the reduce reads (lane r decides row0 + r)
+                        const int t = ng / L.cout, n_own = row0 + lane;
+                        bool need = n_own < n_in;
+                        if (need && L.need) {
+                            if (L.kind == NPVS_CONV_SUBM3) need = __ldg(L.need + (size_t)n_own * 27 + 26 - t) >= 0;
+                            else if (L.kind == NPVS_CONV_DOWN2) need = (__ldg(L.need + n_own) & 7) == t;
+                            else need = __ldg(L.need + (size_t)n_own * 8 + t) >= 0;
+                        }
+                        const unsigned needed = __ballot_sync(0xffffffffu, need);
                         const int lpr = cw / 4;                      // lanes per row: 8, or 4
                         const int rr = lane / lpr, cc = (lane % lpr) * 4;
                         const int rstep = 32 / lpr;                  // rows per store instruction
 #pragma unroll 4
-                        for (int r = rr; r < 32; r += rstep) {
-                            const int n = row0 + r;
-                            if (n < n_in)
-                                *reinterpret_cast<float4*>(P.T + (size_t)n * L.Ntot + ng + cc) =
+                        for (int r = rr; r < 32; r += rstep)
+                            if ((needed >> r) & 1u)
+                                *reinterpret_cast<float4*>(P.T + (size_t)(row0 + r) * L.Ntot + ng + cc) =
                                     *reinterpret_cast<const float4*>(tile + r * kStageLd + cc);
-                        }
                     }
                 }
                 tc_fence_before();
@@ -386,7 +401,7 @@ npvs_status chain_launch(const ChainLayerHost* layers, int n_layers, float* T, s
     for (int i = 0; i < n_layers; ++i) {
         const ChainLayerHost& h = layers[i];
         NPVS_REQUIRE(chain_layer_supported(h.kind, h.cin, h.cout) && h.x && h.w && h.y && h.map && h.n_in &&
-                         h.n_out && h.rows_x > 0 && h.cap_out >= 0,
+                         h.n_out && h.rows_x > 0 && h.cap_out >= 0 && (h.kind == NPVS_CONV_SUBM3 || h.map2),
                      NPVS_ERR_UNSUPPORTED, "layer chain: unsupported layer");
         const bool up = h.kind == NPVS_CONV_UP2;
         const TcShape sh = tc_shape(h.kind, h.cin, h.cout, up ? 0 : 1);
@@ -402,6 +417,8 @@ npvs_status chain_launch(const ChainLayerHost* layers, int n_layers, float* T, s
         L.skip = static_cast<const __nv_bfloat16*>(h.skip);
         L.y = static_cast<__nv_bfloat16*>(h.y);
         L.map = h.map;
+        L.need = h.kind == NPVS_CONV_SUBM3 ? h.map : h.map2;
+        L.kind = h.kind;
         L.n_in = h.n_in;
         L.n_out = h.n_out;
         L.cout = h.cout;

@@ -16,6 +16,8 @@ struct ChainLayerHost {
     const void* skip;     // [cap_out][cout] BF16 added after ReLU, or nullptr
     void* y;              // [cap_out][cout] BF16
     const int32_t* map;   // SUBM3 neighbours, DOWN2 children, UP2 up map
+    const int32_t* map2;  // which product rows the reduce reads: SUBM3 nullptr (map itself), DOWN2 the
+                          // up map of the finer level, UP2 the down map [rows_x][8]
     const int32_t* n_in;  // device row counts of x and y
     const int32_t* n_out;
     int rows_x, cap_out;

@@ -324,6 +324,7 @@ extern "C" npvs_status npvs_forward(const npvs_net_desc* net, const float* boxes
                 h.skip = P.skip_of[j] >= 0 ? acts[P.skip_of[j]] : nullptr;
                 h.y = acts[j];
                 h.map = d.map;
+                h.map2 = d.map2;
                 h.n_in = d.n_in;
                 h.n_out = d.n_out;
                 h.rows_x = d.cap_in;
