@@ -8,13 +8,10 @@
 // separated by grid-wide barriers:
 //   GEMM    T[n][j*cout + o] = sum_c x[n][c] W_j[c][o] over the input rows (tcgen05, FP32 in TMEM;
 //           A = 128-row TMA tiles of x, B = bulk copies of the packed weight image; warp 0 issues
-//           the copies, warp 1 the MMAs, warps 4-7 move the accumulators to T);
+//           the copies, warp 1 the MMAs, warps 4-7 move the accumulators to T through shared memory
+//           with TMA tensor stores);
 //   reduce  y[m] = act(b + sum_t T[map(m, t)][t*cout + o]) (+ skip), taps in fixed order
 //           (transposed conv: y[m] = act(b + T[parent][tap*cout + o]) through the up map),
-// where the GEMM's epilogue writes only the blocks T[n][t*cout ...] that the reduce reads: those
-// of an existing neighbour pair (row n is the tap-t neighbour of an output row exactly when the
-// opposite offset from n is active), of a fine row's own child tap (down conv: one block of eight)
-// and of a coarse row's existing children (up conv),
 // with exactly the operations, in the same order, of the two-kernel product form (conv_tc_kernel
 // with its T epilogue, then conv_reduce_kernel), so the results are bitwise those of the layers
 // launched one by one in that form.
@@ -45,14 +42,13 @@ constexpr uint32_t kAStride = kRows * 128;  // one A stage: 128 rows of the wide
 constexpr uint32_t kBStride = 256 * 128;    // one B stage: up to 256 columns of 128 bytes
 
 struct ChainLayer {
-    CUtensorMap tmap;  // x [rows_x][cin] BF16, box (BKE, 128 rows), swizzle of RB
+    CUtensorMap tmap;   // x [rows_x][cin] BF16, box (BKE, 128 rows), swizzle of RB
+    CUtensorMap tmapT;  // T [rows_x][Ntot] FP32, box (32 columns, 32 rows), 128-byte swizzle (TMA stores)
     const __nv_bfloat16* w;  // packed image of the GEMM's B operand
     const float* bias;
     const __nv_bfloat16* skip;
     __nv_bfloat16* y;
     const int32_t* map;  // SUBM3 [cap_out][27] neighbours, DOWN2 [cap_out][8] children, UP2 [cap_out] up map
-    const int32_t* need;  // product block (row n, tap t) read by the reduce iff: SUBM3 need[n*27 + 26 - t] >= 0,
-                          // DOWN2 need[n] == parent*8 + t (the up map), UP2 need[n*8 + t] >= 0 (the down map)
     const int32_t* n_in;
     const int32_t* n_out;
     int kind, cout, relu, taps;  // taps: 27, 8, or 0 for the transposed conv (one parent per row)
@@ -70,12 +66,21 @@ struct ChainParams {
     uint32_t acc_cols;
 };
 
-constexpr int kStageLd = 36;                   // floats per row of an epilogue warp's staging tile
-constexpr uint32_t kStageTile = 32 * kStageLd * 4;  // 32 rows x 32 columns (padded), one per epilogue warp
+constexpr uint32_t kStageTile = 32 * 32 * 4;  // 32 rows x 32 FP32 columns, 128-byte rows, 128-byte swizzle
 
-size_t chain_smem_bytes() {
-    return 1024 + (size_t)kStages * (kAStride + kBStride) + 4 * kStageTile + (2 * kStages + 5) * 8 + 16;
+size_t chain_smem_bytes() {  // 4 epilogue warps x 2 staging tiles
+    return 1024 + (size_t)kStages * (kAStride + kBStride) + 8 * kStageTile + (2 * kStages + 5) * 8 + 16;
 }
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* tm, int c0, int c1, uint32_t src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(tm)),
+                 "r"(c0), "r"(c1), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
     unsigned v;
@@ -85,14 +90,17 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
 __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
+__device__ __forceinline__ void fence_proxy_async_shared() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 
 __global__ void __launch_bounds__(kThreads, 1) conv_chain_kernel(const __grid_constant__ ChainParams P) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = smem;
     uint8_t* sB = smem + (size_t)kStages * kAStride;
-    float* stage_tiles = reinterpret_cast<float*>(sB + (size_t)kStages * kBStride);  // [4][32][kStageLd]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(stage_tiles) + 4 * kStageTile);
+    float* stage_tiles = reinterpret_cast<float*>(sB + (size_t)kStages * kBStride);  // [4 warps][2][32][32]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(stage_tiles) + 8 * kStageTile);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 5);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kStages);
@@ -224,11 +232,12 @@ __global__ void __launch_bounds__(kThreads, 1) conv_chain_kernel(const __grid_co
             }
             __syncwarp();
         } else if (warp >= 4) {
-            // Each lane holds one accumulator row (TMEM lane); T is row-major, so the rows of a
-            // 32-column chunk go through a shared-memory tile and leave as whole 128-byte lines
-            // (8 lanes per row, 4 rows per store instruction) instead of 32 rows per instruction.
+            // Each lane holds one accumulator row (TMEM lane). Per 32-column chunk the warp's 32 rows
+            // go to a shared-memory tile in the 128-byte swizzle layout and leave with one TMA
+            // tensor store (two tiles alternate; lane 0 issues and tracks the bulk groups).
             const int q = warp - 4;  // warp % 4: the TMEM lane quadrant it may read
-            float* tile = stage_tiles + q * 32 * kStageLd;
+            float* tiles2 = stage_tiles + q * 2 * 32 * 32;
+            int ci = 0;  // chunks stored by this warp in this layer (tile ci & 1)
             for (int u = blockIdx.x; u < tiles; u += gridDim.x, ++tc) {
                 const int mt = u / L.n_tiles, nt = u - mt * L.n_tiles;
                 const int row0 = mt * kRows + q * 32;  // first T row of this warp's 32 rows
@@ -237,47 +246,49 @@ __global__ void __launch_bounds__(kThreads, 1) conv_chain_kernel(const __grid_co
                 if (__any_sync(0xffffffffu, *abort_flag)) break;
                 tc_fence_after();
                 const uint32_t taddr = tmem + buf * P.acc_cols + ((uint32_t)(q * 32) << 16);
-                // chunks start at multiples of their width, so they never straddle a tap block
-                const int cmax = (L.cout % 32 == 0 && L.BN % 32 == 0) ? 32 : 16;
-                for (int c0 = 0; c0 < L.BN; c0 += cmax) {
-                    const int cw = min(cmax, L.BN - c0);  // 32, or 16 (end of a tile, or 16-wide blocks)
+                for (int c0 = 0; c0 < L.BN; c0 += 32) {
+                    const int cw = min(32, L.BN - c0);  // 32, or 16 at the end of a tile
                     uint32_t v[32];
                     tmem_ld16(taddr + (uint32_t)c0, *reinterpret_cast<uint32_t(*)[16]>(v));
                     if (cw == 32) tmem_ld16(taddr + (uint32_t)c0 + 16, *reinterpret_cast<uint32_t(*)[16]>(v + 16));
                     tmem_ld_wait();
-                    __syncwarp();  // the previous chunk's reads of the tile are done
-#pragma unroll
-                    for (int k = 0; k < 32; k += 4)
-                        if (k < cw)
-                            *reinterpret_cast<float4*>(tile + lane * kStageLd + k) =
-                                make_float4(__uint_as_float(v[k]), __uint_as_float(v[k + 1]), __uint_as_float(v[k + 2]),
-                                            __uint_as_float(v[k + 3]));
-                    __syncwarp();
                     const int ng = nt * L.BN + c0;
-                    if (ng < L.Ntot) {  // Ntot is a multiple of 16; a chunk never straddles it or a tap block
-                        // rows whose block of this tap the reduce reads (lane r decides row0 + r)
-                        const int t = ng / L.cout, n_own = row0 + lane;
-                        bool need = n_own < n_in;
-                        if (need && L.need) {
-                            if (L.kind == NPVS_CONV_SUBM3) need = __ldg(L.need + (size_t)n_own * 27 + 26 - t) >= 0;
-                            else if (L.kind == NPVS_CONV_DOWN2) need = (__ldg(L.need + n_own) & 7) == t;
-                            else need = __ldg(L.need + (size_t)n_own * 8 + t) >= 0;
+                    if (ng >= L.Ntot || row0 >= n_in) continue;  // nothing of this chunk is read later
+                    if (cw == 32 && (ng & 31) == 0) {
+                        float* tile = tiles2 + (ci & 1) * 32 * 32;
+                        if (lane == 0) bulk_wait_read1();  // the store that last read this tile is done
+                        __syncwarp();
+#pragma unroll
+                        for (int c = 0; c < 8; ++c)  // row `lane`, 16-byte chunk c at position c ^ (lane % 8)
+                            *reinterpret_cast<float4*>(tile + lane * 32 + ((c ^ (lane & 7)) << 2)) =
+                                make_float4(__uint_as_float(v[4 * c]), __uint_as_float(v[4 * c + 1]),
+                                            __uint_as_float(v[4 * c + 2]), __uint_as_float(v[4 * c + 3]));
+                        fence_proxy_async_shared();
+                        __syncwarp();
+                        if (lane == 0) {
+                            tma_store_2d(&L.tmapT, ng, row0, smem_u32(tile));
+                            bulk_commit();
                         }
-                        const unsigned needed = __ballot_sync(0xffffffffu, need);
-                        const int lpr = cw / 4;                      // lanes per row: 8, or 4
-                        const int rr = lane / lpr, cc = (lane % lpr) * 4;
-                        const int rstep = 32 / lpr;                  // rows per store instruction
-#pragma unroll 4
-                        for (int r = rr; r < 32; r += rstep)
-                            if ((needed >> r) & 1u)
-                                *reinterpret_cast<float4*>(P.T + (size_t)(row0 + r) * L.Ntot + ng + cc) =
-                                    *reinterpret_cast<const float4*>(tile + r * kStageLd + cc);
+                        ++ci;
+                    } else {  // a 16-column tail (tile widths that are odd multiples of 16): plain stores
+                        const int n = row0 + lane;
+                        if (n < n_in)
+#pragma unroll
+                            for (int k = 0; k < 16; k += 4)
+                                *reinterpret_cast<float4*>(P.T + (size_t)n * L.Ntot + ng + k) =
+                                    make_float4(__uint_as_float(v[k]), __uint_as_float(v[k + 1]),
+                                                __uint_as_float(v[k + 2]), __uint_as_float(v[k + 3]));
                     }
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
             }
+            if (lane == 0) {  // this layer's tensor stores have landed; order them before the barrier
+                bulk_wait_all();
+                fence_proxy_async_global();
+            }
+            __syncwarp();
         }
         if (!grid_barrier(false)) {
             ok = false;
@@ -417,7 +428,6 @@ npvs_status chain_launch(const ChainLayerHost* layers, int n_layers, float* T, s
         L.skip = static_cast<const __nv_bfloat16*>(h.skip);
         L.y = static_cast<__nv_bfloat16*>(h.y);
         L.map = h.map;
-        L.need = h.kind == NPVS_CONV_SUBM3 ? h.map : h.map2;
         L.kind = h.kind;
         L.n_in = h.n_in;
         L.n_out = h.n_out;
@@ -438,10 +448,17 @@ npvs_status chain_launch(const ChainLayerHost* layers, int n_layers, float* T, s
         const cuuint64_t gstride[1] = {(cuuint64_t)h.cin * 2};
         const cuuint32_t box[2] = {(cuuint32_t)sh.BKE, (cuuint32_t)kRows};
         const cuuint32_t estride[2] = {1, 1};
-        const CUresult r =
+        CUresult r =
             enc(&L.tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(h.x), gdim, gstride, box, estride,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, sh.RB == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        const cuuint64_t tdim[2] = {(cuuint64_t)sh.Ntot, (cuuint64_t)h.rows_x};
+        const cuuint64_t tstride[1] = {(cuuint64_t)sh.Ntot * 4};
+        const cuuint32_t tbox[2] = {32, 32};
+        if (r == CUDA_SUCCESS)
+            r = enc(&L.tmapT, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, T, tdim, tstride, tbox, estride,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
             set_error("layer chain: cuTensorMapEncodeTiled failed (%d)", (int)r);
             return NPVS_ERR_CUDA;
