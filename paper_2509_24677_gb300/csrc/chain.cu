@@ -142,13 +142,14 @@ __global__ void __launch_bounds__(kThreads, 1) conv_chain_kernel(const __grid_co
     const int total_bars = 2 * P.n_layers;
 
     // Grid-wide barrier: every thread's writes of the phase (T by the epilogue, y by the reduce)
-    // are ordered before it; after the reduce also for the async proxy (TMA reads y next). Thread 0
-    // adds the CTA's arrival and waits, bounded, for all CTAs. Returns false once the CTA has timed
-    // out.
+    // are ordered before it; after the reduce also for the async proxy (TMA reads y next). One
+    // thread of warp 2 (which has no role in the GEMM phase) adds the CTA's arrival and waits,
+    // bounded, for all CTAs. Returns false once the CTA has timed out.
+    constexpr int kBarThread = 64;
     auto grid_barrier = [&](bool async_readers) -> bool {
         if (async_readers) fence_proxy_async_global();
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == kBarThread) {
             __threadfence();
             target += gridDim.x;
             atomicAdd(P.bar, 1u);
@@ -372,7 +373,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv_chain_kernel(const __grid_co
         tc_fence_after();
         tmem_dealloc(tmem, 2 * P.acc_cols);
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == kBarThread) {
         if (*abort_flag) raise_status(P.status, NPVS_ERR_TIMEOUT);
         // arrivals this CTA still owes (after a timeout), so that no other CTA waits for it
         if (bars_done < total_bars) atomicAdd(P.bar, (unsigned)(total_bars - bars_done));
