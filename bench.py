@@ -481,6 +481,44 @@ def select_batched_viewcells(dev, wl, scenes, n_pick=64, per_scene=512, lo=0.01,
     return picked
 
 
+def chain_levels_for(P, wl):
+    """Chain levels the network allows: 0 (none) and every k whose chained layers are tensor-core
+    shapes (cin % 32 == 0, cout % 16 == 0)."""
+    n_levels = 1 + sum(1 for l in wl.layers if l.kind == "down2")
+    out = [0]
+    for k in range(1, n_levels):
+        idx = P.chain_layer_indices(wl.layers, k)
+        if idx and all(wl.layers[i].cin % 32 == 0 and wl.layers[i].cout % 16 == 0 for i in idx):
+            out.append(k)
+    return out
+
+
+def fastest_chain_frame(P, L, wl, net, B, descs, bx, of, nb, cams, dev, capacity_frac=1.0, reps=10):
+    """The captured BF16 frame (npvs_forward) at each allowed chain level, timed over `reps` graph
+    replays; returns (NativeFrame, graph, level, {level: median ms}) of the fastest."""
+    st = torch.cuda.current_stream()
+    best, times = None, {}
+    for k in chain_levels_for(P, wl):
+        nfk = P.NativeFrame(wl, net, B, L.BF16, max_boxes=nb, device=dev, tuned=descs, capacity_frac=capacity_frac,
+                            chain_level=k)
+        gk = nfk.capture(bx, of, nb, cams)
+        ev = []
+        for i in range(3 + reps):
+            s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s_.record(st)
+            gk.replay()
+            e_.record(st)
+            if i >= 3:
+                ev.append((s_, e_))
+        torch.cuda.synchronize()
+        times[k] = statistics.median(s_.elapsed_time(e_) for s_, e_ in ev)
+        if best is None or times[k] < times[best[2]]:
+            best = (nfk, gk, k)
+        else:
+            del gk, nfk
+    return best[0], best[1], best[2], {str(k): round(v, 4) for k, v in times.items()}
+
+
 def run_batched(args, dev, net, tuned):
     """64 viewcells of uneven occupancy in one batched frame (one launch per layer over the
     concatenated rulebooks, one CUDA graph of npvs_forward), and each viewcell alone as a
@@ -513,9 +551,9 @@ def run_batched(args, dev, net, tuned):
     stages = {k: round(v, 3) for k, v in acc.items() if not k.startswith("conv:")}
     stages["convs (22 layers)"] = round(conv_ms, 3)
     del gst
-    nfb = P.NativeFrame(wl, net, B, L.BF16, max_boxes=len(boxes), device=dev, capacity_frac=frac, tuned=fpb.descs)
+    nfb, g, chain_b, chain_b_ms = fastest_chain_frame(P, L, wl, net, B, fpb.descs, bx, of, len(boxes), cams, dev,
+                                                      capacity_frac=frac, reps=5)
     del fpb
-    g = nfb.capture(bx, of, len(boxes), cams)
     st = torch.cuda.current_stream()
     ts = []
     for i in range(3 + max(5, args.steps // 3)):
@@ -560,6 +598,7 @@ def run_batched(args, dev, net, tuned):
             "stage_ms": dict(sorted(stages.items(), key=lambda kv: -kv[1])),
             "occupancy_range": [round(min(occs), 4), round(max(occs), 4)],
             "batch_ms": round(batch_ms, 4), "frames_per_s": round(B * 1000.0 / batch_ms, 2),
+            "chain": {"level": chain_b, "ms_per_batch_by_level": chain_b_ms},
             "per_viewcell_ms": {"p50": round(float(np.percentile(lat, 50)), 4),
                                 "p99": round(float(np.percentile(lat, 99)), 4), "max": round(max(lat), 4)},
             "active_sites_level0": n_act, "capacity_frac": frac,
@@ -623,9 +662,8 @@ def run_grid_workload(args, dev, tf_bf16, hbm_gbs, wl, boxes, vcs, label, capaci
     if stt != 0:
         raise RuntimeError(f"device status {stt:#x} set in the {wl.name} frame")
     tuned = fp.autotune(bx, of, cams, reps=3)
-    nf = P.NativeFrame(wl, net, B, L.BF16, max_boxes=len(boxes) * B, device=dev, tuned=fp.descs,
-                       capacity_frac=capacity_frac)
-    g = nf.capture(bx, of, len(boxes) * B, cams)
+    nf, g, chain_k, chain_ms = fastest_chain_frame(P, L, wl, net, B, fp.descs, bx, of, len(boxes) * B, cams, dev,
+                                                   capacity_frac=capacity_frac, reps=5)
     st = torch.cuda.current_stream()
     ts = []
     for i in range(3 + max(5, args.steps // 3)):
@@ -661,6 +699,7 @@ def run_grid_workload(args, dev, tf_bf16, hbm_gbs, wl, boxes, vcs, label, capaci
     act_bytes = sum(n_lv[lv_of[l.name]] * l.cout * (4 if l.kind == "head1" else 2) for l in wl.layers)
     peak_mb = (torch.cuda.max_memory_allocated() - mem0) / 2**20
     return {"workload": label, "batch": B, "ms_per_batch": round(ms, 3),
+            "chain": {"level": chain_k, "ms_per_batch_by_level": chain_ms},
             "memory_mb": {"peak_device": round(peak_mb, 1), "layer_outputs_active": round(act_bytes / 2**20, 1)},
             "frames_per_s": round(B * 1000.0 / ms, 2), "occupancy": round(occ, 4),
             "active_sites": [int(lv.n_rows.item()) for lv in fp.levels],
