@@ -164,29 +164,29 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
-# Measured DRAM traffic (reads + writes) of the convolution kernels of one city256 frame in the
-# bench's launch configuration (profiles/city256_bf16_frame_launches.md), for the two per-layer
-# configurations the autotuner picks on different GPUs (level-1 layers in the window or the product
-# form); tied to the kernels as they are, so it must be re-measured (or set to None) when they change.
-CONV_FRAME_DRAM_BYTES = {"level1-window": 65_664_000, "level1-product": 68_955_648}
+# Measured DRAM traffic (reads + writes, all 34 launches) of one city256 frame (the frame of viewcell
+# 5 of the bench's cycle: 10,375 active sites at level 0) with the layer chain at level 1 and the
+# level-0 layers in the forms below (profiles/city256_bf16_frame_launches.md), and that frame's
+# algorithmic bytes; tied to the kernels as they are, so it must be measured again (or removed)
+# when they change.
+FRAME_DRAM = {"chain_level": 1,
+              "forms": {"stem": "product", "enc0a": "window3", "enc0b": "window3", "dec0a": "window3",
+                        "dec0b": "window3-nosplit", "head": "gather"},
+              "dram_bytes": 70_240_000, "algorithmic_bytes": 53_287_380,
+              # the convolution kernels alone (layer chain, 6 level-0 conv_tc launches, 1 gather-reduce)
+              "conv_dram_bytes": 63_249_000, "conv_algorithmic_bytes": 40_092_672}
 
 
-# Measured DRAM traffic (reads + writes) of every kernel of one city256 frame in the bench's launch
-# configuration; None until it is measured for the kernels as they are.
-FRAME_DRAM_BYTES = {}
-
-
-def frame_traffic(tuned: dict):
-    """Measured DRAM bytes of one whole frame for the tuned configuration, or None."""
-    lvl1 = {tuned_label(tuned[k][0]).split("-")[0] for k in ("enc1a", "enc1b", "dec1a", "dec1b")}
-    return FRAME_DRAM_BYTES.get("level1-" + lvl1.pop()) if len(lvl1) == 1 else None
-
-
-def conv_frame_traffic(tuned: dict):
-    """Measured convolution DRAM bytes per frame for the tuned configuration `tuned` ({layer:
-    (config, us)}), or None when its level-1 form was not captured."""
-    lvl1 = {tuned_label(tuned[k][0]).split("-")[0] for k in ("enc1a", "enc1b", "dec1a", "dec1b")}
-    return CONV_FRAME_DRAM_BYTES.get("level1-" + lvl1.pop()) if len(lvl1) == 1 else None
+def frame_traffic(tuned: dict, chain_level: int, convs_only: bool = False):
+    """Measured DRAM bytes of one whole frame (or of its convolution kernels), and that frame's
+    algorithmic bytes, when the frame runs in the configuration they were measured with; else
+    (None, None)."""
+    forms = {k: tuned_label(tuned[k][0]) for k in FRAME_DRAM["forms"] if k in tuned}
+    if chain_level == FRAME_DRAM["chain_level"] and forms == FRAME_DRAM["forms"]:
+        if convs_only:
+            return FRAME_DRAM["conv_dram_bytes"], FRAME_DRAM["conv_algorithmic_bytes"]
+        return FRAME_DRAM["dram_bytes"], FRAME_DRAM["algorithmic_bytes"]
+    return None, None
 
 
 def tuned_label(cfg: dict) -> str:
@@ -910,11 +910,11 @@ def run_ours(args):
     frame_flops = sum(v["flops"] for v in alg.values())
     roof = roof_of(frame_bytes, frame_flops, ms_frame * 1e-3)
     roof["kernel"] = "frame (every kernel of npvs_forward, one graph replay)"
-    roof["traffic"] = frame_traffic(tuned)
+    roof["traffic"], roof["traffic_frame_algorithmic_bytes"] = frame_traffic(tuned, chain_level)
     conv_roof = roof_of(sum(alg[k]["bytes"] for k in conv_keys), sum(alg[k]["flops"] for k in conv_keys),
                         sum(stage_ms[k] for k in conv_keys) * 1e-3)
     conv_roof["kernel"] = "conv (all %d layers: tcgen05 GEMM + gather-reduce kernels)" % len(conv_keys)
-    conv_roof["traffic"] = conv_frame_traffic(tuned)
+    conv_roof["traffic"], conv_roof["traffic_frame_algorithmic_bytes"] = frame_traffic(tuned, chain_level, True)
 
     line = {
         "metric": METRIC, "value": round(replica_rate(world, fps_step, ms), 3), "unit": "frames/s", "n_gpus": world,

@@ -131,9 +131,9 @@ typedef enum {
  *                 child rows of each coarse row [cap_in][8] (the down map of the same level pair)
  *        HEAD1 -> NULL
  *        DOWN3 -> input rows of the 27 taps of each output [cap_out][27] (the map of a DOWN3
- *                 rulebook); UP3 -> the map2 of that rulebook, [cap_out][27] coarse rows
- *        (DOWN3 / UP3: forward only, npvs_sparse_conv_bwd returns NPVS_ERR_UNSUPPORTED; n_in and
- *        cap_in are required)
+ *                 rulebook), map2 -> the rulebook's map2 (for the backward's dgrad);
+ *        UP3   -> the map2 of that rulebook, [cap_out][27] coarse rows, map2 -> its map
+ *        (DOWN3 / UP3: n_in and cap_in are required)
  *  n_out: device row count of the output level; cap_out its capacity (grid sizing).
  *  x: [cap_in][cin]; y: [cap_out][cout]; skip (nullable): [cap_out][cout] added after ReLU.
  *  dtype: F32 / F64 (SIMT FMA kernels, weights [taps][cin][cout]) or BF16 (tcgen05 kernels,
@@ -438,7 +438,9 @@ size_t npvs_conv_bwd_workspace_bytes(const npvs_conv_desc* desc);
  *  dx:     nullable [cap_in][cin] (dtype): gradient of x, rows < n_in written. dx_add (nullable,
  *          same shape) is added to it: a gradient reaching x by another path (a skip).
  *  dw, db: FP32 (FP64 for F64) [taps][cin][cout] and [cout], overwritten; db nullable.
- *  The stride-2 kinds need map2 (the other map of the level pair), n_in and cap_in for dx.
+ *  The stride-2 kinds (DOWN2, UP2, DOWN3, UP3) need map2 (the other map of the level pair), n_in and
+ *  cap_in for dx: the dgrad of DOWN2 / DOWN3 is the UP2 / UP3 convolution of g with W_t^T on the same
+ *  rulebook, and the other way round.
  *  Sums are taken in a fixed order: results are bitwise reproducible for the same capacities.
  *  desc->workspace is not used; workspace must hold npvs_conv_bwd_workspace_bytes(desc). */
 npvs_status npvs_sparse_conv_bwd(const npvs_conv_desc* desc, const void* x, const void* w, const void* y,

@@ -9,7 +9,9 @@
 // the forward kernels (tensor cores for BF16): a submanifold conv's transpose is the submanifold
 // conv with the opposite taps (the neighbour map is symmetric: map(n, t) = i iff
 // map(i, 26 - t) = n) and weights W_{26-t}^T; a stride-2 down conv's transpose is the up conv on
-// the same level pair with W_t^T and vice versa; a 1x1 conv's transpose is the 1x1 conv with W^T.
+// the same level pair with W_t^T and vice versa (2x2x2: the down map and the up map; 3x3x3 with
+// padding 1: the two maps of a DOWN3 rulebook, input rows of each coarse output and coarse rows of
+// each fine row and tap); a 1x1 conv's transpose is the 1x1 conv with W^T.
 //
 // Determinism: every sum has a fixed order. Rows are cut into a fixed number of chunks of the device
 // row count; each chunk's partial sums are written to the workspace and added in chunk order.
@@ -253,7 +255,11 @@ __global__ void __launch_bounds__(256) transpose_taps_kernel(const T* __restrict
     }
 }
 
-int host_taps(int kind) { return kind == NPVS_CONV_SUBM3 ? 27 : (kind == NPVS_CONV_HEAD1 ? 1 : 8); }
+int host_taps(int kind) { return conv_taps(kind); }
+
+bool strided(int kind) {
+    return kind == NPVS_CONV_DOWN2 || kind == NPVS_CONV_UP2 || kind == NPVS_CONV_DOWN3 || kind == NPVS_CONV_UP3;
+}
 
 struct BwdPlan {
     int taps, n_db, n_chunks, tile, tiles;
@@ -305,6 +311,8 @@ BwdPlan plan_bwd(const npvs_conv_desc& d) {
         case NPVS_CONV_SUBM3: t.kind = NPVS_CONV_SUBM3; t.map2 = nullptr; p.mode = 2; break;
         case NPVS_CONV_DOWN2: t.kind = NPVS_CONV_UP2; t.map = d.map2; t.map2 = d.map; break;
         case NPVS_CONV_UP2: t.kind = NPVS_CONV_DOWN2; t.map = d.map2; t.map2 = d.map; break;
+        case NPVS_CONV_DOWN3: t.kind = NPVS_CONV_UP3; t.map = d.map2; t.map2 = d.map; break;
+        case NPVS_CONV_UP3: t.kind = NPVS_CONV_DOWN3; t.map = d.map2; t.map2 = d.map; break;
         default: t.kind = NPVS_CONV_HEAD1; t.map = nullptr; t.map2 = nullptr; break;
     }
     p.td = t;
@@ -400,7 +408,7 @@ size_t bwd_bytes(const BwdPlan& p) {
 using namespace npvs;
 
 extern "C" size_t npvs_conv_bwd_workspace_bytes(const npvs_conv_desc* desc) {
-    if (!desc || desc->kind < NPVS_CONV_SUBM3 || desc->kind > NPVS_CONV_HEAD1) return 0;
+    if (!desc || !valid_conv_kind(desc->kind)) return 0;
     BwdPlan p = plan_bwd(*desc);
     return bwd_bytes(p);
 }
@@ -410,8 +418,7 @@ extern "C" npvs_status npvs_sparse_conv_bwd(const npvs_conv_desc* desc, const vo
                                             void* workspace, size_t workspace_bytes, void* stream) {
     NPVS_REQUIRE(desc && x && w && dy && dw && desc->n_out, NPVS_ERR_INVALID_ARG, "npvs_sparse_conv_bwd: NULL argument");
     const npvs_conv_desc& d = *desc;
-    NPVS_REQUIRE(d.kind >= NPVS_CONV_SUBM3 && d.kind <= NPVS_CONV_HEAD1, NPVS_ERR_UNSUPPORTED,
-                 "npvs_sparse_conv_bwd: unknown kind (DOWN3 / UP3 have a forward only)");
+    NPVS_REQUIRE(valid_conv_kind(d.kind), NPVS_ERR_UNSUPPORTED, "npvs_sparse_conv_bwd: unknown kind");
     NPVS_REQUIRE(d.cin > 0 && d.cout > 0 && d.cap_out >= 0, NPVS_ERR_INVALID_ARG, "npvs_sparse_conv_bwd: bad sizes");
     NPVS_REQUIRE(d.kind == NPVS_CONV_HEAD1 || d.map, NPVS_ERR_INVALID_ARG, "npvs_sparse_conv_bwd: map is NULL");
     NPVS_REQUIRE(d.dtype != NPVS_BF16 || !bf16_narrow(d.cin, d.cout), NPVS_ERR_UNSUPPORTED,
@@ -420,8 +427,8 @@ extern "C" npvs_status npvs_sparse_conv_bwd(const npvs_conv_desc* desc, const vo
     NPVS_REQUIRE(!(d.relu && d.out_f32), NPVS_ERR_UNSUPPORTED, "npvs_sparse_conv_bwd: ReLU with out_f32 is not supported");
     NPVS_REQUIRE(!dx || d.kind == NPVS_CONV_SUBM3 || d.kind == NPVS_CONV_HEAD1 || d.map2, NPVS_ERR_INVALID_ARG,
                  "npvs_sparse_conv_bwd: the dgrad of a stride-2 conv needs map2 (the other map of the level pair)");
-    NPVS_REQUIRE(!dx || !(d.kind == NPVS_CONV_DOWN2 || d.kind == NPVS_CONV_UP2) || (d.n_in && d.cap_in > 0),
-                 NPVS_ERR_INVALID_ARG, "npvs_sparse_conv_bwd: the dgrad of a stride-2 conv needs n_in and cap_in");
+    NPVS_REQUIRE(!dx || !strided(d.kind) || (d.n_in && d.cap_in > 0), NPVS_ERR_INVALID_ARG,
+                 "npvs_sparse_conv_bwd: the dgrad of a stride-2 conv needs n_in and cap_in");
     BwdPlan p = plan_bwd(d);
     NPVS_REQUIRE(workspace && workspace_bytes >= bwd_bytes(p), NPVS_ERR_WORKSPACE,
                  "npvs_sparse_conv_bwd: workspace smaller than npvs_conv_bwd_workspace_bytes()");

@@ -327,7 +327,7 @@ struct WgPlan {
 
 WgPlan plan_wgrad(const npvs_conv_desc& d) {
     WgPlan w;
-    w.taps = d.kind == NPVS_CONV_SUBM3 ? 27 : (d.kind == NPVS_CONV_HEAD1 ? 1 : 8);
+    w.taps = conv_taps(d.kind);
     w.n_chunks = std::max(1, ceil_div(std::max(d.cap_out, 1), kPairChunk));
     w.MT = ceil_div(d.cin, 128);
     w.Ntile = std::min(256, (d.cout + 15) / 16 * 16);

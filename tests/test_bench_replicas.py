@@ -55,8 +55,8 @@ def test_single_process_needs_no_group():
 
 
 def test_tuned_labels_and_traffic_selection():
-    """The bench names the tuned forms and reports the measured convolution traffic only for a
-    level-1 form that was captured."""
+    """The bench names the tuned forms and reports the measured frame traffic only for the chain
+    level and level-0 forms it was captured with."""
     sys.path.insert(0, ROOT)
     import bench
     prod = {"tune_form": 2}
@@ -67,12 +67,15 @@ def test_tuned_labels_and_traffic_selection():
     assert bench.tuned_label(win) == "window-nosplit"
     assert bench.tuned_label(win3) == "window3"
     assert bench.tuned_label(gat) == "gather-4w"
-    l1 = ("enc1a", "enc1b", "dec1a", "dec1b")
-    assert bench.conv_frame_traffic({k: (win, 1.0) for k in l1}) == bench.CONV_FRAME_DRAM_BYTES["level1-window"]
-    assert bench.conv_frame_traffic({k: (prod, 1.0) for k in l1}) == bench.CONV_FRAME_DRAM_BYTES["level1-product"]
-    assert bench.conv_frame_traffic({k: (win3, 1.0) for k in l1}) is None
-    mixed = {k: (prod if k == "enc1a" else win, 1.0) for k in l1}
-    assert bench.conv_frame_traffic(mixed) is None
+    cfg = {"product": prod, "window3": win3, "window3-nosplit": dict(win3, tune_max_split=1),
+           "gather": {"tune_form": 1}}
+    tuned = {k: (cfg[v], 1.0) for k, v in bench.FRAME_DRAM["forms"].items()}
+    assert bench.frame_traffic(tuned, 1) == (bench.FRAME_DRAM["dram_bytes"], bench.FRAME_DRAM["algorithmic_bytes"])
+    assert bench.frame_traffic(tuned, 1, True) == (bench.FRAME_DRAM["conv_dram_bytes"],
+                                                   bench.FRAME_DRAM["conv_algorithmic_bytes"])
+    assert bench.frame_traffic(tuned, 0) == (None, None) and bench.frame_traffic(tuned, 2) == (None, None)
+    other = dict(tuned, stem=(win3, 1.0))
+    assert bench.frame_traffic(other, 1) == (None, None)
 
 
 def test_step_quantiles_nearest_rank():

@@ -1,7 +1,7 @@
 """k = 3, stride 2, padding 1 sparse convolutions and their transposes (DOWN3 / UP3, the strided
 sparse convolution of Sec. 2.3 with a 3^3 kernel and a dilated output set): the DOWN3 rulebook
 bit-exact against the oracle's brute force, and the convolutions (FP64, FP32, BF16; gather and
-product forms) against the oracle's masked dense definition."""
+product forms) and their backward against the oracle's masked dense definition."""
 import numpy as np
 import pytest
 import torch
@@ -136,8 +136,81 @@ def test_strided3_conv_parity(kind, cin, cout, dt, mode):
     assert normwise(got, ref) <= tol
 
 
+BWD_CASES = [("down3", 16, 32), ("down3", 32, 64), ("down3", 64, 32), ("up3", 32, 16), ("up3", 64, 64),
+             ("up3", 128, 32)]
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("kind,cin,cout", BWD_CASES)
+def test_strided3_conv_backward_parity(kind, cin, cout, dt):
+    """Backward of the k = 3, stride 2 pair against the oracle's autograd of its masked dense
+    definition: g = dy * 1[y > 0], db = sum g, dW_k = sum x[in]^T g[out] over the tap's pairs, and dx
+    by the transposed conv on the same rulebook (DOWN3's is UP3 with W_k^T, and the other way
+    round), plus a gradient dx_add from another path; rows past n_in untouched; bitwise
+    reproducible."""
+    L, ops, P = lib()
+    rng = np.random.default_rng(cin * 31 + cout * 3 + (kind == "up3"))
+    occ = rng.random((2, 6, 8, 10)) < 0.15
+    fine, coarse, down, up, c0, status = strided3_levels(occ)
+    assert ops.npvs_check_status(status) == 0
+    flv = onet.Level(c0, occ.shape)
+    clv = flv.strided3()
+    if kind == "down3":
+        lv_in, lv_out, mp, mp2, n_in, n_out = fine, coarse, down, up, flv.n, clv.n
+    else:
+        lv_in, lv_out, mp, mp2, n_in, n_out = coarse, fine, up, down, clv.n, flv.n
+    w = I.kaiming_uniform([I.Layer("t", kind, cin, cout, True)], seed=13)[0][0]
+    b = (rng.normal(size=cout) * 0.1).astype(np.float32)
+    x = rng.normal(size=(n_in, cin)).astype(np.float32)
+    dy = rng.normal(size=(n_out, cout)).astype(np.float32)
+    add = rng.normal(size=(n_in, cin)).astype(np.float32)
+    rnd = bf16_round if dt == "bf16" else (lambda a: np.asarray(a, np.float64))
+    x_r, dy_r, add_r = rnd(x), rnd(dy), rnd(add)
+    xt = torch.tensor(x_r, requires_grad=True)
+    wt = torch.tensor(w.astype(np.float64), requires_grad=True)
+    bt = torch.tensor(b.astype(np.float64), requires_grad=True)
+    pre = onet.down3(flv, clv, xt, wt, bt) if kind == "down3" else onet.up3(clv, flv, xt, wt, bt)
+    y_ref = torch.relu(pre)
+    g = torch.tensor(dy_r) * (y_ref > 0).double()
+    gx, gw, gb = torch.autograd.grad(pre, (xt, wt, bt), grad_outputs=g)
+    dtype = {"f32": L.F32, "bf16": L.BF16, "f64": L.F64}[dt]
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f64": torch.float64}[dt]
+    mdt = torch.float64 if dt == "f64" else torch.float32
+
+    def dev_rows(a, cap):
+        t = torch.zeros(cap, a.shape[1], dtype=tdt, device=DEV)
+        t[:len(a)] = torch.from_numpy(np.asarray(a, np.float64)).to(DEV).to(tdt)
+        return t
+
+    xin, dyd = dev_rows(x, lv_in.capacity), dev_rows(dy, lv_out.capacity)
+    yd, addd = dev_rows(y_ref.detach().numpy(), lv_out.capacity), dev_rows(add, lv_in.capacity)
+    st = torch.zeros(1, dtype=torch.int32, device=DEV)
+    desc = ops.conv_desc(P.KIND[kind], dtype, cin, cout, True, mp, lv_out.n_rows, lv_out.capacity, map2=mp2,
+                         n_in=lv_in.n_rows, cap_in=lv_in.capacity, status=st)
+    ws = ops.conv_workspace(ops.npvs_conv_bwd_workspace_bytes(desc), DEV)
+    w_dev = torch.from_numpy(w).to(DEV).to(mdt).contiguous()
+    results = []
+    for rep in range(2):
+        dx = torch.full((lv_in.capacity, cin), float("nan"), dtype=tdt, device=DEV)
+        dw = torch.full(w.shape, float("nan"), dtype=mdt, device=DEV)
+        db = torch.full((cout,), float("nan"), dtype=mdt, device=DEV)
+        ops.npvs_sparse_conv_bwd(desc, xin, w_dev, yd, dyd, dx, addd, dw, db, ws)
+        assert ops.npvs_check_status(st) == 0
+        results.append((dx, dw, db))
+    dx, dw, db = results[0]
+    tol_dx = {"f32": 1e-5, "bf16": 2e-2, "f64": 1e-12}[dt]
+    tol_w = {"f32": 1e-5, "bf16": 1e-5, "f64": 1e-12}[dt]
+    assert normwise(dw.cpu().numpy(), gw.numpy()) <= tol_w
+    assert normwise(db.cpu().numpy(), gb.numpy()) <= tol_w
+    got = dx[:n_in].double().cpu().numpy()
+    assert normwise(got - add_r, gx.numpy()) <= tol_dx, normwise(got - add_r, gx.numpy())
+    assert torch.isnan(dx[n_in:].float()).all()
+    for a, b2 in zip(results[0], results[1]):
+        assert torch.equal(torch.nan_to_num(a.float(), 7.0), torch.nan_to_num(b2.float(), 7.0))
+
+
 def test_strided3_argument_errors():
-    """DOWN3 / UP3 need n_in and cap_in, and have no backward."""
+    """DOWN3 / UP3 need n_in and cap_in, and their dgrad needs the rulebook's other map."""
     L, ops, P = lib()
     occ = np.ones((1, 4, 4, 4), bool)
     fine, coarse, down, up, c0, _ = strided3_levels(occ)
@@ -149,8 +222,9 @@ def test_strided3_argument_errors():
     assert e.value.status == L.ERR_INVALID_ARG
     d = ops.conv_desc(L.CONV_DOWN3, L.F32, 16, 16, True, down, coarse.n_rows, coarse.capacity,
                       n_in=fine.n_rows, cap_in=fine.capacity)
-    assert ops.npvs_conv_bwd_workspace_bytes(d) == 0
-    ws = torch.zeros(1024, dtype=torch.uint8, device=DEV)
-    with pytest.raises(L.NpvsError) as e:
-        ops.npvs_sparse_conv_bwd(d, z, w, z[:8], z[:8], None, None, torch.zeros_like(w), None, ws)
-    assert e.value.status == L.ERR_UNSUPPORTED
+    nb = ops.npvs_conv_bwd_workspace_bytes(d)
+    assert nb > 0
+    ws = torch.zeros(nb, dtype=torch.uint8, device=DEV)
+    with pytest.raises(L.NpvsError) as e:     # dx without map2
+        ops.npvs_sparse_conv_bwd(d, z, w, z[:8], z[:8], z, None, torch.zeros_like(w), None, ws)
+    assert e.value.status == L.ERR_INVALID_ARG
