@@ -2,10 +2,12 @@
 // and pruning: the test of every box's froxels against a PVS (Sec. 3.2 occlusion culling, Sec. 5.6
 // temporal bounding volumes of dynamic objects).
 //
-// Work decomposition: every box face gets a conservative bounding rectangle of froxel columns
-// (the face clipped against half the near distance and projected); a prefix sum over the
-// per-face column counts gives a flat list of (face, column) items; each item casts the s x s
-// supersampled rays of its column against its one face. Every floating-point step of the ray
+// Work decomposition: every box face gets a conservative bounding rectangle of supersampled
+// pixels (the face clipped against half the near distance and projected, two sub-pixels of margin:
+// the float error of the projection is an order of magnitude smaller) and the froxel columns that
+// rectangle touches; a prefix sum over the per-face column counts gives a flat list of
+// (face, column) items; each item casts the rays of its column that lie in the face's rectangle
+// against its one face (rays outside it cannot hit the face). Every floating-point step of the ray
 // test is an explicit round-to-nearest binary32 intrinsic in a fixed order, so the resulting
 // bits do not depend on how the work is split. A hit sets its bit with atomicOr.
 #include "common.cuh"
@@ -16,7 +18,8 @@ namespace {
 struct __align__(16) FaceRec {
     int b, axis;
     float P, lo1, hi1, lo2, hi2;
-    int x0, y0, nx, ny, pad;
+    int x0, y0, nx, ny;      // froxel columns touched
+    int sa0, sa1, sb0, sb1;  // supersampled pixels of the rectangle (inclusive)
 };
 
 constexpr int kScanChunk = 1024;
@@ -31,7 +34,7 @@ __device__ __forceinline__ int batch_of_box(const int32_t* off, int B, int j) {
 }
 
 __global__ void face_setup_kernel(const float* __restrict__ boxes, const int32_t* __restrict__ box_off,
-                                  int n_boxes, const npvs_camera* __restrict__ cams, npvs_grid g,
+                                  int n_boxes, const npvs_camera* __restrict__ cams, npvs_grid g, int s,
                                   FaceRec* __restrict__ faces, int* __restrict__ counts) {
     pdl_begin();
     int f = blockIdx.x * blockDim.x + threadIdx.x;
@@ -40,7 +43,8 @@ __global__ void face_setup_kernel(const float* __restrict__ boxes, const int32_t
     FaceRec rec;
     rec.nx = rec.ny = 0;
     rec.x0 = rec.y0 = 0;
-    rec.pad = 0;
+    rec.sa0 = rec.sb0 = 0;
+    rec.sa1 = rec.sb1 = -1;
     int cnt = 0;
     if (j >= box_off[0] && j < box_off[g.B]) {
         int b = batch_of_box(box_off, g.B, j);
@@ -93,15 +97,19 @@ __global__ void face_setup_kernel(const float* __restrict__ boxes, const int32_t
             }
         }
         if (any && !all_far) {
-            // froxel column coordinate (n + 1) / 2 * W, one column of margin each side
-            float gx0 = (xmin + 1.f) * 0.5f * g.W, gx1 = (xmax + 1.f) * 0.5f * g.W;
-            float gy0 = (ymin + 1.f) * 0.5f * g.H, gy1 = (ymax + 1.f) * 0.5f * g.H;
-            gx0 = fmaxf(fminf(gx0, 1e8f), -1e8f); gx1 = fmaxf(fminf(gx1, 1e8f), -1e8f);
-            gy0 = fmaxf(fminf(gy0, 1e8f), -1e8f); gy1 = fmaxf(fminf(gy1, 1e8f), -1e8f);
-            int x0 = max((int)floorf(gx0) - 1, 0), x1 = min((int)floorf(gx1) + 1, g.W - 1);
-            int y0 = max((int)floorf(gy0) - 1, 0), y1 = min((int)floorf(gy1) + 1, g.H - 1);
-            if (x0 <= x1 && y0 <= y1) {
-                rec.x0 = x0; rec.y0 = y0; rec.nx = x1 - x0 + 1; rec.ny = y1 - y0 + 1;
+            // supersampled pixel coordinate (n + 1) / 2 * sW (pixel a has its centre at a + 1/2),
+            // two pixels of margin each side; then the froxel columns of those pixels
+            const int sW = s * g.W, sH = s * g.H;
+            float gx0 = (xmin + 1.f) * 0.5f * sW, gx1 = (xmax + 1.f) * 0.5f * sW;
+            float gy0 = (ymin + 1.f) * 0.5f * sH, gy1 = (ymax + 1.f) * 0.5f * sH;
+            gx0 = fmaxf(fminf(gx0, 1e9f), -1e9f); gx1 = fmaxf(fminf(gx1, 1e9f), -1e9f);
+            gy0 = fmaxf(fminf(gy0, 1e9f), -1e9f); gy1 = fmaxf(fminf(gy1, 1e9f), -1e9f);
+            const int a0 = max((int)floorf(gx0) - 2, 0), a1 = min((int)floorf(gx1) + 2, sW - 1);
+            const int b0 = max((int)floorf(gy0) - 2, 0), b1 = min((int)floorf(gy1) + 2, sH - 1);
+            if (a0 <= a1 && b0 <= b1) {
+                rec.sa0 = a0; rec.sa1 = a1; rec.sb0 = b0; rec.sb1 = b1;
+                rec.x0 = a0 / s; rec.y0 = b0 / s;
+                rec.nx = a1 / s - rec.x0 + 1; rec.ny = b1 / s - rec.y0 + 1;
                 cnt = rec.nx * rec.ny;
             }
         }
@@ -246,13 +254,17 @@ __global__ void __launch_bounds__(256, 4) froxel_items_kernel(
         int last_k = -1;
         float zlo = 0.f, zhi = -1.f;  // slice interval of last_k
         bool kept = false;            // TEST: the item found a froxel of the PVS
-        for (int bb = y * s; bb < y * s + s && !kept; ++bb) {
+        // the column's rays inside the face's pixel rectangle
+        const int i0 = max(fr.sa0 - x * s, 0), i1 = min(fr.sa1 - x * s, s - 1);
+        const int b_end = min(fr.sb1 + 1, y * s + s);
+        for (int bb = max(y * s, fr.sb0); bb < b_end && !kept; ++bb) {
             const float ny = ys[bb];
             const float sy = __fmul_rn(ny, tanh_);
             const float su_ax = __fmul_rn(sy, u_ax), su_1 = __fmul_rn(sy, u1), su_2 = __fmul_rn(sy, u2);
 #pragma unroll
             for (int i = 0; i < CAP; ++i) {
                 if (i >= s) break;
+                if (i < i0 || i > i1) continue;
                 const float d_ax = __fadd_rn(ca_ax[i], su_ax);
                 if (d_ax == 0.0f) continue;
                 const float t = __fdiv_rn(num, d_ax);
@@ -330,7 +342,7 @@ static npvs_status froxel_run(const float* boxes, const int32_t* box_offsets, in
     float* centres = ar.take<float>((size_t)s * g.W + (size_t)s * g.H);
     launch_k(raster_centres_kernel, ceil_div((long long)s * (g.W + g.H), 256), 256, 0, st, s * g.W, s * g.H, centres);
     NPVS_TRY(check_launch("raster_centres_kernel"));
-    launch_k(face_setup_kernel, ceil_div(F, 256), 256, 0, st, boxes, box_offsets, n_boxes, cams, g, faces, counts);
+    launch_k(face_setup_kernel, ceil_div(F, 256), 256, 0, st, boxes, box_offsets, n_boxes, cams, g, (int)s, faces, counts);
     NPVS_TRY(check_launch("face_setup_kernel"));
     launch_k(chunk_scan_kernel, nchunk, kScanChunk, 0, st, counts, offs, F, csum);
     NPVS_TRY(check_launch("chunk_scan_kernel"));
