@@ -53,7 +53,16 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-viewcell batched measurement")
     ap.add_argument("--no-highres", action="store_true", help="skip the 512x512x192 measurement")
     ap.add_argument("--no-paper256", action="store_true",
-                    help="skip the 256^3 measurements (d=16, and d=1 without interleave)")
+                    help="skip the 256^3 measurements (d=8, 16, 32, and d=1 without interleave)")
+    ap.add_argument("--grid-only", default=None,
+                    choices=["city512", "paper256", "paper256_d1", "paper256_d8", "paper256_d32"],
+                    help="measure only this grid workload and print its record (not the headline line)")
+    ap.add_argument("--grid-batch", type=int, default=0, help="viewcells of the grid workload (0: its default)")
+    ap.add_argument("--grid-capacity", type=float, default=0.0,
+                    help="level capacity as a fraction of the sites (0: the workload's default)")
+    ap.add_argument("--profile-frame", action="store_true",
+                    help="after timing, run one eager frame of the tuned grid workload inside the NVTX range "
+                         "npvs_profile_frame (for a profiler's NVTX filter)")
     ap.add_argument("--train-points", type=int, default=256, help="ground-truth viewpoints per viewcell")
     ap.add_argument("--save-tuned", default=None,
                     help="write the autotuned per-layer kernel configurations of the headline frame (JSON)")
@@ -192,7 +201,7 @@ def frame_traffic(tuned: dict, chain_level: int, convs_only: bool = False):
 def tuned_label(cfg: dict) -> str:
     """Short name of an autotuned BF16 layer configuration."""
     if cfg.get("tune_form") == 2:
-        return "product"
+        return "product-split" if cfg.get("tune_max_split", 0) > 1 else "product"
     name = {3: "window", 4: "window3", 2: "gather-cp.async"}.get(cfg.get("tune_gather", 0), "gather")
     if cfg.get("tune_max_split") == 1:
         name += "-nosplit"
@@ -610,11 +619,12 @@ def run_highres(args, dev, tf_bf16, hbm_gbs):
     BF16, batch 4: four street viewcells of the 10,000-building city (heights lognormal(2.3, 0.7)).
     Per layer: achieved GB/s of the algorithmic bytes and TFLOP/s of the algorithmic FLOPs, from
     stage events captured in a graph of the same frame."""
+    B = args.grid_batch or 4
     boxes = I.city_boxes(0, I.CITY_LARGE)
-    vcs = I.city_viewcells(0, 4, I.CITY_LARGE)
+    vcs = I.city_viewcells(0, B, I.CITY_LARGE)
     return run_grid_workload(args, dev, tf_bf16, hbm_gbs, I.workload("city512"), boxes, vcs,
                              "city512: 512x512x192 froxels (s=4), d=8 (1024 ch), U-Net 64/128/256/512, "
-                             "10,000-building city seed 0, 4 viewcells")
+                             f"10,000-building city seed 0, {B} viewcells")
 
 
 def run_paper256(args, dev, tf_bf16, hbm_gbs):
@@ -623,7 +633,7 @@ def run_paper256(args, dev, tf_bf16, hbm_gbs):
     U-Net 192/256, head to 4096 logits; BF16, batch 1 (one viewcell of the 2,000-building city), as
     the paper's per-frame inference. Per layer: achieved GB/s and TFLOP/s of the algorithmic work."""
     boxes = I.city_boxes(0)
-    vcs = I.city_viewcells(0, 1)
+    vcs = I.city_viewcells(0, args.grid_batch or 1)
     return run_grid_workload(args, dev, tf_bf16, hbm_gbs, I.workload("paper256"), boxes, vcs,
                              "paper256: 256x256x256 froxels (s=8), d=16 (4096 ch), U-Net 192/256, "
                              "2,001-box city seed 0, 1 viewcell")
@@ -634,10 +644,22 @@ def run_paper256_d1(args, dev, tf_bf16, hbm_gbs):
     (192/256) on the 256^3 froxel grid itself, d = 1, one occupancy channel per froxel (stem 1 ->
     192, head 256 -> 1 logit). Level capacities at 10 % of the sites (1.9 % are occupied)."""
     boxes = I.city_boxes(0)
-    vcs = I.city_viewcells(0, 1)
+    vcs = I.city_viewcells(0, args.grid_batch or 1)
     return run_grid_workload(args, dev, tf_bf16, hbm_gbs, I.workload("paper256_d1"), boxes, vcs,
                              "paper256_d1: 256x256x256 froxels (s=8), d=1 (1 ch), U-Net 192/256, "
                              "2,001-box city seed 0, 1 viewcell", capacity_frac=0.1)
+
+
+def run_paper256_factor(args, dev, tf_bf16, hbm_gbs, d):
+    """The paper's runtime-and-memory comparison over the interleaving factor (d in {8, 16, 32},
+    Sec. 5 figure on runtime and peak memory): the paper256 scene and U-Net 192/256 at d = 8 (512
+    input channels per coarse site, 32^3 coarse grid) or d = 32 (32,768 channels, 8^3 coarse grid;
+    stem 32768 -> 192 and head 192 -> 32768)."""
+    boxes = I.city_boxes(0)
+    vcs = I.city_viewcells(0, args.grid_batch or 1)
+    return run_grid_workload(args, dev, tf_bf16, hbm_gbs, I.workload(f"paper256_d{d}"), boxes, vcs,
+                             f"paper256_d{d}: 256x256x256 froxels (s=8), d={d} ({d ** 3} ch), U-Net 192/256, "
+                             "2,001-box city seed 0, 1 viewcell")
 
 
 def run_grid_workload(args, dev, tf_bf16, hbm_gbs, wl, boxes, vcs, label, capacity_frac=1.0):
@@ -647,6 +669,8 @@ def run_grid_workload(args, dev, tf_bf16, hbm_gbs, wl, boxes, vcs, label, capaci
     for the rows that are active."""
     from paper_2509_24677_gb300 import _lib as L
     from paper_2509_24677_gb300 import ops, pipeline as P
+    if args.grid_capacity > 0:
+        capacity_frac = args.grid_capacity
     torch.cuda.synchronize()
     torch.cuda.reset_peak_memory_stats()
     mem0 = torch.cuda.memory_allocated()
@@ -693,12 +717,22 @@ def run_grid_workload(args, dev, tf_bf16, hbm_gbs, wl, boxes, vcs, label, capaci
             per_layer[k[5:]] = {"ms": round(acc[k], 4), "GB/s": round(v["bytes"] / t / 1e9, 1),
                                 "TFLOP/s": round(v["flops"] / t / 1e12, 2),
                                 "tensor_frac": round(v["flops"] / t / 1e12 / tf_bf16, 4)}
+    profiled = None
+    if args.profile_frame:
+        # one eager frame of the tuned per-layer kernels, in layer order, bracketed for a profiler
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("npvs_profile_frame")
+        fp.run(bx, of, cams)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        profiled = [[l.name, "simt" if l.cin % 8 or l.cout % 8 else tuned_label(tuned[l.name][0])]
+                    for l in wl.layers]
     occ = float(np.unpackbits(fp.occ.cpu().numpy().view(np.uint8)).mean())
     n_lv = [int(lv.n_rows.item()) for lv in fp.levels]
     lv_of = fp._level_of_layers()
     act_bytes = sum(n_lv[lv_of[l.name]] * l.cout * (4 if l.kind == "head1" else 2) for l in wl.layers)
     peak_mb = (torch.cuda.max_memory_allocated() - mem0) / 2**20
-    return {"workload": label, "batch": B, "ms_per_batch": round(ms, 3),
+    rec = {"workload": label, "batch": B, "ms_per_batch": round(ms, 3),
             "chain": {"level": chain_k, "ms_per_batch_by_level": chain_ms},
             "memory_mb": {"peak_device": round(peak_mb, 1), "layer_outputs_active": round(act_bytes / 2**20, 1)},
             "frames_per_s": round(B * 1000.0 / ms, 2), "occupancy": round(occ, 4),
@@ -706,7 +740,28 @@ def run_grid_workload(args, dev, tf_bf16, hbm_gbs, wl, boxes, vcs, label, capaci
             "stage_ms": {k: round(v, 4) for k, v in sorted(acc.items(), key=lambda kv: -kv[1]) if not k.startswith("conv:")},
             "conv_layers": per_layer, "peaks": {"hbm_gbs": hbm_gbs, "bf16_tflops": tf_bf16},
             "autotuned": {l.name: ("simt" if l.cin % 8 or l.cout % 8 else tuned_label(tuned[l.name][0]))
-                          for l in wl.layers}}
+                          for l in wl.layers}, "capacity_frac": capacity_frac}
+    if profiled:
+        rec["profile_frame_layers"] = profiled
+    return rec
+
+
+def run_grid_only(args):
+    """One grid workload on its own (its record as the printed line): for profiling one workload
+    without the headline frame and the other measurements."""
+    torch.cuda.set_device(0)
+    dev = "cuda:0"
+    hbm_gbs, tf_bf16, _ = load_peaks()
+    name = args.grid_only
+    if name == "city512":
+        rec = run_highres(args, dev, tf_bf16, hbm_gbs)
+    elif name == "paper256":
+        rec = run_paper256(args, dev, tf_bf16, hbm_gbs)
+    elif name == "paper256_d1":
+        rec = run_paper256_d1(args, dev, tf_bf16, hbm_gbs)
+    else:
+        rec = run_paper256_factor(args, dev, tf_bf16, hbm_gbs, int(name.split("_d")[1]))
+    print(json.dumps({"grid_only": name, **rec}), flush=True)
 
 
 def run_ours(args):
@@ -962,6 +1017,15 @@ def run_ours(args):
                                 "what": "ms per frame without interleave / with d=16 (the paper's Sec. 5.4 ablation "
                                         "table: 25.4 / 10.1 ms)"}
         line["paper256_d1"] = d1
+        by_d = {}
+        for d in (8, 32):
+            r = run_paper256_factor(args, dev, tf_bf16, hbm_gbs, d)
+            line[f"paper256_d{d}"] = r
+        for d in (8, 16, 32):
+            r = line["paper256"] if d == 16 else line[f"paper256_d{d}"]
+            by_d[str(d)] = {"ms_per_frame": r["ms_per_batch"], "peak_device_mb": r["memory_mb"]["peak_device"],
+                            "active_coarse_sites": r["active_sites"][0]}
+        line["paper256_by_interleave_factor"] = by_d
     if not args.no_train:
         del g16, g32, g16t
         line["train"] = run_train(args, dev, flush)
@@ -991,6 +1055,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.grid_only:
+        run_grid_only(args)
     else:
         run_ours(args)
 

@@ -164,7 +164,10 @@ typedef struct {
     size_t workspace_bytes;
     int32_t tune_stages;    /* BF16: shared-memory pipeline stages, 3..12 (window gather 2..12;
                                0 = the most that fit) */
-    int32_t tune_max_split; /* BF16: largest split-K factor (0 = 8; 1 = never split) */
+    int32_t tune_max_split; /* BF16: largest split-K factor (0 = 8; 1 = never split). The product
+                               form's GEMM splits only with tune_form 2 and tune_max_split >= 2
+                               (its partial tiles are summed in chunk order, so T differs from the
+                               unsplit tiles in rounding; the default keeps them unsplit) */
     int32_t tune_lag;       /* BF16 cp.async gather: groups in flight per thread before a stage is
                                published (0 = 2; clamped to stages - 1) */
     int32_t tune_gather;    /* BF16 gather form: 0 auto, 1 TMA tile::gather4 (cin % 32 == 0),
@@ -176,6 +179,11 @@ typedef struct {
     int32_t tune_gather_warps; /* BF16: gather warps per CTA, 4 or 8 (0 = 8) */
     int32_t tune_form;      /* BF16 SUBM3 / DOWN2 / UP2: 0 auto (product form when the workspace
                                holds T), 1 gather (UP2: scatter-epilogue) form, 2 product form */
+    const void* w_transposed; /* npvs_sparse_conv_bwd with BF16, nullable: the image of the
+                                 transposed convolution of the same weights (npvs_pack_weights_many,
+                                 transposed = 1), read by the dgrad instead of packing it from w in
+                                 the call. Must be NULL with F32 / F64 (NPVS_ERR_INVALID_ARG).
+                                 The forward ignores it. */
 } npvs_conv_desc;
 
 /* ---- status and errors --------------------------------------------------------------------- */
@@ -334,6 +342,29 @@ size_t npvs_packed_weight_bytes(int32_t kind, int32_t cin, int32_t cout);
  * npvs_packed_weight_bytes) with round-to-nearest-even. */
 npvs_status npvs_pack_weights(int32_t kind, int32_t cin, int32_t cout, const float* w,
                               void* packed, void* stream);
+
+/* One weight tensor of npvs_pack_weights_many: FP32 [taps][cin][cout] (device) of a (kind, cin,
+ * cout) convolution, packed into `packed` (device) as
+ *  - transposed = 0: the forward image, exactly as npvs_pack_weights (npvs_packed_weight_bytes);
+ *  - transposed = 1: the image of the convolution that the BF16 backward's dgrad runs (input and
+ *    output channels swapped; SUBM3 with the taps reversed, DOWN2 <-> UP2, DOWN3 <-> UP3, HEAD1),
+ *    npvs_packed_weight_bytes_transposed bytes, for npvs_conv_desc.w_transposed. */
+typedef struct {
+    int32_t kind, cin, cout, transposed;
+    const float* w;
+    void* packed;
+} npvs_pack_job;
+
+/* Bytes of the transposed image of a (kind, cin, cout) convolution's weights (0 when cin or cout
+ * is not a multiple of 8: that backward is not on the tensor cores). */
+size_t npvs_packed_weight_bytes_transposed(int32_t kind, int32_t cin, int32_t cout);
+
+/* Packs n weight tensors (host array of jobs) in one launch per 24 jobs (round to nearest even,
+ * the layouts of npvs_pack_weights): after an optimizer step, every forward and dgrad image of a
+ * network at once. All jobs are checked before the first launch (NPVS_ERR_INVALID_ARG for a NULL
+ * pointer or a non-positive size, NPVS_ERR_UNSUPPORTED for an unknown kind or a transposed image
+ * of a convolution whose cin or cout is not a multiple of 8); n = 0 launches nothing. */
+npvs_status npvs_pack_weights_many(int32_t n, const npvs_pack_job* jobs, void* stream);
 
 /* y = act(b + conv(x)) (+ skip); see npvs_conv_desc. bias (nullable): [cout], FP32, or FP64 with
  * dtype F64. Output-stationary: every output row is written exactly once (no atomics); rows >=

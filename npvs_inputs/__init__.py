@@ -266,6 +266,14 @@ def workload(name: str) -> Workload:
         return Workload(name, 256, 256, 256, 16, 1, 8, tuple(unet_layers(4096, [192, 256], 4096)))
     if name == "paper64":      # the same network at d=16 on a 64^3 grid (4^3 coarse sites)
         return Workload(name, 64, 64, 64, 16, 1, 8, tuple(unet_layers(4096, [192, 256], 4096)))
+    if name == "paper256_d8":  # the paper's grid at d=8 (512 ch), the same U-Net
+        return Workload(name, 256, 256, 256, 8, 1, 8, tuple(unet_layers(512, [192, 256], 512)))
+    if name == "paper64_d8":   # the same network on a 64^3 grid (8^3 coarse sites)
+        return Workload(name, 64, 64, 64, 8, 1, 8, tuple(unet_layers(512, [192, 256], 512)))
+    if name == "paper256_d32":  # the paper's grid at d=32 (32,768 ch), the same U-Net
+        return Workload(name, 256, 256, 256, 32, 1, 8, tuple(unet_layers(32768, [192, 256], 32768)))
+    if name == "paper64_d32":  # the same network on a 64^3 grid (2^3 coarse sites)
+        return Workload(name, 64, 64, 64, 32, 1, 8, tuple(unet_layers(32768, [192, 256], 32768)))
     if name == "paper256_d1":  # the paper256 network without interleave: one channel per froxel
         return Workload(name, 256, 256, 256, 1, 1, 8, tuple(unet_layers(1, [192, 256], 1)))
     if name == "nointerleave64":  # d=1 on a 64^3 grid, narrow widths (small enough for the oracle)

@@ -54,7 +54,11 @@ class ConvDesc(ctypes.Structure):
                 ("map", P), ("map2", P), ("n_out", P), ("cap_out", I32), ("n_in", P), ("cap_in", I32),
                 ("status", P), ("workspace", P), ("workspace_bytes", SZ), ("tune_stages", I32),
                 ("tune_max_split", I32), ("tune_lag", I32), ("tune_gather", I32), ("tune_gather_warps", I32),
-                ("tune_form", I32)]
+                ("tune_form", I32), ("w_transposed", P)]
+
+
+class PackJob(ctypes.Structure):
+    _fields_ = [("kind", I32), ("cin", I32), ("cout", I32), ("transposed", I32), ("w", P), ("packed", P)]
 
 
 class LossParams(ctypes.Structure):
@@ -103,6 +107,8 @@ SIGNATURES = {
     "npvs_conv_workspace_bytes": (SZ, [ctypes.POINTER(ConvDesc)]),
     "npvs_packed_weight_bytes": (SZ, [I32, I32, I32]),
     "npvs_pack_weights": (I32, [I32, I32, I32, P, P, P]),
+    "npvs_packed_weight_bytes_transposed": (SZ, [I32, I32, I32]),
+    "npvs_pack_weights_many": (I32, [I32, ctypes.POINTER(PackJob), P]),
     "npvs_sparse_conv_fwd": (I32, [ctypes.POINTER(ConvDesc), P, P, P, P, P, P]),
     "npvs_gt_raycast": (I32, [P, P, P, P, I32, Grid, I32, P, P, P]),
     "npvs_forward_workspace_bytes": (SZ, [ctypes.POINTER(NetDesc)]),

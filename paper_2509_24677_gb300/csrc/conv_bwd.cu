@@ -306,14 +306,16 @@ BwdPlan plan_bwd(const npvs_conv_desc& d) {
     }
     t.workspace = nullptr;
     t.workspace_bytes = 0;
-    p.mode = 1;
-    switch (d.kind) {
-        case NPVS_CONV_SUBM3: t.kind = NPVS_CONV_SUBM3; t.map2 = nullptr; p.mode = 2; break;
-        case NPVS_CONV_DOWN2: t.kind = NPVS_CONV_UP2; t.map = d.map2; t.map2 = d.map; break;
-        case NPVS_CONV_UP2: t.kind = NPVS_CONV_DOWN2; t.map = d.map2; t.map2 = d.map; break;
-        case NPVS_CONV_DOWN3: t.kind = NPVS_CONV_UP3; t.map = d.map2; t.map2 = d.map; break;
-        case NPVS_CONV_UP3: t.kind = NPVS_CONV_DOWN3; t.map = d.map2; t.map2 = d.map; break;
-        default: t.kind = NPVS_CONV_HEAD1; t.map = nullptr; t.map2 = nullptr; break;
+    t.w_transposed = nullptr;
+    t.kind = transposed_kind(d.kind, &p.mode);
+    if (d.kind == NPVS_CONV_SUBM3) {
+        t.map2 = nullptr;
+    } else if (d.kind == NPVS_CONV_HEAD1) {
+        t.map = nullptr;
+        t.map2 = nullptr;
+    } else {  // the strided pairs: the maps swap roles
+        t.map = d.map2;
+        t.map2 = d.map;
     }
     p.td = t;
     if (d.dtype == NPVS_BF16) {
@@ -380,7 +382,8 @@ npvs_status run_dgrad(const npvs_conv_desc& d, BwdPlan& p, const void* w, const 
     if (!dx) return NPVS_OK;
     void* wt = ar.take<char>(p.wt_bytes);
     if (d.dtype == NPVS_BF16) {
-        NPVS_TRY(pack_weights_mode(p.td.kind, p.td.cin, p.td.cout, (const float*)w, wt, p.mode, st));
+        if (d.w_transposed) wt = const_cast<void*>(d.w_transposed);  // packed after the optimizer step
+        else NPVS_TRY(pack_weights_mode(p.td.kind, p.td.cin, p.td.cout, (const float*)w, wt, p.mode, st));
         p.td.workspace = ar.take<char>(p.conv_bytes);
         p.td.workspace_bytes = p.conv_bytes;
     } else {
@@ -423,6 +426,8 @@ extern "C" npvs_status npvs_sparse_conv_bwd(const npvs_conv_desc* desc, const vo
     NPVS_REQUIRE(d.kind == NPVS_CONV_HEAD1 || d.map, NPVS_ERR_INVALID_ARG, "npvs_sparse_conv_bwd: map is NULL");
     NPVS_REQUIRE(d.dtype != NPVS_BF16 || !bf16_narrow(d.cin, d.cout), NPVS_ERR_UNSUPPORTED,
                  "npvs_sparse_conv_bwd: BF16 needs cin and cout multiples of 8");
+    NPVS_REQUIRE(!d.w_transposed || d.dtype == NPVS_BF16, NPVS_ERR_INVALID_ARG,
+                 "npvs_sparse_conv_bwd: w_transposed is a BF16 image");
     NPVS_REQUIRE(!d.relu || y, NPVS_ERR_INVALID_ARG, "npvs_sparse_conv_bwd: a ReLU layer needs its output y");
     NPVS_REQUIRE(!(d.relu && d.out_f32), NPVS_ERR_UNSUPPORTED, "npvs_sparse_conv_bwd: ReLU with out_f32 is not supported");
     NPVS_REQUIRE(!dx || d.kind == NPVS_CONV_SUBM3 || d.kind == NPVS_CONV_HEAD1 || d.map2, NPVS_ERR_INVALID_ARG,

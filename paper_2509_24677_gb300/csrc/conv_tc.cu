@@ -48,6 +48,7 @@ struct TcParams {
     int kind, cin, cout, relu, out_f32;
     int scatter;   // epilogue: GEMM column block j -> child row map2[n][j] (transposed stride-2 conv)
     int tout;      // epilogue: raw FP32 accumulators into T [rows][Ntot] (product form)
+    int tout_split;  // product form: the k-blocks may be split (partials summed in chunk order)
     int KB, Kflat, Ntot, Npad, BN, n_tiles, stages;
     int gmode;     // A operand: 0 cp.async gather, 1 TMA gather4, 2 TMA dense tile (rows m0..m0+127),
                    // 3 window gather (SUBM3: dense TMA windows of input rows, A built in shared memory)
@@ -269,7 +270,8 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
     const int n_rows = min(*p.n_rows, p.cap_rows);
     const int tiles = ((n_rows + kBM - 1) / kBM) * p.n_tiles;
     int ksplit = 1, kbc = p.KB;
-    if (p.part != nullptr && !p.tout && tiles > 0 && 2 * tiles <= (int)gridDim.x && p.max_split > 1) {
+    if (p.part != nullptr && (!p.tout || p.tout_split) && tiles > 0 && 2 * tiles <= (int)gridDim.x &&
+        p.max_split > 1) {
         ksplit = min(min(p.KB, p.max_split), (int)gridDim.x / tiles);
         kbc = (p.KB + ksplit - 1) / ksplit;
         ksplit = (p.KB + kbc - 1) / kbc;
@@ -602,7 +604,7 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
             mbar_wait(tfull0 + 8 * buf, (tc >> 1) & 1, abort_flag, p.wait_limit);
             if (__any_sync(0xffffffffu, *abort_flag)) break;
             tc_fence_after();
-            if (p.tout) {
+            if (p.tout && ksplit == 1) {
                 for (int c0 = 0; c0 < p.BN; c0 += 16) {
                     uint32_t v[16];
                     tmem_ld16(taddr_row + (uint32_t)c0, v);
@@ -676,7 +678,21 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
                                     acc[q + 3] += v4.w;
                                 }
                             }
-                            store16(p, n, nt * p.BN + c0, wb + c0, acc);
+                            if (p.tout) {  // the summed product tile into T, no epilogue
+                                const int ng = nt * p.BN + c0;
+                                if (ng >= p.Ntot) continue;
+                                float* dst = p.T + (size_t)n * p.Ntot + ng;
+                                if (ng + 16 <= p.Ntot) {
+#pragma unroll
+                                    for (int q = 0; q < 16; q += 4)
+                                        *reinterpret_cast<float4*>(dst + q) =
+                                            make_float4(acc[q], acc[q + 1], acc[q + 2], acc[q + 3]);
+                                } else {
+                                    for (int q = 0; q < 16 && ng + q < p.Ntot; ++q) dst[q] = acc[q];
+                                }
+                            } else {
+                                store16(p, n, nt * p.BN + c0, wb + c0, acc);
+                            }
                         }
                     }
                     if (lane == 0) p.counters[tile * 4 + ew] = 0;
@@ -823,39 +839,65 @@ __device__ __forceinline__ float weight_at(const float* __restrict__ w, int mode
     return w[((size_t)s * cout + co) * cin + ci];
 }
 
-__global__ void pack_weights_kernel(int kind, int cin, int cout, TcShape sh, const float* __restrict__ w,
-                                    __nv_bfloat16* __restrict__ out, int mode) {
-    pdl_begin();
-    const int taps = conv_taps(kind);
-    const size_t total = (size_t)sh.KB * sh.Npad * sh.BKE;
-    const int nchunk = sh.BKE / 8;
-    const bool colblocks = sh.J > 1;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-        const int kk = (int)(e % sh.BKE);
-        const size_t rest = e / sh.BKE;
-        const int n = (int)(rest % sh.Npad), kb = (int)(rest / sh.Npad);
-        const int k = kb * sh.BKE + kk;
-        float v = 0.0f;
-        if (k < sh.Kflat && n < sh.Ntot) {
-            if (colblocks) {
-                const int j = n / cout, o = n - j * cout;
-                v = weight_at(w, mode, taps, cin, cout, j, k, o);
-            } else {
-                const int t = k / cin, ci = k - t * cin;
-                v = weight_at(w, mode, taps, cin, cout, t, ci, n);
-            }
-        }
-        const int sw = ((n * sh.RB) >> 7) & (nchunk - 1);
-        const size_t dst = ((size_t)kb * sh.Npad + n) * sh.BKE + ((((kk >> 3) ^ sw) << 3) | (kk & 7));
-        out[dst] = __float2bfloat16_rn(v);
+// One element e of the image of a (kind, cin, cout) convolution in form sh (plain = 1: the plain
+// [taps][cin][cout] BF16 image of the SIMT-path convolutions, e indexes it directly).
+struct PackImage {
+    TcShape sh;
+    const float* w;
+    __nv_bfloat16* out;
+    int kind, cin, cout, mode, plain;
+    long long begin;  // first element of this image in the launch's element range
+    long long size;   // its elements
+};
+
+__device__ __forceinline__ void pack_element(const PackImage& im, long long e) {
+    if (im.plain) {
+        im.out[e] = __float2bfloat16_rn(im.w[e]);
+        return;
     }
+    const TcShape& sh = im.sh;
+    const int taps = conv_taps(im.kind);
+    const int nchunk = sh.BKE / 8;
+    const int kk = (int)(e % sh.BKE);
+    const long long rest = e / sh.BKE;
+    const int n = (int)(rest % sh.Npad), kb = (int)(rest / sh.Npad);
+    const int k = kb * sh.BKE + kk;
+    float v = 0.0f;
+    if (k < sh.Kflat && n < sh.Ntot) {
+        if (sh.J > 1) {  // column blocks: n = j * cout + o, k = ci
+            const int j = n / im.cout, o = n - j * im.cout;
+            v = weight_at(im.w, im.mode, taps, im.cin, im.cout, j, k, o);
+        } else {         // n = o, k = t * cin + ci
+            const int t = k / im.cin, ci = k - t * im.cin;
+            v = weight_at(im.w, im.mode, taps, im.cin, im.cout, t, ci, n);
+        }
+    }
+    const int sw = ((n * sh.RB) >> 7) & (nchunk - 1);
+    const size_t dst = ((size_t)kb * sh.Npad + n) * sh.BKE + ((((kk >> 3) ^ sw) << 3) | (kk & 7));
+    im.out[dst] = __float2bfloat16_rn(v);
 }
 
-// Plain BF16 image [taps][cin][cout] (round to nearest even) of the SIMT-path convolutions.
-__global__ void pack_plain_kernel(size_t total, const float* __restrict__ w, __nv_bfloat16* __restrict__ out) {
+constexpr int kMaxPackImages = 48;
+
+struct PackBatch {
+    PackImage im[kMaxPackImages];
+    int n;
+    long long total;
+};
+
+// Every image of the batch in one grid-stride loop over the concatenated element ranges.
+__global__ void __launch_bounds__(256) pack_images_kernel(const __grid_constant__ PackBatch b) {
     pdl_begin();
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x)
-        out[e] = __float2bfloat16_rn(w[e]);
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < b.total;
+         e += (long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = b.n - 1;  // the last image that begins at or before e
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (b.im[mid].begin <= e) lo = mid;
+            else hi = mid - 1;
+        }
+        pack_element(b.im[lo], e - b.im[lo].begin);
+    }
 }
 
 int conv_taps_host(int kind) { return conv_taps(kind); }
@@ -1094,6 +1136,9 @@ npvs_status conv_tc_fwd(const npvs_conv_desc& d, const void* x, const void* w, c
                  : reinterpret_cast<const __nv_bfloat16*>(reinterpret_cast<const char*>(w) + img0);
         p.taps = 0;
         p.tout = 1;
+        // k-split only when asked for explicitly: the unsplit product tiles are what the layer chain
+        // reproduces bit for bit
+        p.tout_split = d.tune_form == 2 && d.tune_max_split > 1;
         p.T = T;
         p.n_rows = n_x;
         p.cap_rows = rows_x;
@@ -1150,27 +1195,56 @@ extern "C" size_t npvs_packed_weight_bytes(int32_t kind, int32_t cin, int32_t co
 
 namespace npvs {
 
+// The images of one weight tensor (mode as weight_at) appended to the batch: the plain image of a
+// narrow convolution, else the direct (or transposed-conv) form and, where it exists, the product form.
+static void add_images(PackBatch& b, int kind, int cin, int cout, const float* w, void* packed, int mode) {
+    char* out = (char*)packed;
+    auto push = [&](const PackImage& im) {
+        b.im[b.n] = im;
+        b.im[b.n].begin = b.total;
+        b.total += im.size;
+        ++b.n;
+    };
+    if (bf16_narrow(cin, cout)) {
+        PackImage im{};
+        im.w = w;
+        im.out = (__nv_bfloat16*)out;
+        im.plain = 1;
+        im.size = (long long)conv_taps_host(kind) * cin * cout;
+        push(im);
+        return;
+    }
+    const int nforms = has_product_form(kind) ? 2 : 1;
+    for (int f = 0; f < nforms; ++f) {
+        PackImage im{};
+        im.sh = tc_shape(kind, cin, cout, f);
+        im.w = w;
+        im.out = (__nv_bfloat16*)out;
+        im.kind = kind;
+        im.cin = cin;
+        im.cout = cout;
+        im.mode = mode;
+        im.size = (long long)im.sh.KB * im.sh.Npad * im.sh.BKE;
+        push(im);
+        out += packed_image_bytes(kind, cin, cout, f);
+    }
+}
+
+static npvs_status launch_pack(const PackBatch& b, cudaStream_t st) {
+    if (b.n == 0 || b.total == 0) return NPVS_OK;
+    const int grid = (int)std::min<long long>((b.total + 255) / 256, (long long)kNumSMs * 16);
+    launch_k(pack_images_kernel, grid, 256, 0, st, b);
+    return check_launch("pack_images_kernel");
+}
+
 npvs_status pack_weights_mode(int kind, int cin, int cout, const float* w, void* packed, int mode, cudaStream_t st) {
     NPVS_REQUIRE(w && packed && cin > 0 && cout > 0, NPVS_ERR_INVALID_ARG, "npvs_pack_weights: bad arguments");
     NPVS_REQUIRE(valid_conv_kind(kind), NPVS_ERR_UNSUPPORTED, "npvs_pack_weights: unknown kind");
-    if (bf16_narrow(cin, cout)) {
-        NPVS_REQUIRE(mode == 0, NPVS_ERR_UNSUPPORTED, "BF16 conv: transposed packing needs cin and cout multiples of 8");
-        const size_t total = (size_t)conv_taps_host(kind) * cin * cout;
-        const int grid = (int)std::min<size_t>((total + 255) / 256, (size_t)kNumSMs * 16);
-        launch_k(pack_plain_kernel, grid, 256, 0, st, total, w, (__nv_bfloat16*)packed);
-        return check_launch("pack_plain_kernel");
-    }
-    const int nforms = has_product_form(kind) ? 2 : 1;
-    char* out = (char*)packed;
-    for (int f = 0; f < nforms; ++f) {
-        TcShape sh = tc_shape(kind, cin, cout, f);
-        const size_t total = (size_t)sh.KB * sh.Npad * sh.BKE;
-        const int grid = (int)std::min<size_t>((total + 255) / 256, (size_t)kNumSMs * 16);
-        launch_k(pack_weights_kernel, grid, 256, 0, st, kind, cin, cout, sh, w, (__nv_bfloat16*)out, mode);
-        NPVS_TRY(check_launch("pack_weights_kernel"));
-        out += packed_image_bytes(kind, cin, cout, f);
-    }
-    return NPVS_OK;
+    NPVS_REQUIRE(mode == 0 || !bf16_narrow(cin, cout), NPVS_ERR_UNSUPPORTED,
+                 "BF16 conv: transposed packing needs cin and cout multiples of 8");
+    PackBatch b{};
+    add_images(b, kind, cin, cout, w, packed, mode);
+    return launch_pack(b, st);
 }
 
 }  // namespace npvs
@@ -1178,4 +1252,43 @@ npvs_status pack_weights_mode(int kind, int cin, int cout, const float* w, void*
 extern "C" npvs_status npvs_pack_weights(int32_t kind, int32_t cin, int32_t cout, const float* w, void* packed,
                                          void* stream) {
     return pack_weights_mode(kind, cin, cout, w, packed, 0, as_stream(stream));
+}
+
+extern "C" size_t npvs_packed_weight_bytes_transposed(int32_t kind, int32_t cin, int32_t cout) {
+    if (!valid_conv_kind(kind) || cin <= 0 || cout <= 0 || bf16_narrow(cin, cout)) return 0;
+    int mode;
+    return npvs_packed_weight_bytes(transposed_kind(kind, &mode), cout, cin);
+}
+
+extern "C" npvs_status npvs_pack_weights_many(int32_t n, const npvs_pack_job* jobs, void* stream) {
+    NPVS_REQUIRE(n >= 0 && (n == 0 || jobs), NPVS_ERR_INVALID_ARG, "npvs_pack_weights_many: bad arguments");
+    for (int i = 0; i < n; ++i) {  // every job is checked before the first launch
+        const npvs_pack_job& j = jobs[i];
+        if (!(j.w && j.packed && j.cin > 0 && j.cout > 0 && (j.transposed == 0 || j.transposed == 1))) {
+            set_error("npvs_pack_weights_many: bad job %d", i);
+            return NPVS_ERR_INVALID_ARG;
+        }
+        if (!valid_conv_kind(j.kind) || (j.transposed && bf16_narrow(j.cin, j.cout))) {
+            set_error("npvs_pack_weights_many: job %d: unknown kind, or a transposed image of a convolution whose "
+                      "cin or cout is not a multiple of 8", i);
+            return NPVS_ERR_UNSUPPORTED;
+        }
+    }
+    cudaStream_t st = as_stream(stream);
+    PackBatch b{};
+    for (int i = 0; i < n; ++i) {
+        const npvs_pack_job& j = jobs[i];
+        if (b.n + 2 > kMaxPackImages) {  // a job adds at most two images
+            NPVS_TRY(launch_pack(b, st));
+            b = PackBatch{};
+        }
+        if (j.transposed) {
+            int mode;
+            const int tk = transposed_kind(j.kind, &mode);
+            add_images(b, tk, j.cout, j.cin, j.w, j.packed, mode);
+        } else {
+            add_images(b, j.kind, j.cin, j.cout, j.w, j.packed, 0);
+        }
+    }
+    return launch_pack(b, st);
 }

@@ -54,6 +54,21 @@ TcShape tc_shape(int kind, int cin, int cout, int form);
 // reversed, the transpose of a submanifold convolution).
 npvs_status pack_weights_mode(int kind, int cin, int cout, const float* w, void* packed, int mode, cudaStream_t st);
 
+// The convolution whose forward is the dgrad of `kind` (input and output channels swapped), and the
+// packing mode that reads the stored weights as its weights: the submanifold conv is its own
+// transpose with the taps reversed (mode 2), the strided pairs and the head swap (mode 1).
+inline int transposed_kind(int kind, int* mode) {
+    *mode = kind == NPVS_CONV_SUBM3 ? 2 : 1;
+    switch (kind) {
+        case NPVS_CONV_SUBM3: return NPVS_CONV_SUBM3;
+        case NPVS_CONV_DOWN2: return NPVS_CONV_UP2;
+        case NPVS_CONV_UP2: return NPVS_CONV_DOWN2;
+        case NPVS_CONV_DOWN3: return NPVS_CONV_UP3;
+        case NPVS_CONV_UP3: return NPVS_CONV_DOWN3;
+        default: return NPVS_CONV_HEAD1;
+    }
+}
+
 // BF16 weight gradient on the tensor cores (dW FP32 [taps][cin][cout]) from the layer input x and
 // the masked output gradient g; scratch from `ar` (wgrad_tc_bytes).
 bool wgrad_tc_supported(const npvs_conv_desc& d);

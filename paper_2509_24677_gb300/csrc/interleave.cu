@@ -22,20 +22,27 @@ struct ILParams {
     int d, in_ch, dtype, cap;
     int Xc, Yc, Zc;
     long long n_sites;
+    const uint8_t* flags;  // nullable: each site's activity, written by il_active_kernel (d >= 16)
 };
 
 // DD: the interleave factor as a compile-time constant (0: runtime p.d). The d row words of SG
 // depth slices (SG = 4 for d >= 16, else 1) are loaded together and OR-ed; the test stops after
 // the first occupied group.
-template <int DD>
-__device__ __forceinline__ bool site_active(const ILParams& p, long long site, int& b, int& Z, int& Y,
-                                            int& X) {
+__device__ __forceinline__ void site_coords(const ILParams& p, long long site, int& b, int& Z, int& Y, int& X) {
     X = (int)(site % p.Xc);
     long long t = site / p.Xc;
     Y = (int)(t % p.Yc);
     t /= p.Yc;
     Z = (int)(t % p.Zc);
     b = (int)(t / p.Zc);
+}
+
+// Whether the d^3 block of site (b, Z, Y, X) holds an occupied froxel: the given activity flag, else
+// the d row words of SG depth slices (SG = 4 for d >= 16, else 1) loaded together and OR-ed, the
+// test stopping after the first occupied group.
+template <int DD>
+__device__ __forceinline__ bool site_active(const ILParams& p, long long site, int b, int Z, int Y, int X) {
+    if (p.flags) return p.flags[site] != 0;
     const int d = DD ? DD : p.d, WW = p.g.W >> 5, x0 = d * X;
     const uint32_t mask = d == 32 ? 0xffffffffu : (((1u << d) - 1u) << (x0 & 31));
     const uint32_t* w = p.bits + (((size_t)b * p.g.D + (size_t)d * Z) * p.g.H + (size_t)d * Y) * WW + (x0 >> 5);
@@ -52,12 +59,40 @@ __device__ __forceinline__ bool site_active(const ILParams& p, long long site, i
     return false;
 }
 
+// Activity of every site for d >= 16, one warp per site: the lanes share the d^2 row words of the
+// site's block and the warp votes (a thread per site would walk up to 1,024 words alone).
+__global__ void __launch_bounds__(256) il_active_kernel(ILParams p, uint8_t* __restrict__ flags) {
+    pdl_begin();
+    const int lane = threadIdx.x & 31;
+    const int d = p.d, dd = d * d, WW = p.g.W >> 5;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long site = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); site < p.n_sites;
+         site += warps) {  // warp-uniform bound
+        int b, Z, Y, X;
+        site_coords(p, site, b, Z, Y, X);
+        const int x0 = d * X;
+        const uint32_t mask = d == 32 ? 0xffffffffu : (((1u << d) - 1u) << (x0 & 31));
+        const uint32_t* w = p.bits + (((size_t)b * p.g.D + (size_t)d * Z) * p.g.H + (size_t)d * Y) * WW + (x0 >> 5);
+        uint32_t acc = 0;
+#pragma unroll 8
+        for (int j = lane; j < dd; j += 32) {
+            const int dz = j / d, dy = j - dz * d;
+            acc |= __ldg(w + ((size_t)dz * p.g.H + dy) * WW);
+        }
+        const bool any = __any_sync(0xffffffffu, (acc & mask) != 0u);
+        if (lane == 0) flags[site] = any ? 1 : 0;
+    }
+}
+
 template <int DD>
 __global__ void __launch_bounds__(kSitesPerCta) il_count_kernel(ILParams p, int* __restrict__ counts) {
     pdl_begin();
     long long site = (long long)blockIdx.x * kSitesPerCta + threadIdx.x;
-    int b, Z, Y, X;
-    int f = site < p.n_sites ? (int)site_active<DD>(p, site, b, Z, Y, X) : 0;
+    int b = 0, Z = 0, Y = 0, X = 0, f = 0;
+    if (site < p.n_sites) {
+        site_coords(p, site, b, Z, Y, X);
+        f = (int)site_active<DD>(p, site, b, Z, Y, X);
+    }
     int c = __syncthreads_count(f);
     if (threadIdx.x == 0) counts[blockIdx.x] = c;
 }
@@ -128,7 +163,11 @@ __global__ void __launch_bounds__(kSitesPerCta) il_write_kernel(ILParams p, cons
     long long site = (long long)blockIdx.x * kSitesPerCta + threadIdx.x;
     int b = 0, Z = 0, Y = 0, X = 0;
     bool in = site < p.n_sites;
-    int f = in ? (int)site_active<DD>(p, site, b, Z, Y, X) : 0;
+    int f = 0;
+    if (in) {
+        site_coords(p, site, b, Z, Y, X);
+        f = (int)site_active<DD>(p, site, b, Z, Y, X);
+    }
     int nloc;
     int loc = block_exclusive_scan(f, sw, &nloc);
     int rank = block_off[blockIdx.x] + loc;
@@ -155,18 +194,35 @@ __global__ void __launch_bounds__(kSitesPerCta) il_write_kernel(ILParams p, cons
     }
 }
 
-// The features of large interleave factors, spread over the whole device: one item per (feature
-// row, slab dz) of the rows il_write_kernel compacted (n_active, device).
+// The features of large interleave factors (d >= 16), spread over the whole device: one item per
+// (feature row, slab dz, row dy) of the rows il_write_kernel compacted (n_active, device), writing
+// the d occupancy values of that froxel row (and, with in_ch = 2, its d depth values) eight at a
+// time; the values are those il_write_slab writes.
 template <int DD>
 __global__ void __launch_bounds__(256) il_feats_kernel(ILParams p, const int32_t* __restrict__ coords,
                                                        const int32_t* __restrict__ n_active, void* __restrict__ feats) {
     pdl_begin();
-    const int d = DD ? DD : p.d;
-    const long long n = (long long)min(*n_active, p.cap) * d;
+    const int d = DD ? DD : p.d, d2 = d * d, d3 = d2 * d, C = p.in_ch * d3, WW = p.g.W >> 5;
+    const long long n = (long long)min(*n_active, p.cap) * d2;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int r = (int)(e / d), dz = (int)(e - (long long)r * d);
+        const int r = (int)(e / d2), q = (int)(e - (long long)r * d2), dz = q / d, dy = q - dz * d;
         const int4 st = reinterpret_cast<const int4*>(coords)[r];
-        il_write_slab<DD>(p, st, r, dz, feats);
+        const int k = d * st.y + dz, x0 = d * st.w;
+        const float dep = __fdiv_rn((float)(2 * k + 1), (float)(2 * p.g.D));
+        const uint32_t wbits =
+            p.bits[(((size_t)st.x * p.g.D + k) * p.g.H + (size_t)d * st.z + dy) * WW + (x0 >> 5)] >> (x0 & 31);
+        const size_t base = (size_t)r * C + (size_t)dz * d2 + (size_t)dy * d;
+        for (int j0 = 0; j0 < d; j0 += 8) {
+            float vo[8], vd[8];
+#pragma unroll
+            for (int q2 = 0; q2 < 8; ++q2) {
+                const bool occ = (wbits >> (j0 + q2)) & 1u;
+                vo[q2] = occ ? 1.0f : 0.0f;
+                vd[q2] = occ ? dep : 0.0f;
+            }
+            store_vals(feats, p.dtype, base + j0, vo, 8);
+            if (p.in_ch == 2) store_vals(feats, p.dtype, base + d3 + j0, vd, 8);
+        }
     }
 }
 
@@ -238,7 +294,8 @@ static void launch_il_write(const ILParams& p, int nb, const int* offs, int32_t*
         default: launch_k(il_write_kernel<0>, nb, kSitesPerCta, 0, st, p, offs, coords, feats, table, status, wf);
     }
     if (wf) return;
-    const int grid = (int)std::max<long long>(1, std::min<long long>(ceil_div((long long)p.cap * p.d, 256), kNumSMs * 8));
+    const int grid =
+        (int)std::max<long long>(1, std::min<long long>(ceil_div((long long)p.cap * p.d * p.d, 256), kNumSMs * 8));
     if (p.d == 16) launch_k(il_feats_kernel<16>, grid, 256, 0, st, p, coords, n_active, feats);
     else launch_k(il_feats_kernel<0>, grid, 256, 0, st, p, coords, n_active, feats);
 }
@@ -253,11 +310,20 @@ static void launch_il_count(const ILParams& p, int nb, int* counts, cudaStream_t
     }
 }
 
+// The site activity pre-pass for large interleave factors (flags: one byte per site).
+static bool il_flags_pass(int d) { return d >= 16; }
+
+static void launch_il_active(const ILParams& p, uint8_t* flags, cudaStream_t st) {
+    const int grid = (int)std::max<long long>(1, std::min<long long>(ceil_div(p.n_sites, 8), kNumSMs * 16));
+    launch_k(il_active_kernel, grid, 256, 0, st, p, flags);
+}
+
 extern "C" size_t npvs_interleave_workspace_bytes(npvs_grid g, int32_t d) {
     if (!valid_d(d) || d <= 0) return 0;
     long long sites = (long long)g.B * (g.W / d) * (g.H / d) * (g.D / d);
     long long nb = (sites + kSitesPerCta - 1) / kSitesPerCta;
-    return 2 * Arena::round((size_t)(nb + 1) * sizeof(int)) + 256;
+    const size_t flags = il_flags_pass(d) ? Arena::round((size_t)sites) : 0;
+    return 2 * Arena::round((size_t)(nb + 1) * sizeof(int)) + flags + 256;
 }
 
 extern "C" npvs_status npvs_interleave(const uint32_t* occ_bits, npvs_grid g, int32_t d, int32_t in_ch,
@@ -288,9 +354,16 @@ extern "C" npvs_status npvs_interleave(const uint32_t* occ_bits, npvs_grid g, in
     p.Zc = g.D / d;
     p.n_sites = (long long)g.B * p.Xc * p.Yc * p.Zc;
     const int nb = ceil_div(p.n_sites, kSitesPerCta);
+    p.flags = nullptr;
     Arena ar(workspace, workspace_bytes);
     int* counts = ar.take<int>(nb + 1);
     int* offs = ar.take<int>(nb + 1);
+    if (il_flags_pass(d)) {
+        uint8_t* flags = ar.take<uint8_t>((size_t)p.n_sites);
+        launch_il_active(p, flags, st);
+        NPVS_TRY(check_launch("il_active_kernel"));
+        p.flags = flags;
+    }
     launch_il_count(p, nb, counts, st);
     NPVS_TRY(check_launch("il_count_kernel"));
     NPVS_TRY(scan_block_counts(counts, offs, nb, n_active, capacity, status, st));
@@ -404,6 +477,7 @@ extern "C" npvs_status npvs_interleave_noalloc(const uint32_t* occ_bits, npvs_gr
     p.Yc = g.H / d;
     p.Zc = g.D / d;
     p.n_sites = n_sites;
+    p.flags = nullptr;  // no room for the activity pre-pass: every site is tested where it is read
     const int nb = ceil_div(p.n_sites, kSitesPerCta);
     int* counts = scratch;                      // fully rewritten by every call before it is read
     int* offs = scratch + kNoAllocMaxCtas + 1;  // likewise

@@ -205,6 +205,29 @@ def npvs_pack_weights(kind: int, cin: int, cout: int, w32: torch.Tensor, packed:
     check(_lib().npvs_pack_weights(kind, cin, cout, _p(w32), _p(packed), _s(stream)), "npvs_pack_weights")
 
 
+def npvs_packed_weight_bytes_transposed(kind: int, cin: int, cout: int) -> int:
+    return _lib().npvs_packed_weight_bytes_transposed(kind, cin, cout)
+
+
+def make_pack_jobs(jobs):
+    """A host array of npvs_pack_job from (kind, cin, cout, transposed, w32, packed) tuples; the
+    tensors must stay alive while the array is used."""
+    arr = (L.PackJob * max(1, len(jobs)))()
+    for i, (kind, cin, cout, transposed, w32, packed) in enumerate(jobs):
+        _need_cuda(w32, packed)
+        assert w32.dtype == torch.float32 and w32.is_contiguous()
+        arr[i] = L.PackJob(kind, cin, cout, int(transposed), _p(w32), _p(packed))
+    return arr, len(jobs)
+
+
+def npvs_pack_weights_many(jobs, stream=None):
+    """jobs: the pair make_pack_jobs returns (or a list of its tuples)."""
+    if isinstance(jobs, list):
+        jobs = make_pack_jobs(jobs)
+    arr, n = jobs
+    check(_lib().npvs_pack_weights_many(n, arr, _s(stream)), "npvs_pack_weights_many")
+
+
 def npvs_conv_workspace_bytes(desc: Optional[L.ConvDesc] = None) -> int:
     return int(_lib().npvs_conv_workspace_bytes(ctypes.byref(desc) if desc is not None else None))
 

@@ -88,12 +88,10 @@ class Net:
 
     def packed(self) -> List[torch.Tensor]:
         if self._packed is None:
-            self._packed = []
-            for l, w in zip(self.layers, self.w32):
-                nb = ops.npvs_packed_weight_bytes(KIND[l.kind], l.cin, l.cout)
-                buf = torch.empty(nb, dtype=torch.uint8, device=self.device)
-                ops.npvs_pack_weights(KIND[l.kind], l.cin, l.cout, w, buf)
-                self._packed.append(buf)
+            self._packed = [torch.empty(ops.npvs_packed_weight_bytes(KIND[l.kind], l.cin, l.cout), dtype=torch.uint8,
+                                        device=self.device) for l in self.layers]
+            ops.npvs_pack_weights_many([(KIND[l.kind], l.cin, l.cout, 0, w, buf)
+                                        for l, w, buf in zip(self.layers, self.w32, self._packed)])
         return self._packed
 
     def repack(self):
@@ -261,12 +259,12 @@ class FramePipeline:
 
     # ---- autotuning ------------------------------------------------------------------------------
     CANDIDATES = {
-        "subm3": [dict(tune_form=2), dict(tune_form=1, tune_gather_warps=8),
+        "subm3": [dict(tune_form=2), dict(tune_form=2, tune_max_split=8), dict(tune_form=1, tune_gather_warps=8),
                   dict(tune_form=1, tune_gather_warps=8, tune_max_split=1), dict(tune_form=1, tune_gather_warps=4),
                   dict(tune_form=1, tune_gather=3), dict(tune_form=1, tune_gather=3, tune_max_split=1),
                   dict(tune_form=1, tune_gather=3, tune_gather_warps=4), dict(tune_form=1, tune_gather=4),
                   dict(tune_form=1, tune_gather=4, tune_max_split=1)],
-        "down2": [dict(tune_form=2), dict(tune_form=1, tune_gather_warps=8),
+        "down2": [dict(tune_form=2), dict(tune_form=2, tune_max_split=8), dict(tune_form=1, tune_gather_warps=8),
                   dict(tune_form=1, tune_gather_warps=8, tune_max_split=1)],
         "up2": [dict(tune_form=2), dict(tune_form=1)],
         "head1": [dict()],

@@ -145,10 +145,20 @@ class Trainer:
         self.v = torch.zeros_like(self.params.theta)
         self.adam_state = torch.zeros(2, dtype=torch.int32, device=device)
         self.packed: List[torch.Tensor] = []
+        self.packed_t: List[Optional[torch.Tensor]] = []   # dgrad images (BF16 tensor-core layers)
         if dtype == L.BF16:
-            for l in self.layers:
-                self.packed.append(torch.empty(ops.npvs_packed_weight_bytes(KIND[l.kind], l.cin, l.cout),
+            jobs = []
+            for i, l in enumerate(self.layers):
+                k = KIND[l.kind]
+                self.packed.append(torch.empty(ops.npvs_packed_weight_bytes(k, l.cin, l.cout),
                                                dtype=torch.uint8, device=device))
+                jobs.append((k, l.cin, l.cout, 0, self.params.w[i], self.packed[i]))
+                # the first layer's input has no gradient: no dgrad image
+                nt = ops.npvs_packed_weight_bytes_transposed(k, l.cin, l.cout) if i > 0 else 0
+                self.packed_t.append(torch.empty(nt, dtype=torch.uint8, device=device) if nt else None)
+                if nt:
+                    jobs.append((k, l.cin, l.cout, 1, self.params.w[i], self.packed_t[i]))
+            self._pack_jobs = ops.make_pack_jobs(jobs)
             self.repack()
 
     def state_dict(self) -> dict:
@@ -164,9 +174,9 @@ class Trainer:
 
     # ---- parts of a step ----------------------------------------------------------------------
     def repack(self):
-        """BF16 tensor-core images of the current master weights."""
-        for i, l in enumerate(self.layers):
-            ops.npvs_pack_weights(KIND[l.kind], l.cin, l.cout, self.params.w[i], self.packed[i])
+        """BF16 tensor-core images of the current master weights: every layer's forward image and
+        the image its backward's dgrad reads, in one launch per 24 layers."""
+        ops.npvs_pack_weights_many(self._pack_jobs)
 
     def _operands(self):
         return self.packed if self.dtype == L.BF16 else self.params.w
@@ -209,9 +219,14 @@ class Trainer:
                 y = self.u[i]
             dx = None if i == 0 else self.dacts[self.layers[i - 1].name]
             sg = self.skip_grad.get(i)
-            ops.npvs_sparse_conv_bwd(desc, x, self.params.w[i], y if l.relu else None, self.dacts[l.name], dx,
-                                     self.dacts[sg] if sg else None, self.params.gw[i], self.params.gb[i],
-                                     self.bwd_ws)
+            wt = self.packed_t[i] if self.dtype == L.BF16 and dx is not None else None
+            desc.w_transposed = wt.data_ptr() if wt is not None else None
+            try:
+                ops.npvs_sparse_conv_bwd(desc, x, self.params.w[i], y if l.relu else None, self.dacts[l.name], dx,
+                                         self.dacts[sg] if sg else None, self.params.gw[i], self.params.gb[i],
+                                         self.bwd_ws)
+            finally:
+                desc.w_transposed = None
 
     def optimizer_step(self):
         ops.npvs_adam_step(self.params.theta, self.params.grad, self.m, self.v, self.adam_prm, self.adam_state)
@@ -263,7 +278,8 @@ class SparseConv(torch.autograd.Function):
     @staticmethod
     def backward(ctx, dy):
         x, w, b = ctx.saved_tensors[:3]
-        d = ctx.desc
+        d = L.ConvDesc.from_buffer_copy(ctx.desc)
+        d.w_transposed = None            # the dgrad image is packed from w in the call
         y = None
         if d.relu:
             if ctx.has_skip:   # recompute the output before the skip for the ReLU mask

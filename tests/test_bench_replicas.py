@@ -64,6 +64,7 @@ def test_tuned_labels_and_traffic_selection():
     win3 = {"tune_form": 1, "tune_gather": 4}
     gat = {"tune_form": 1, "tune_gather_warps": 4}
     assert bench.tuned_label(prod) == "product"
+    assert bench.tuned_label({"tune_form": 2, "tune_max_split": 8}) == "product-split"
     assert bench.tuned_label(win) == "window-nosplit"
     assert bench.tuned_label(win3) == "window3"
     assert bench.tuned_label(gat) == "gather-4w"

@@ -103,7 +103,7 @@ def test_packed_weight_and_workspace_sizes_of_narrow_bf16_convs():
 
 def test_strided3_sizes_on_host():
     """DOWN3 / UP3 keep product tiles of 27 taps and a tiled BF16 image at least as large as the
-    plain one; they have no backward (no backward workspace)."""
+    plain one; their backward's workspace holds the dgrad image (the transposed pair's)."""
     from paper_2509_24677_gb300 import _lib as L
     from paper_2509_24677_gb300 import ops
     base = ops.npvs_conv_workspace_bytes(None)
@@ -111,7 +111,9 @@ def test_strided3_sizes_on_host():
         d = ops.conv_desc(kind, L.BF16, 32, 64, True, None, None, 500, cap_in=700)
         assert ops.npvs_conv_workspace_bytes(d) >= base + 700 * 27 * 64 * 4
         assert ops.npvs_packed_weight_bytes(kind, 32, 64) >= 2 * 27 * 32 * 64 * 2
-        assert ops.npvs_conv_bwd_workspace_bytes(d) == 0
+        other = L.CONV_UP3 if kind == L.CONV_DOWN3 else L.CONV_DOWN3
+        assert ops.npvs_packed_weight_bytes_transposed(kind, 32, 64) == ops.npvs_packed_weight_bytes(other, 64, 32)
+        assert ops.npvs_conv_bwd_workspace_bytes(d) >= ops.npvs_packed_weight_bytes_transposed(kind, 32, 64)
     assert ops.npvs_packed_weight_bytes(6, 32, 64) == 0
 
 
@@ -141,9 +143,15 @@ def test_argument_errors_of_the_strided3_entry_points_on_host():
         d = L.ConvDesc(kind, L.F32, 16, 16, 1, 0, fake, None, n, 24, None, 0)   # no n_in / cap_in
         assert lib.npvs_sparse_conv_fwd(ctypes.byref(d), fake, fake, None, None, fake, None) == L.ERR_INVALID_ARG
         d.n_in, d.cap_in = n, 192
-        assert lib.npvs_sparse_conv_bwd(ctypes.byref(d), fake, fake, fake, fake, None, None, fake, None, fake,
-                                        1 << 20, None) == L.ERR_UNSUPPORTED
-        assert "forward only" in lib.npvs_last_error().decode()
+        # the dgrad of a strided conv runs the transposed pair over the other map: map2 is required
+        assert lib.npvs_sparse_conv_bwd(ctypes.byref(d), fake, fake, fake, fake, fake, None, fake, None, fake,
+                                        1 << 20, None) == L.ERR_INVALID_ARG
+        assert "map2" in lib.npvs_last_error().decode()
+        d.map2 = fake
+        d.w_transposed = fake   # a prepacked dgrad image is a BF16 operand
+        assert lib.npvs_sparse_conv_bwd(ctypes.byref(d), fake, fake, fake, fake, fake, None, fake, None, fake,
+                                        1 << 20, None) == L.ERR_INVALID_ARG
+        assert "w_transposed" in lib.npvs_last_error().decode()
     d = L.ConvDesc(9, L.F32, 16, 16, 1, 0, fake, None, n, 24, n, 24)
     assert lib.npvs_sparse_conv_fwd(ctypes.byref(d), fake, fake, None, None, fake, None) == L.ERR_UNSUPPORTED
 
@@ -160,3 +168,32 @@ def test_wait_limit_setter_is_host_only_and_checks_its_argument():
         ops.npvs_set_wait_limit(-1)
     assert e.value.status == L.ERR_INVALID_ARG
     assert ops.npvs_set_wait_limit(0) == 4_000_000_000
+
+
+def test_pack_weights_many_checks_every_job_on_host():
+    """npvs_pack_weights_many validates all jobs before any launch (placeholder pointers are never
+    dereferenced), n = 0 is a no-op, and the dgrad image of each kind has the size of the forward
+    image of its transposed convolution."""
+    import ctypes
+    from paper_2509_24677_gb300 import _lib as L
+    from paper_2509_24677_gb300 import ops
+    lib = L.load()
+    fake = ctypes.c_void_p(256).value
+    ok = L.PackJob(L.CONV_SUBM3, 32, 64, 0, fake, fake)
+    arr = (L.PackJob * 3)(ok, ok, L.PackJob(L.CONV_SUBM3, 32, 64, 0, None, fake))
+    assert lib.npvs_pack_weights_many(3, arr, None) == L.ERR_INVALID_ARG
+    assert "job 2" in lib.npvs_last_error().decode()
+    arr[2] = L.PackJob(L.CONV_SUBM3, 1, 64, 1, fake, fake)        # transposed image of a narrow conv
+    assert lib.npvs_pack_weights_many(3, arr, None) == L.ERR_UNSUPPORTED
+    arr[2] = L.PackJob(11, 32, 64, 0, fake, fake)
+    assert lib.npvs_pack_weights_many(3, arr, None) == L.ERR_UNSUPPORTED
+    arr[2] = L.PackJob(L.CONV_SUBM3, 32, 64, 2, fake, fake)        # transposed is 0 or 1
+    assert lib.npvs_pack_weights_many(3, arr, None) == L.ERR_INVALID_ARG
+    assert lib.npvs_pack_weights_many(-1, arr, None) == L.ERR_INVALID_ARG
+    assert lib.npvs_pack_weights_many(0, None, None) == L.OK
+    pairs = {L.CONV_SUBM3: L.CONV_SUBM3, L.CONV_DOWN2: L.CONV_UP2, L.CONV_UP2: L.CONV_DOWN2,
+             L.CONV_HEAD1: L.CONV_HEAD1, L.CONV_DOWN3: L.CONV_UP3, L.CONV_UP3: L.CONV_DOWN3}
+    for k, t in pairs.items():
+        for cin, cout in ((32, 64), (192, 256), (64, 48)):
+            assert ops.npvs_packed_weight_bytes_transposed(k, cin, cout) == ops.npvs_packed_weight_bytes(t, cout, cin)
+        assert ops.npvs_packed_weight_bytes_transposed(k, 1, 64) == 0

@@ -126,7 +126,8 @@ def clustered_bits(rng, B, D, H, W, frac=0.04):
 
 
 @pytest.mark.parametrize("d,in_ch,dt", [(2, 1, "f32"), (4, 2, "bf16"), (4, 2, "f32"), (8, 2, "bf16"), (2, 2, "bf16"),
-                                        (16, 1, "bf16"), (16, 2, "f32"), (1, 1, "bf16"), (1, 2, "f32")])
+                                        (16, 1, "bf16"), (16, 2, "f32"), (1, 1, "bf16"), (1, 2, "f32"),
+                                        (8, 1, "f32"), (32, 1, "bf16"), (32, 1, "f32")])
 def test_interleave_bit_exact(d, in_ch, dt):
     L, ops, _ = lib()
     rng = np.random.default_rng(d * 10 + in_ch)
@@ -288,13 +289,14 @@ WINDOW_MODES = ("window", "window-split", "window-s2", "window3", "window3-split
 
 
 @pytest.mark.parametrize("dt,mode", [("f32", None), ("bf16", "gather"), ("bf16", "gather-split"),
-                                     ("bf16", "product"), ("bf16", "window"), ("bf16", "window-split"),
+                                     ("bf16", "product"), ("bf16", "product-split"), ("bf16", "window"),
+                                     ("bf16", "window-split"),
                                      ("bf16", "window3"), ("f32", "product"), ("f32", "gather")])
 @pytest.mark.parametrize("kind,cin,cout", CONV_CASES)
 def test_single_conv_parity(kind, cin, cout, dt, mode):
     if dt == "bf16" and kind == "up2" and cout % 16 and cin % 8 == 0 and cout % 8 == 0:
         pytest.skip("BF16 up conv on the tensor cores needs cout % 16 == 0")
-    if mode == "product" and kind not in ("subm3", "down2", "up2"):
+    if mode in ("product", "product-split") and kind not in ("subm3", "down2", "up2"):
         pytest.skip("the product form applies to submanifold, strided and transposed convs")
     if mode in WINDOW_MODES and (kind != "subm3" or cin % 32):
         pytest.skip("the window gather applies to submanifold convs with cin % 32 == 0")
@@ -387,11 +389,13 @@ def single_conv(kind, cin, cout, dt, mode, occ, rng, want_ref=True):
     lv_in = lvs[1] if kind == "up2" else lvs[0]
     desc = ops.conv_desc(kid, dtype, cin, cout, True, mp, lv_out.n_rows, lv_out.capacity, out_f32=out_f32,
                          map2=lvs[0].down if kind == "up2" else None, n_in=lv_in.n_rows, cap_in=lv_in.capacity,
-                         status=status, form={"gather": 1, "gather-split": 1, "product": 2}.get(mode, 0),
+                         status=status, form={"gather": 1, "gather-split": 1, "product": 2,
+                                              "product-split": 2}.get(mode, 0),
                          gather=(4 if mode.startswith("window3") else 3) if mode in WINDOW_MODES else 0,
-                         max_split=1 if mode in ("window", "window-s2", "window3") else 0,
+                         max_split=1 if mode in ("window", "window-s2", "window3") else
+                         (8 if mode == "product-split" else 0),
                          stages=2 if mode == "window-s2" else 0)
-    if mode in ("gather-split", "product", "window-split", "window3-split"):
+    if mode in ("gather-split", "product", "product-split", "window-split", "window3-split"):
         ws = ops.conv_workspace(ops.npvs_conv_workspace_bytes(desc), DEV)
         desc.workspace, desc.workspace_bytes = ws.data_ptr(), ws.numel()
     w_dev = torch.from_numpy(w).to(DEV).contiguous()
@@ -441,7 +445,8 @@ def gpu_frame(wl, boxes, vc, ws, bs, dtype, tune=False):
 @pytest.mark.parametrize("name,dt", [("plain64", "f32"), ("plain64", "bf16"), ("city256", "bf16"), ("city256", "f32"),
                                      ("city256", "bf16-tuned"), ("paper64", "bf16"), ("paper64", "f32"),
                                      ("paper64", "bf16-tuned"), ("nointerleave64", "bf16"), ("nointerleave64", "f32"),
-                                     ("nointerleave64", "bf16-tuned")])
+                                     ("nointerleave64", "bf16-tuned"), ("paper64_d8", "bf16"), ("paper64_d8", "f32"),
+                                     ("paper64_d8", "bf16-tuned"), ("paper64_d32", "bf16"), ("paper64_d32", "f32")])
 def test_frame_parity(name, dt):
     L, ops, P = lib()
     wl = I.workload(name)

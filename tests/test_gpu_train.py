@@ -332,6 +332,22 @@ def oracle_grads(wl, G, GT, ws, bs):
     return float(Lref), [w.grad.numpy() for w in W_], [b.grad.numpy() for b in B_]
 
 
+# BF16 gradients of the 3-level U-Net against the FP64 oracle, per layer: measured normwise errors of
+# (weights, biases) on the seeded inputs of make_trainer. The BF16 forward's rounding flips the ReLU
+# masks of near-zero pre-activations, and the gradients of the deeper layers sum over those flips;
+# the backward kernels themselves are within 2e-2 of the oracle at the GPU's own activations
+# (test_backward_given_forward_matches_oracle). Each layer must stay within 1.5x its measured error
+# (kernel-order changes move the flips a little); the cosine must stay >= 0.95.
+BF16_UNET_GRAD_ERR = {
+    "stem": (3.86e-2, 1.44e-2), "enc0a": (2.88e-2, 1.64e-2), "enc0b": (2.31e-2, 1.77e-2),
+    "down0": (2.14e-1, 8.49e-2), "enc1a": (1.14e-1, 9.35e-2), "enc1b": (1.56e-1, 1.16e-1),
+    "down1": (2.01e-1, 3.17e-1), "enc2a": (4.40e-1, 2.82e-1), "enc2b": (3.90e-1, 2.43e-1),
+    "up1": (1.65e-1, 8.79e-2), "dec1a": (1.50e-1, 8.09e-2), "dec1b": (9.15e-2, 6.86e-2),
+    "up0": (1.60e-1, 4.37e-2), "dec0a": (2.85e-2, 1.77e-2), "dec0b": (7.96e-3, 3.55e-3),
+    "head": (3.21e-3, 4.19e-4),
+}
+
+
 @pytest.mark.parametrize("wl_name,dt", [("plain64", "f32"), ("plain64", "bf16"), ("unet-small", "f32"),
                                         ("unet-small", "bf16")])
 def test_network_gradients_match_oracle(wl_name, dt):
@@ -357,10 +373,10 @@ def test_network_gradients_match_oracle(wl_name, dt):
     print("per-layer gradient error (weights, biases, cosine):",
           [(n, f"{a:.2e}", f"{b:.2e}", f"{c:.4f}") for (n, a, b), c in zip(worst, cosines)])
     if wl_name == "unet-small" and dt == "bf16":
-        # The BF16 forward's rounding flips ReLU masks of near-zero pre-activations; deep in the
-        # U-Net that moves the FP64-oracle gradient by up to tens of percent normwise (the backward
-        # kernels themselves stay within 2e-2 at the GPU's own activations, see
-        # test_backward_given_forward_matches_oracle). Stated here, bounded by direction.
+        assert [n for n, _, _ in worst] == list(BF16_UNET_GRAD_ERR)
+        over = [(n, a, b) for n, a, b in worst
+                if a > 1.5 * BF16_UNET_GRAD_ERR[n][0] or b > 1.5 * BF16_UNET_GRAD_ERR[n][1]]
+        assert not over, over
         assert min(cosines) >= 0.95, cosines
         return
     bad = [(n, a, b) for n, a, b in worst if a > tol or b > tol]
