@@ -65,7 +65,8 @@ def parse():
                          "npvs_profile_frame (for a profiler's NVTX filter)")
     ap.add_argument("--train-points", type=int, default=256, help="ground-truth viewpoints per viewcell")
     ap.add_argument("--save-tuned", default=None,
-                    help="write the autotuned per-layer kernel configurations of the headline frame (JSON)")
+                    help="write the autotuned per-layer kernel configurations of the headline frame (of the "
+                         "grid workload with --grid-only) (JSON)")
     ap.add_argument("--tuned", default=None,
                     help="use saved per-layer configurations instead of autotuning (a run under a profiler "
                          "would otherwise tune on the profiler's launch times)")
@@ -685,7 +686,15 @@ def run_grid_workload(args, dev, tf_bf16, hbm_gbs, wl, boxes, vcs, label, capaci
     stt = ops.npvs_check_status(fp.status)
     if stt != 0:
         raise RuntimeError(f"device status {stt:#x} set in the {wl.name} frame")
-    tuned = fp.autotune(bx, of, cams, reps=3)
+    if args.grid_only and args.tuned:            # the configuration a plain run saved (for profiling)
+        with open(args.tuned) as fh:
+            fp.apply_tuned(json.load(fh))
+        tuned = {k: (v, float("nan")) for k, v in fp.tuned_configs().items()}
+    else:
+        tuned = fp.autotune(bx, of, cams, reps=3)
+    if args.grid_only and args.save_tuned:
+        with open(args.save_tuned, "w") as fh:
+            json.dump(fp.tuned_configs(), fh)
     nf, g, chain_k, chain_ms = fastest_chain_frame(P, L, wl, net, B, fp.descs, bx, of, len(boxes) * B, cams, dev,
                                                    capacity_frac=capacity_frac, reps=5)
     st = torch.cuda.current_stream()
