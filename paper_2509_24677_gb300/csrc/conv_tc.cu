@@ -43,12 +43,15 @@ namespace {
 constexpr int threads_for(int PW) { return 32 * (PW + 5); }
 constexpr int kBM = 128;
 constexpr int kSplitSlots = kNumSMs;
+constexpr uint32_t kOutTileBytes = 32 * 16 * 4;                // 32 rows x 16 FP32 columns (64-byte rows)
+constexpr uint32_t kOutStageBytes = 4 * 2 * kOutTileBytes;    // two tiles per epilogue warp
 
 struct TcParams {
     int kind, cin, cout, relu, out_f32;
     int scatter;   // epilogue: GEMM column block j -> child row map2[n][j] (transposed stride-2 conv)
     int tout;      // epilogue: raw FP32 accumulators into T [rows][Ntot] (product form)
     int tout_split;  // product form: the k-blocks may be split (partials summed in chunk order)
+    int tout_tma;    // product form: T leaves through staging tiles and TMA stores (Ntot % 16 == 0)
     int KB, Kflat, Ntot, Npad, BN, n_tiles, stages;
     int gmode;     // A operand: 0 cp.async gather, 1 TMA gather4, 2 TMA dense tile (rows m0..m0+127),
                    // 3 window gather (SUBM3: dense TMA windows of input rows, A built in shared memory)
@@ -218,7 +221,8 @@ __device__ __forceinline__ void window_build_a(uint8_t* a_stage, const uint8_t* 
 // and MMAs before TMEM is freed.
 template <int LAG, int PW>
 __global__ void __launch_bounds__(threads_for(PW), 1)
-    conv_tc_kernel(const TcParams p, const __grid_constant__ CUtensorMap tmap) {
+    conv_tc_kernel(const TcParams p, const __grid_constant__ CUtensorMap tmap,
+                   const __grid_constant__ CUtensorMap tmap_t) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int S = p.stages;
@@ -228,7 +232,9 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
     const uint32_t win1 = p.gmode == 3 ? (uint32_t)p.win_rows * p.RB : 0u;  // bytes of one window
     uint8_t* sA = smem;
     uint8_t* sB = smem + (size_t)S * a_bytes;
-    uint8_t* win = sB + (size_t)S * b_bytes;  // window gather: 3 windows (dz = -1, 0, 1)
+    // product form: per epilogue warp two 32-row x 16-column FP32 staging tiles for the T stores
+    float* s_out = reinterpret_cast<float*>(sB + (size_t)S * b_bytes);
+    uint8_t* win = sB + (size_t)S * b_bytes + (p.tout_tma ? kOutStageBytes : 0u);  // window gather: 3 windows
     int* map_s = reinterpret_cast<int*>(win + 3 * (size_t)win1);
     float* s_bias = reinterpret_cast<float*>(map_s + kBM * p.taps + 4);  // [4 warps][256]
     uint64_t* bars = reinterpret_cast<uint64_t*>(s_bias + 4 * 256);
@@ -586,6 +592,7 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
         const int ew = warp - PW, r = ew * 32 + lane;
         float* wb = s_bias + ew * 256;
         uint32_t tc = 0;
+        uint32_t out_it = 0;  // product form: T chunks stored by this warp (staging tile out_it & 1)
         for (int u = blockIdx.x; u < units; u += gridDim.x, ++tc) {
             const int tile = u / ksplit;
             const int mt = tile / p.n_tiles, nt = tile - mt * p.n_tiles;
@@ -604,7 +611,7 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
             mbar_wait(tfull0 + 8 * buf, (tc >> 1) & 1, abort_flag, p.wait_limit);
             if (__any_sync(0xffffffffu, *abort_flag)) break;
             tc_fence_after();
-            if (p.tout && ksplit == 1) {
+            if (p.tout && ksplit == 1 && !p.tout_tma) {  // rows of 16 columns by plain stores
                 for (int c0 = 0; c0 < p.BN; c0 += 16) {
                     uint32_t v[16];
                     tmem_ld16(taddr_row + (uint32_t)c0, v);
@@ -621,6 +628,38 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
                     } else {
                         for (int q = 0; q < 16 && ng + q < p.Ntot; ++q) dst[q] = __uint_as_float(v[q]);
                     }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
+            } else if (p.tout && ksplit == 1) {
+                // Per 16-column chunk the warp's 32 accumulator rows go to a staging tile in the
+                // 64-byte swizzle (row r's 16-byte chunk c at position c ^ ((r >> 1) & 3)) and leave
+                // with one TMA tensor store of 32 full 64-byte row segments; two tiles alternate and
+                // lane 0 tracks the bulk groups. Rows past n_rows (up to the tile end) carry values
+                // of rows nothing reads; rows past T's capacity are clipped by the tensor map.
+                const int row0 = mt * kBM + ew * 32;
+                for (int c0 = 0; c0 < p.BN; c0 += 16) {
+                    uint32_t v[16];
+                    tmem_ld16(taddr_row + (uint32_t)c0, v);
+                    tmem_ld_wait();
+                    const int ng = nt * p.BN + c0;
+                    if (row0 >= n_rows || ng >= p.Ntot) continue;  // warp-uniform
+                    float* tile = s_out + (ew * 2 + (out_it & 1)) * (kOutTileBytes / 4);
+                    if (lane == 0) bulk_wait_read1();  // the store that last read this tile is done
+                    __syncwarp();
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        *reinterpret_cast<float4*>(tile + lane * 16 + ((c ^ ((lane >> 1) & 3)) << 2)) =
+                            make_float4(__uint_as_float(v[4 * c]), __uint_as_float(v[4 * c + 1]),
+                                        __uint_as_float(v[4 * c + 2]), __uint_as_float(v[4 * c + 3]));
+                    fence_proxy_async_shared();
+                    __syncwarp();
+                    if (lane == 0) {
+                        tma_store_2d(&tmap_t, ng, row0, smem_u32(tile));
+                        bulk_commit();
+                    }
+                    ++out_it;
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -699,6 +738,11 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
                 }
             }
         }
+        if (p.tout_tma && lane == 0) {  // the T stores have read their tiles and landed (also after a timeout)
+            bulk_wait_all();
+            fence_proxy_async_global();
+        }
+        __syncwarp();
     } else {
         if (lane == 0) {
             // -------------------------------------------------------------- MMA issuer
@@ -906,14 +950,15 @@ constexpr int kMaxStages = 12;
 constexpr size_t kMaxSmem = 227 * 1024;
 
 // win: bytes of the three windows of the window gather (0 otherwise); G: k-blocks per stage.
-size_t tc_smem_bytes(int BN, int RB, int taps, int S, size_t win = 0, int G = 1) {
-    return 1024 + (size_t)S * G * (kBM + BN) * RB + win + (size_t)kBM * taps * 4 + 16 + 4 * 256 * 4 +
+// out: the product form's T staging tiles (kOutStageBytes), else 0
+size_t tc_smem_bytes(int BN, int RB, int taps, int S, size_t win = 0, int G = 1, size_t out = 0) {
+    return 1024 + (size_t)S * G * (kBM + BN) * RB + out + win + (size_t)kBM * taps * 4 + 16 + 4 * 256 * 4 +
            (3 * S + 8) * 8 + 16 + 8 * 3 * 4;
 }
 
-int tc_stages(int BN, int RB, int taps) {
+int tc_stages(int BN, int RB, int taps, size_t out = 0) {
     for (int S = kMaxStages; S > 4; --S)
-        if (tc_smem_bytes(BN, RB, taps, S) <= kMaxSmem) return S;
+        if (tc_smem_bytes(BN, RB, taps, S, 0, 1, out) <= kMaxSmem) return S;
     return 4;
 }
 
@@ -932,21 +977,23 @@ int win_rows_for(int BN, int RB, int G, int* stages) {
 }
 
 template <int LAG, int PW>
-npvs_status launch_tc(const TcParams& p, const CUtensorMap& tm, int grid, size_t smem, cudaStream_t st) {
+npvs_status launch_tc(const TcParams& p, const CUtensorMap& tm, const CUtensorMap& tm_t, int grid, size_t smem,
+                      cudaStream_t st) {
     static std::atomic<unsigned long long> seen[kMaxDevices];
     NPVS_TRY(ensure_dynamic_smem((const void*)conv_tc_kernel<LAG, PW>, (int)kMaxSmem, seen, "conv_tc_kernel"));
-    launch_k(conv_tc_kernel<LAG, PW>, grid, threads_for(PW), smem, st, p, tm);
+    launch_k(conv_tc_kernel<LAG, PW>, grid, threads_for(PW), smem, st, p, tm, tm_t);
     return check_launch("conv_tc_kernel");
 }
 
 template <int PW>
-npvs_status launch_tc_lag(int lag, const TcParams& p, const CUtensorMap& tm, int grid, size_t smem, cudaStream_t st) {
+npvs_status launch_tc_lag(int lag, const TcParams& p, const CUtensorMap& tm, const CUtensorMap& tm_t, int grid,
+                          size_t smem, cudaStream_t st) {
     switch (lag) {
-        case 1: return launch_tc<1, PW>(p, tm, grid, smem, st);
-        case 2: return launch_tc<2, PW>(p, tm, grid, smem, st);
-        case 3: return launch_tc<3, PW>(p, tm, grid, smem, st);
-        case 4: return launch_tc<4, PW>(p, tm, grid, smem, st);
-        case 6: return launch_tc<6, PW>(p, tm, grid, smem, st);
+        case 1: return launch_tc<1, PW>(p, tm, tm_t, grid, smem, st);
+        case 2: return launch_tc<2, PW>(p, tm, tm_t, grid, smem, st);
+        case 3: return launch_tc<3, PW>(p, tm, tm_t, grid, smem, st);
+        case 4: return launch_tc<4, PW>(p, tm, tm_t, grid, smem, st);
+        case 6: return launch_tc<6, PW>(p, tm, tm_t, grid, smem, st);
         default: return fail(NPVS_ERR_INVALID_ARG, "npvs_sparse_conv_fwd: unsupported pipeline lag");
     }
 }
@@ -995,7 +1042,7 @@ npvs_status run_gemm(TcParams& p, const TcShape& sh, const npvs_conv_desc& d, co
         p.KB = 27 / p.G * p.ncb;  // pipeline stages of one tile
         win = 3 * (size_t)p.win_rows * sh.RB;
     } else {
-        p.stages = tc_stages(sh.BN, sh.RB, p.taps);
+        p.stages = tc_stages(sh.BN, sh.RB, p.taps, p.tout_tma ? kOutStageBytes : 0);
     }
     if (d.tune_stages >= (p.gmode == 3 ? 2 : 3) && d.tune_stages < p.stages) p.stages = d.tune_stages;
     lag = std::min(lag, p.stages - 1);
@@ -1003,9 +1050,23 @@ npvs_status run_gemm(TcParams& p, const TcShape& sh, const npvs_conv_desc& d, co
     p.acc_cols = 32;
     while ((int)p.acc_cols < sh.BN) p.acc_cols <<= 1;
     if (p.cap_rows <= 0) return NPVS_OK;
-    const size_t smem = tc_smem_bytes(sh.BN, sh.RB, p.taps, p.stages, win, p.G);
+    const size_t smem = tc_smem_bytes(sh.BN, sh.RB, p.taps, p.stages, win, p.G, p.tout_tma ? kOutStageBytes : 0);
     alignas(64) CUtensorMap tm;
     std::memset(&tm, 0, sizeof(tm));
+    alignas(64) CUtensorMap tm_t;  // product form: T [cap_rows][Ntot] FP32, 16 x 32 boxes, 64-byte swizzle
+    std::memset(&tm_t, 0, sizeof(tm_t));
+    if (p.tout_tma) {
+        EncodeTiledFn enc = encode_tiled();
+        NPVS_REQUIRE(enc != nullptr, NPVS_ERR_CUDA, "BF16 conv: cuTensorMapEncodeTiled unavailable");
+        const cuuint64_t gdim[2] = {(cuuint64_t)p.Ntot, (cuuint64_t)p.cap_rows};
+        const cuuint64_t gstride[1] = {(cuuint64_t)p.Ntot * 4};
+        const cuuint32_t box[2] = {16, 32};
+        const cuuint32_t estride[2] = {1, 1};
+        CUresult r = enc(&tm_t, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p.T, gdim, gstride, box, estride,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        NPVS_REQUIRE(r == CUDA_SUCCESS, NPVS_ERR_CUDA, "BF16 conv: product-tile tensor map encoding failed");
+    }
     if (p.gmode != 0) {
         EncodeTiledFn enc = encode_tiled();
         NPVS_REQUIRE(enc != nullptr, NPVS_ERR_CUDA, "BF16 conv: cuTensorMapEncodeTiled unavailable");
@@ -1027,8 +1088,8 @@ npvs_status run_gemm(TcParams& p, const TcShape& sh, const npvs_conv_desc& d, co
     }
     const long long tiles_cap = (long long)ceil_div(p.cap_rows, kBM) * sh.n_tiles;
     const int grid = (int)std::min<long long>(tiles_cap * (p.part ? p.KB : 1), kNumSMs);
-    return d.tune_gather_warps == 4 ? launch_tc_lag<4>(lag, p, tm, grid, smem, st)
-                                    : launch_tc_lag<8>(lag, p, tm, grid, smem, st);
+    return d.tune_gather_warps == 4 ? launch_tc_lag<4>(lag, p, tm, tm_t, grid, smem, st)
+                                    : launch_tc_lag<8>(lag, p, tm, tm_t, grid, smem, st);
 }
 
 }  // namespace
@@ -1140,6 +1201,8 @@ npvs_status conv_tc_fwd(const npvs_conv_desc& d, const void* x, const void* w, c
         // reproduces bit for bit
         p.tout_split = d.tune_form == 2 && d.tune_max_split > 1;
         p.T = T;
+        // TMA stores need 16-byte rows and addresses (the arena aligns T to 256 bytes)
+        p.tout_tma = sh.Ntot % 16 == 0 && (reinterpret_cast<uintptr_t>(T) & 255) == 0;
         p.n_rows = n_x;
         p.cap_rows = rows_x;
         p.gmode = sh.tma ? 2 : 0;
