@@ -196,17 +196,16 @@ __global__ void __launch_bounds__(kThreads, 1) conv_chain_kernel(const __grid_co
                     if (*abort_flag) break;
                     tc_fence_after();
                     for (int kb = 0; kb < L.KB; ++kb) {
-                        mbar_wait(full0 + 8 * m_s, m_ph, abort_flag, lim);
-                        if (*abort_flag) {
+                        if (!mbar_wait_ok(full0 + 8 * m_s, m_ph, abort_flag, lim)) {
                             stop = true;
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t a0 = smem_u32(sA + (size_t)m_s * kAStride);
-                        const uint32_t b0 = smem_u32(sB + (size_t)m_s * kBStride);
+                        // descriptors advanced by adding the 32-byte K steps to their address field
+                        const uint64_t ad = make_sdesc(smem_u32(sA) + (uint32_t)m_s * kAStride, L.RB);
+                        const uint64_t bd = make_sdesc(smem_u32(sB) + (uint32_t)m_s * kBStride, L.RB);
                         for (int k = 0; k < kk_steps; ++k)
-                            tc_mma(acc, make_sdesc(a0 + 32 * k, L.RB), make_sdesc(b0 + 32 * k, L.RB), idesc,
-                                   (kb > 0 || k > 0) ? 1u : 0u);
+                            tc_mma(acc, ad + 2 * k, bd + 2 * k, idesc, (kb > 0 || k > 0) ? 1u : 0u);
                         tc_commit(empty0 + 8 * m_s);
                         if (++m_s == kStages) {
                             m_s = 0;

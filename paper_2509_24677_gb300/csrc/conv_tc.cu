@@ -43,8 +43,9 @@ namespace {
 constexpr int threads_for(int PW) { return 32 * (PW + 5); }
 constexpr int kBM = 128;
 constexpr int kSplitSlots = kNumSMs;
-constexpr uint32_t kOutTileBytes = 32 * 16 * 4;                // 32 rows x 16 FP32 columns (64-byte rows)
-constexpr uint32_t kOutStageBytes = 4 * 2 * kOutTileBytes;    // two tiles per epilogue warp
+constexpr uint32_t kOutTileBytes = 32 * 16 * 4;  // 32 rows x 16 FP32 columns (64-byte rows)
+constexpr int kOutTilesPerWarp = 2;              // 32 columns per TMEM wait and bulk group
+constexpr uint32_t kOutStageBytes = 4 * kOutTilesPerWarp * kOutTileBytes;
 
 struct TcParams {
     int kind, cin, cout, relu, out_f32;
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
     const uint32_t win1 = p.gmode == 3 ? (uint32_t)p.win_rows * p.RB : 0u;  // bytes of one window
     uint8_t* sA = smem;
     uint8_t* sB = smem + (size_t)S * a_bytes;
-    // product form: per epilogue warp two 32-row x 16-column FP32 staging tiles for the T stores
+    // product form: per epilogue warp four 32-row x 16-column FP32 staging tiles for the T stores
     float* s_out = reinterpret_cast<float*>(sB + (size_t)S * b_bytes);
     uint8_t* win = sB + (size_t)S * b_bytes + (p.tout_tma ? kOutStageBytes : 0u);  // window gather: 3 windows
     int* map_s = reinterpret_cast<int*>(win + 3 * (size_t)win1);
@@ -306,13 +307,17 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
                         stop = true;
                         break;
                     }
-                    if (lane == 0) {
+                    if (lane == 0) {  // the stage's G k-blocks: weight blocks and 128-row tiles of x
                         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full0 + 8 * s),
                                      "r"(a_bytes + b_bytes)
                                      : "memory");
-                        const __nv_bfloat16* wsrc = p.w + ((size_t)kb * p.Npad + (size_t)nt * p.BN) * p.BKE;
-                        bulk_g2s(smem_u32(sB + (size_t)s * b_bytes), wsrc, b_bytes, full0 + 8 * s);
-                        tma_tile2d(smem_u32(sA + (size_t)s * a_bytes), &tmap, kb * p.BKE, mt * kBM, full0 + 8 * s);
+                        for (int g = 0; g < p.G; ++g) {
+                            const int kbb = kb * p.G + g;
+                            const __nv_bfloat16* wsrc = p.w + ((size_t)kbb * p.Npad + (size_t)nt * p.BN) * p.BKE;
+                            bulk_g2s(smem_u32(sB + (size_t)s * b_bytes + g * b_sub), wsrc, b_sub, full0 + 8 * s);
+                            tma_tile2d(smem_u32(sA + (size_t)s * a_bytes + g * a_sub), &tmap, kbb * p.BKE, mt * kBM,
+                                       full0 + 8 * s);
+                        }
                     }
                     __syncwarp();
                 }
@@ -592,7 +597,6 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
         const int ew = warp - PW, r = ew * 32 + lane;
         float* wb = s_bias + ew * 256;
         uint32_t tc = 0;
-        uint32_t out_it = 0;  // product form: T chunks stored by this warp (staging tile out_it & 1)
         for (int u = blockIdx.x; u < units; u += gridDim.x, ++tc) {
             const int tile = u / ksplit;
             const int mt = tile / p.n_tiles, nt = tile - mt * p.n_tiles;
@@ -633,33 +637,44 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
                 __syncwarp();
                 if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
             } else if (p.tout && ksplit == 1) {
-                // Per 16-column chunk the warp's 32 accumulator rows go to a staging tile in the
-                // 64-byte swizzle (row r's 16-byte chunk c at position c ^ ((r >> 1) & 3)) and leave
-                // with one TMA tensor store of 32 full 64-byte row segments; two tiles alternate and
-                // lane 0 tracks the bulk groups. Rows past n_rows (up to the tile end) carry values
-                // of rows nothing reads; rows past T's capacity are clipped by the tensor map.
+                // Per 64 columns the warp loads its 32 accumulator rows with up to four TMEM loads and
+                // one wait; each 16-column chunk goes to a staging tile in the 64-byte swizzle (row r's
+                // 16-byte chunk c at position c ^ ((r >> 1) & 3)) and leaves with one TMA tensor store
+                // of 32 full 64-byte row segments (lane 0 issues the group and waits for the previous
+                // group to have read its tiles before they are rewritten). Rows past n_rows (up to the
+                // tile end) carry values of rows nothing reads; rows past T's capacity are clipped by
+                // the tensor map.
                 const int row0 = mt * kBM + ew * 32;
-                for (int c0 = 0; c0 < p.BN; c0 += 16) {
-                    uint32_t v[16];
-                    tmem_ld16(taddr_row + (uint32_t)c0, v);
+                float* grp = s_out + ew * (kOutTilesPerWarp * kOutTileBytes / 4);
+                for (int c0 = 0; c0 < p.BN; c0 += 16 * kOutTilesPerWarp) {
+                    const int nch = min(kOutTilesPerWarp, (p.BN - c0) >> 4);  // warp-uniform
+                    uint32_t v[kOutTilesPerWarp][16];
+#pragma unroll
+                    for (int q = 0; q < kOutTilesPerWarp; ++q)
+                        if (q < nch) tmem_ld16(taddr_row + (uint32_t)(c0 + 16 * q), v[q]);
                     tmem_ld_wait();
-                    const int ng = nt * p.BN + c0;
-                    if (row0 >= n_rows || ng >= p.Ntot) continue;  // warp-uniform
-                    float* tile = s_out + (ew * 2 + (out_it & 1)) * (kOutTileBytes / 4);
-                    if (lane == 0) bulk_wait_read1();  // the store that last read this tile is done
+                    const int ng0 = nt * p.BN + c0;
+                    if (row0 >= n_rows || ng0 >= p.Ntot) continue;  // warp-uniform
+                    const int nst = min(nch, (p.Ntot - ng0) >> 4);   // chunks inside T (Ntot % 16 == 0)
+                    if (lane == 0) bulk_wait_read0();  // the last group has read its tiles
                     __syncwarp();
 #pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        *reinterpret_cast<float4*>(tile + lane * 16 + ((c ^ ((lane >> 1) & 3)) << 2)) =
-                            make_float4(__uint_as_float(v[4 * c]), __uint_as_float(v[4 * c + 1]),
-                                        __uint_as_float(v[4 * c + 2]), __uint_as_float(v[4 * c + 3]));
+                    for (int q = 0; q < kOutTilesPerWarp; ++q) {
+                        if (q >= nst) break;
+                        float* tile = grp + q * (kOutTileBytes / 4);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c)
+                            *reinterpret_cast<float4*>(tile + lane * 16 + ((c ^ ((lane >> 1) & 3)) << 2)) =
+                                make_float4(__uint_as_float(v[q][4 * c]), __uint_as_float(v[q][4 * c + 1]),
+                                            __uint_as_float(v[q][4 * c + 2]), __uint_as_float(v[q][4 * c + 3]));
+                    }
                     fence_proxy_async_shared();
                     __syncwarp();
                     if (lane == 0) {
-                        tma_store_2d(&tmap_t, ng, row0, smem_u32(tile));
+                        for (int q = 0; q < nst; ++q)
+                            tma_store_2d(&tmap_t, ng0 + 16 * q, row0, smem_u32(grp + q * (kOutTileBytes / 4)));
                         bulk_commit();
                     }
-                    ++out_it;
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -748,6 +763,7 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
             // -------------------------------------------------------------- MMA issuer
             const uint32_t idesc = make_idesc(kBM, p.BN);
             const int kk_steps = p.BKE / 16;  // MMAs (K = 16) per k-block
+            const uint32_t sA_u32 = smem_u32(sA), sB_u32 = smem_u32(sB);
             uint32_t tc = 0;
             int s = 0;          // stage of the next k-block
             uint32_t ph = 0;    // its phase parity
@@ -761,18 +777,21 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
                 if (*abort_flag) break;
                 tc_fence_after();
                 for (int kb = kb0; kb < kb1; ++kb) {
-                    mbar_wait(full0 + 8 * s, ph, abort_flag, p.wait_limit);
-                    if (p.gmode == 0) mbar_wait(bfull0 + 8 * s, ph, abort_flag, p.wait_limit);
-                    if (*abort_flag) {
+                    // this thread issues every MMA of the CTA: the loop is kept short (one probe of a
+                    // completed stage, descriptors advanced by adding the 32-byte K steps to their
+                    // address field), else issuing would take longer than the MMAs of a k-block
+                    if (!mbar_wait_ok(full0 + 8 * s, ph, abort_flag, p.wait_limit) ||
+                        (p.gmode == 0 && !mbar_wait_ok(bfull0 + 8 * s, ph, abort_flag, p.wait_limit))) {
                         stop = true;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a0 = smem_u32(sA + (size_t)s * a_bytes), b0 = smem_u32(sB + (size_t)s * b_bytes);
+                    const uint64_t ad = make_sdesc(sA_u32 + (uint32_t)s * a_bytes, p.RB);
+                    const uint64_t bd = make_sdesc(sB_u32 + (uint32_t)s * b_bytes, p.RB);
                     for (int g = 0; g < p.G; ++g)
                         for (int k = 0; k < kk_steps; ++k)
-                            tc_mma(acc, make_sdesc(a0 + g * a_sub + 32 * k, p.RB), make_sdesc(b0 + g * b_sub + 32 * k, p.RB),
-                                   idesc, (kb > kb0 || g > 0 || k > 0) ? 1u : 0u);
+                            tc_mma(acc, ad + ((g * a_sub + 32 * k) >> 4), bd + ((g * b_sub + 32 * k) >> 4), idesc,
+                                   (kb > kb0 || g > 0 || k > 0) ? 1u : 0u);
                     tc_commit(empty0 + 8 * s);
                     if (++s == S) {
                         s = 0;
@@ -1043,8 +1062,20 @@ npvs_status run_gemm(TcParams& p, const TcShape& sh, const npvs_conv_desc& d, co
         win = 3 * (size_t)p.win_rows * sh.RB;
     } else {
         p.stages = tc_stages(sh.BN, sh.RB, p.taps, p.tout_tma ? kOutStageBytes : 0);
+        // dense 128-row tiles: two k-blocks per stage halve the stage hand-offs (each costs a few
+        // hundred cycles of the single MMA-issuing thread), with as many stages as fit (at least 2)
+        if (p.gmode == 2 && sh.KB % 2 == 0 && sh.KB >= 4) {
+            int S2 = 0;
+            for (int S = kMaxStages; S >= 2 && S2 == 0; --S)
+                if (tc_smem_bytes(sh.BN, sh.RB, p.taps, S, 0, 2, p.tout_tma ? kOutStageBytes : 0) <= kMaxSmem) S2 = S;
+            if (S2 >= 2) {
+                p.G = 2;
+                p.KB = sh.KB / 2;  // pipeline stages of one tile
+                p.stages = S2;
+            }
+        }
     }
-    if (d.tune_stages >= (p.gmode == 3 ? 2 : 3) && d.tune_stages < p.stages) p.stages = d.tune_stages;
+    if (d.tune_stages >= (p.gmode == 3 || p.G > 1 ? 2 : 3) && d.tune_stages < p.stages) p.stages = d.tune_stages;
     lag = std::min(lag, p.stages - 1);
     if (lag == 5) lag = 4;  // instantiated lags: 1, 2, 3, 4, 6 (all < stages)
     p.acc_cols = 32;
@@ -1088,8 +1119,10 @@ npvs_status run_gemm(TcParams& p, const TcShape& sh, const npvs_conv_desc& d, co
     }
     const long long tiles_cap = (long long)ceil_div(p.cap_rows, kBM) * sh.n_tiles;
     const int grid = (int)std::min<long long>(tiles_cap * (p.part ? p.KB : 1), kNumSMs);
-    return d.tune_gather_warps == 4 ? launch_tc_lag<4>(lag, p, tm, tm_t, grid, smem, st)
-                                    : launch_tc_lag<8>(lag, p, tm, tm_t, grid, smem, st);
+    // dense TMA tiles (gmode 2) are issued by warp 0 alone: four gather warps leave the epilogue warps
+    // more registers (the block has 288 threads instead of 416)
+    return (d.tune_gather_warps == 4 || p.gmode == 2) ? launch_tc_lag<4>(lag, p, tm, tm_t, grid, smem, st)
+                                                     : launch_tc_lag<8>(lag, p, tm, tm_t, grid, smem, st);
 }
 
 }  // namespace
@@ -1125,7 +1158,11 @@ TcShape tc_shape(int kind, int cin, int cout, int form) {
     s.Kflat = s.taps_eff * cin;
     s.KB = (s.Kflat + s.BKE - 1) / s.BKE;
     s.BN = 0;
-    if (form == 1)  // an exact divisor keeps T free of padding columns
+    // product form: 256-column tiles when the padding costs at most ~6 % of the columns (the widest
+    // MMA per issued instruction, fewer tiles per SM), else the widest exact divisor, which keeps
+    // the weight image free of padding columns (T itself is never padded)
+    const bool pad256 = form == 1 && s.Ntot > 256 && (long long)round_up(s.Ntot, 256) * 100 <= (long long)s.Ntot * 106;
+    if (form == 1 && !pad256)
         for (int bn = 256; bn >= 16; bn -= 16)
             if (s.Ntot % bn == 0) {
                 s.BN = bn;

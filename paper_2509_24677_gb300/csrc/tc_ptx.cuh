@@ -62,6 +62,14 @@ __device__ __forceinline__ void mbar_wait(uint32_t bar, uint32_t parity, volatil
         }
     }
 }
+// mbar_wait for a hot loop: a phase that is already complete costs one probe and no read of the
+// abort flag; false when this CTA has timed out (here or in another warp), checked only after a
+// wait that had to block.
+__device__ __forceinline__ bool mbar_wait_ok(uint32_t bar, uint32_t parity, volatile int* abort_flag, long long limit) {
+    if (limit < kPollBelowCycles ? mbar_test_wait(bar, parity) : mbar_try_wait(bar, parity)) return true;
+    mbar_wait(bar, parity, abort_flag, limit);
+    return *abort_flag == 0;
+}
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
@@ -83,6 +91,8 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* tm, int c0, int 
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // all but the newest bulk group have finished reading their shared-memory source
 __device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+// every bulk group of this thread has finished reading its shared-memory source
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 // every bulk group of this thread has completed (its writes are done)
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {

@@ -271,17 +271,17 @@ __global__ void __launch_bounds__(kWgThreads, 1) wgrad_tc_kernel(const WgParams 
                 tc_fence_after();
                 for (int kb = 0; kb < w.nkb; ++kb, ++it) {
                     const int s = (int)(it % S);
-                    mbar_wait(full0 + 8 * s, (it / S) & 1, abort_flag, p.wait_limit);
-                    if (*abort_flag) {
+                    if (!mbar_wait_ok(full0 + 8 * s, (it / S) & 1, abort_flag, p.wait_limit)) {
                         stop = true;
                         break;
                     }
                     tc_fence_after();
                     const uint32_t a0 = smem_u32(sA + (size_t)s * a_bytes), b0 = smem_u32(sB + (size_t)s * b_bytes);
+                    // descriptors advanced by adding the 2048-byte K steps (16 rows) to their address field
+                    const uint64_t ad = make_sdesc_mn(a0, kAtom, 1024), bd = make_sdesc_mn(b0, kAtom, 1024);
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
-                        tc_mma(acc, make_sdesc_mn(a0 + 2048 * k, kAtom, 1024), make_sdesc_mn(b0 + 2048 * k, kAtom, 1024),
-                               idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                        tc_mma(acc, ad + 128 * k, bd + 128 * k, idesc, (kb > 0 || k > 0) ? 1u : 0u);
                     tc_commit(empty0 + 8 * s);
                 }
                 if (!stop) tc_commit(tfull0 + 8 * buf);
