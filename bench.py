@@ -54,8 +54,9 @@ def parse():
     ap.add_argument("--no-highres", action="store_true", help="skip the 512x512x192 measurement")
     ap.add_argument("--no-paper256", action="store_true",
                     help="skip the 256^3 measurements (d=8, 16, 32, and d=1 without interleave)")
+    ap.add_argument("--no-k3", action="store_true", help="skip the k = 3 stride-2 U-Net frame")
     ap.add_argument("--grid-only", default=None,
-                    choices=["city512", "paper256", "paper256_d1", "paper256_d8", "paper256_d32"],
+                    choices=["city512", "paper256", "paper256_d1", "paper256_d8", "paper256_d32", "city256_k3"],
                     help="measure only this grid workload and print its record (not the headline line)")
     ap.add_argument("--grid-batch", type=int, default=0, help="viewcells of the grid workload (0: its default)")
     ap.add_argument("--grid-capacity", type=float, default=0.0,
@@ -231,13 +232,19 @@ def layer_algorithmic(fp, wl):
         elif l.kind == "up2":
             pairs = n[li]
             n_in, n_out, taps = n[li + 1], n[li], 8
+        elif l.kind == "down3":        # pairs: the existing inputs of each coarse output's 27 taps
+            pairs = int((fp.levels[li - 1].down[:n[li]] >= 0).sum().item())
+            n_in, n_out, taps = n[li - 1], n[li], 27
+        elif l.kind == "up3":          # the same pairs, seen from the fine rows
+            pairs = int((fp.levels[li].up[:n[li]] >= 0).sum().item())
+            n_in, n_out, taps = n[li + 1], n[li], 27
         else:
             pairs = n[li]
             n_in = n_out = n[li]
             taps = 1
         ob = 4 if l.kind == "head1" else b
         byts = n_in * l.cin * b + n_out * l.cout * ob + taps * l.cin * l.cout * b + 4 * taps * n_out
-        if l.kind == "up2":
+        if l.kind in ("up2", "up3"):   # the skip input
             byts += n_out * l.cout * b
         out["conv:" + l.name] = dict(bytes=byts, flops=2 * pairs * l.cin * l.cout)
     W, H, D = wl.W, wl.H, wl.D
@@ -494,6 +501,8 @@ def select_batched_viewcells(dev, wl, scenes, n_pick=64, per_scene=512, lo=0.01,
 def chain_levels_for(P, wl):
     """Chain levels the network allows: 0 (none) and every k whose chained layers are tensor-core
     shapes (cin % 32 == 0, cout % 16 == 0)."""
+    if any(l.kind in ("down3", "up3") for l in wl.layers):
+        return [0]                    # the layer chain runs the 2x2x2 pair only
     n_levels = 1 + sum(1 for l in wl.layers if l.kind == "down2")
     out = [0]
     for k in range(1, n_levels):
@@ -663,6 +672,17 @@ def run_paper256_factor(args, dev, tf_bf16, hbm_gbs, d):
                              "2,001-box city seed 0, 1 viewcell")
 
 
+def run_city256_k3(args, dev, tf_bf16, hbm_gbs):
+    """The headline scene and U-Net (256x256x128, d = 4, 32/64/128/256) with the backbone's k = 3,
+    stride 2, padding 1 down convs (each coarser level the dilated output set) and their transposes
+    in place of the 2x2x2 pair: one viewcell per frame, BF16, every layer its own launch."""
+    boxes = I.city_boxes(0)
+    vcs = I.city_viewcells(0, args.grid_batch or 1)
+    return run_grid_workload(args, dev, tf_bf16, hbm_gbs, I.workload("city256_k3"), boxes, vcs,
+                             "city256_k3: 256x256x128 froxels (s=8), d=4 (128 ch), U-Net 32/64/128/256 with k=3 "
+                             "stride-2 down convs and their transposes, 2,001-box city seed 0")
+
+
 def run_grid_workload(args, dev, tf_bf16, hbm_gbs, wl, boxes, vcs, label, capacity_frac=1.0):
     """Batch of len(vcs) viewcells of one scene through the BF16 frame (autotuned, one graph of
     npvs_forward), then stage and per-layer times from a stage-timed graph of the same frame.
@@ -768,6 +788,8 @@ def run_grid_only(args):
         rec = run_paper256(args, dev, tf_bf16, hbm_gbs)
     elif name == "paper256_d1":
         rec = run_paper256_d1(args, dev, tf_bf16, hbm_gbs)
+    elif name == "city256_k3":
+        rec = run_city256_k3(args, dev, tf_bf16, hbm_gbs)
     else:
         rec = run_paper256_factor(args, dev, tf_bf16, hbm_gbs, int(name.split("_d")[1]))
     print(json.dumps({"grid_only": name, **rec}), flush=True)
@@ -1035,6 +1057,8 @@ def run_ours(args):
             by_d[str(d)] = {"ms_per_frame": r["ms_per_batch"], "peak_device_mb": r["memory_mb"]["peak_device"],
                             "active_coarse_sites": r["active_sites"][0]}
         line["paper256_by_interleave_factor"] = by_d
+    if not args.no_k3:
+        line["city256_k3"] = run_city256_k3(args, dev, tf_bf16, hbm_gbs)
     if not args.no_train:
         del g16, g32, g16t
         line["train"] = run_train(args, dev, flush)

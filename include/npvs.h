@@ -377,7 +377,10 @@ npvs_status npvs_sparse_conv_fwd(const npvs_conv_desc* desc, const void* x, cons
 /* One layer of a network for npvs_forward, in canonical order (a plain SubM3 stack, or a U-Net:
  * stem, per level SubM3 layers and a DOWN2, then per decoder level an UP2 whose output gets the
  * output of the layer just before the matching DOWN2 added after its ReLU, SubM3 layers, and a
- * HEAD1 with d^3 outputs). tune_*: as npvs_conv_desc (0 = defaults). */
+ * HEAD1 with d^3 outputs). A U-Net may use the k = 3 stride-2 pair instead (DOWN3 / UP3 in place
+ * of every DOWN2 / UP2, each coarser level then being the dilated output set of a DOWN3
+ * rulebook); the two pairs cannot be mixed in one network (NPVS_ERR_UNSUPPORTED), and such a
+ * network has no layer chain. tune_*: as npvs_conv_desc (0 = defaults). */
 typedef struct {
     int32_t kind, cin, cout, relu;
     const void* w;     /* device: BF16 packed image (npvs_pack_weights) or F32 [taps][cin][cout] */

@@ -198,18 +198,20 @@ def plain_layers(channels: Sequence[int]) -> List[Layer]:
     return [Layer(f"conv{i}", "subm3", channels[i], channels[i + 1], i < n - 1) for i in range(n)]
 
 
-def unet_layers(cin: int, levels: Sequence[int], cout: int) -> List[Layer]:
+def unet_layers(cin: int, levels: Sequence[int], cout: int, k3: bool = False) -> List[Layer]:
     """Sparse U-Net layer list in canonical order: stem, per level two SubM3 (+ down), then per
-    decoder level an inverse conv and two SubM3, then a 1x1 head."""
+    decoder level an inverse conv and two SubM3, then a 1x1 head. k3: the down convs are k = 3,
+    stride 2, padding 1 (onto the dilated output set) and the up convs their transposes."""
+    dk, uk = ("down3", "up3") if k3 else ("down2", "up2")
     L: List[Layer] = [Layer("stem", "subm3", cin, levels[0], True)]
     nl = len(levels)
     for i in range(nl):
         L.append(Layer(f"enc{i}a", "subm3", levels[i], levels[i], True))
         L.append(Layer(f"enc{i}b", "subm3", levels[i], levels[i], True))
         if i + 1 < nl:
-            L.append(Layer(f"down{i}", "down2", levels[i], levels[i + 1], True))
+            L.append(Layer(f"down{i}", dk, levels[i], levels[i + 1], True))
     for i in range(nl - 2, -1, -1):
-        L.append(Layer(f"up{i}", "up2", levels[i + 1], levels[i], True))
+        L.append(Layer(f"up{i}", uk, levels[i + 1], levels[i], True))
         L.append(Layer(f"dec{i}a", "subm3", levels[i], levels[i], True))
         L.append(Layer(f"dec{i}b", "subm3", levels[i], levels[i], True))
     L.append(Layer("head", "head1", levels[0], cout, False))
@@ -260,6 +262,8 @@ def workload(name: str) -> Workload:
         return Workload(name, 64, 64, 32, 2, 1, 8, tuple(plain_layers([8, 16, 32, 16, 8])))
     if name == "city256":      # 256x256x128 froxels, d=4, occupancy + depth, U-Net 32/64/128/256
         return Workload(name, 256, 256, 128, 4, 2, 8, tuple(unet_layers(128, [32, 64, 128, 256], 64)))
+    if name == "city256_k3":   # city256 with k = 3, stride 2 down convs (dilated levels) and their transposes
+        return Workload(name, 256, 256, 128, 4, 2, 8, tuple(unet_layers(128, [32, 64, 128, 256], 64, k3=True)))
     if name == "city512":      # 512x512x192 froxels, d=8, occupancy + depth, U-Net 64/128/256/512
         return Workload(name, 512, 512, 192, 8, 2, 4, tuple(unet_layers(1024, [64, 128, 256, 512], 512)))
     if name == "paper256":     # the paper's grid: 256^3 froxels, d=16 (4096 ch), stem to ~200 ch, 2 levels

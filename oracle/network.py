@@ -135,11 +135,18 @@ def head1(level: Level, x, W, b):
     return x @ W[0] + b
 
 
-def build_levels(coords, dims, n_levels: int) -> List[Level]:
+def build_levels(coords, dims, n_levels: int, strided3: bool = False) -> List[Level]:
+    """Level 0 from the active coords, then each coarser level: the parents (2x2x2 stride-2 down
+    convs) or, with strided3, the output set of a k = 3, stride 2, padding 1 convolution."""
     L = [Level(coords, dims)]
     for _ in range(n_levels - 1):
-        L.append(L[-1].parent())
+        L.append(L[-1].strided3() if strided3 else L[-1].parent())
     return L
+
+
+def unet_is_k3(layers) -> bool:
+    """Whether a U-Net's down / up convs are the k = 3 stride-2 pair."""
+    return any(l.kind in ("down3", "up3") for l in layers)
 
 
 def forward(layers, weights: Sequence[torch.Tensor], biases: Sequence[torch.Tensor],
@@ -163,7 +170,9 @@ def forward(layers, weights: Sequence[torch.Tensor], biases: Sequence[torch.Tens
         for l in layers:
             a = run(l.name, subm3, levels[0], a)
         return a
-    nl = sum(1 for l in layers if l.kind == "down2") + 1
+    nl = sum(1 for l in layers if l.kind in ("down2", "down3")) + 1
+    k3 = unet_is_k3(layers)
+    dn, upf = (down3, up3) if k3 else (down2, up2)
     a = run("stem", subm3, levels[0], x)
     skips = []
     for i in range(nl):
@@ -171,9 +180,9 @@ def forward(layers, weights: Sequence[torch.Tensor], biases: Sequence[torch.Tens
         a = run(f"enc{i}b", subm3, levels[i], a)
         skips.append(a)
         if i + 1 < nl:
-            a = run(f"down{i}", lambda x_, W, b, i=i: down2(levels[i], levels[i + 1], x_, W, b), a)
+            a = run(f"down{i}", lambda x_, W, b, i=i: dn(levels[i], levels[i + 1], x_, W, b), a)
     for i in range(nl - 2, -1, -1):
-        a = run(f"up{i}", lambda x_, W, b, i=i: up2(levels[i + 1], levels[i], x_, W, b), a)
+        a = run(f"up{i}", lambda x_, W, b, i=i: upf(levels[i + 1], levels[i], x_, W, b), a)
         a = a + skips[i]
         if keep is not None:
             keep[f"up{i}+skip"] = a

@@ -34,6 +34,7 @@ struct FwdPlan {
     std::vector<size_t> act_off;
     size_t el = 2;
     int chain_first = -1, chain_last = -1;  // layers run as one persistent launch (chain_level)
+    bool k3 = false;  // the levels are linked by the k = 3 stride-2 pair (DOWN3 / UP3), not DOWN2 / UP2
 };
 
 npvs_status plan_net(const npvs_net_desc& n, FwdPlan* P) {
@@ -49,16 +50,26 @@ npvs_status plan_net(const npvs_net_desc& n, FwdPlan* P) {
     P->skip_of.assign(n.n_layers, -1);
     std::vector<int> stack;
     int lv = 0, maxlv = 0;
+    bool seen_pair = false;
     for (int i = 0; i < n.n_layers; ++i) {
         const npvs_layer& l = n.layers[i];
-        NPVS_REQUIRE(l.kind >= NPVS_CONV_SUBM3 && l.kind <= NPVS_CONV_HEAD1 && l.w, NPVS_ERR_INVALID_ARG,
+        NPVS_REQUIRE(l.kind >= NPVS_CONV_SUBM3 && l.kind <= NPVS_CONV_UP3 && l.w, NPVS_ERR_INVALID_ARG,
                      "npvs_forward: bad layer");
         const int cin_expected = i == 0 ? n.in_ch * n.d * n.d * n.d : n.layers[i - 1].cout;
         NPVS_REQUIRE(l.cin == cin_expected, NPVS_ERR_INVALID_ARG, "npvs_forward: layer cin differs from the input width");
-        if (l.kind == NPVS_CONV_DOWN2) {
+        const bool down = l.kind == NPVS_CONV_DOWN2 || l.kind == NPVS_CONV_DOWN3;
+        const bool up = l.kind == NPVS_CONV_UP2 || l.kind == NPVS_CONV_UP3;
+        if (down || up) {  // one pair for the whole network: the level sets follow from it
+            const bool k3 = l.kind == NPVS_CONV_DOWN3 || l.kind == NPVS_CONV_UP3;
+            NPVS_REQUIRE(!seen_pair || k3 == P->k3, NPVS_ERR_UNSUPPORTED,
+                         "npvs_forward: the 2x2x2 and the k = 3 stride-2 pairs cannot be mixed");
+            P->k3 = k3;
+            seen_pair = true;
+        }
+        if (down) {
             stack.push_back(i - 1);
             ++lv;
-        } else if (l.kind == NPVS_CONV_UP2) {
+        } else if (up) {
             NPVS_REQUIRE(!stack.empty() && lv > 0, NPVS_ERR_INVALID_ARG, "npvs_forward: up conv without a matching down conv");
             const int src = stack.back();
             stack.pop_back();
@@ -142,7 +153,7 @@ npvs_conv_desc layer_desc(const npvs_net_desc& n, const FwdPlan& P, const std::v
         d.map = l.kind == NPVS_CONV_SUBM3 ? L[li].nbr : nullptr;
         d.n_in = L[li].n_rows;
         d.cap_in = L[li].cap;
-    } else if (l.kind == NPVS_CONV_DOWN2) {
+    } else if (l.kind == NPVS_CONV_DOWN2 || l.kind == NPVS_CONV_DOWN3) {  // the input rows of each output
         d.map = L[li - 1].down;
         d.map2 = L[li - 1].up;
         d.n_in = L[li - 1].n_rows;
@@ -174,9 +185,9 @@ size_t carve(const npvs_net_desc& n, FwdPlan& P, void* base, size_t size, std::v
         v.nbr = ar.take<int32_t>((size_t)v.cap * 27);
         v.down = v.up = nullptr;
     }
-    for (int li = 0; li + 1 < P.n_levels; ++li) {
-        L[li].down = ar.take<int32_t>((size_t)L[li + 1].cap * 8);
-        L[li].up = ar.take<int32_t>((size_t)L[li].cap);
+    for (int li = 0; li + 1 < P.n_levels; ++li) {  // k = 3 pair: 27 taps each way
+        L[li].down = ar.take<int32_t>((size_t)L[li + 1].cap * (P.k3 ? 27 : 8));
+        L[li].up = ar.take<int32_t>((size_t)L[li].cap * (P.k3 ? 27 : 1));
     }
     *feats = ar.take<char>((size_t)L[0].cap * n.in_ch * n.d * n.d * n.d * P.el);
     acts.assign(n.n_layers, nullptr);
@@ -292,7 +303,8 @@ extern "C" npvs_status npvs_forward(const npvs_net_desc* net, const float* boxes
     for (int li = 0; li + 1 < P.n_levels; ++li) {
         npvs_level lv = {L[li].dims, L[li].cap, L[li].coords, L[li].n_rows, L[li].table};
         npvs_level nx = {L[li + 1].dims, L[li + 1].cap, L[li + 1].coords, L[li + 1].n_rows, L[li + 1].table};
-        NPVS_TRY(npvs_build_rulebook(NPVS_RB_DOWN2, &lv, &nx, L[li].down, L[li].up, status, sc, scb, rs));
+        NPVS_TRY(npvs_build_rulebook(P.k3 ? NPVS_RB_DOWN3 : NPVS_RB_DOWN2, &lv, &nx, L[li].down, L[li].up, status, sc,
+                                     scb, rs));
         NPVS_TRY(npvs_build_rulebook(NPVS_RB_SUBM3_TABLE, &nx, nullptr, L[li + 1].nbr, nullptr, status, sc, scb, rs));
     }
     bool joined = !(side.ok && P.n_levels > 1);

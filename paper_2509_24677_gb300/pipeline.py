@@ -18,6 +18,8 @@ from . import _lib as L
 from . import ops
 
 TORCH_DT = {L.F32: torch.float32, L.BF16: torch.bfloat16, L.F64: torch.float64}
+DOWN_KINDS = ("down2", "down3")
+UP_KINDS = ("up2", "up3")
 KIND = {"subm3": L.CONV_SUBM3, "down2": L.CONV_DOWN2, "up2": L.CONV_UP2, "head1": L.CONV_HEAD1,
         "down3": L.CONV_DOWN3, "up3": L.CONV_UP3}
 
@@ -124,11 +126,11 @@ def chain_layer_indices(layers, chain_level: int) -> List[int]:
         return []
     lv, first = 0, None
     for i, l in enumerate(layers):
-        if l.kind == "down2":
+        if l.kind in DOWN_KINDS:
             lv += 1
             if first is None and lv == chain_level:
                 first = i
-        elif l.kind == "up2":
+        elif l.kind in UP_KINDS:
             lv -= 1
             if first is not None and lv == chain_level - 1:
                 return list(range(first, i + 1))
@@ -144,7 +146,10 @@ class FramePipeline:
         self.device = device
         d = wl.d
         self.grid = L.Grid(wl.W, wl.H, wl.D, batch)
-        self.n_levels = 1 + sum(1 for l in net.layers if l.kind == "down2")
+        self.n_levels = 1 + sum(1 for l in net.layers if l.kind in DOWN_KINDS)
+        # k = 3 stride-2 pair: each coarser level is the dilated output set of a DOWN3 rulebook
+        self.k3 = any(l.kind in ("down3", "up3") for l in net.layers)
+        taps = 27 if self.k3 else 8
         i32 = dict(dtype=torch.int32, device=device)
         self.occ = torch.empty(batch * wl.D * wl.H * (wl.W // 32), **i32)
         self.pvs = torch.empty_like(self.occ)
@@ -158,9 +163,8 @@ class FramePipeline:
             X, Y, Z = X // 2, Y // 2, Z // 2
         for li in range(self.n_levels - 1):
             a, b = self.levels[li], self.levels[li + 1]
-            b_down = torch.empty(b.capacity, 8, **i32)
-            a.down = b_down
-            a.up = torch.empty(a.capacity, 1, **i32)
+            a.down = torch.empty(b.capacity, taps, **i32)   # input rows of each coarse output
+            a.up = torch.empty(a.capacity, 27 if self.k3 else 1, **i32)
         act_dt = TORCH_DT[dtype]
         cap0 = self.levels[0].capacity
         self.feats = torch.zeros(cap0, wl.feat_ch, dtype=act_dt, device=device)
@@ -184,9 +188,9 @@ class FramePipeline:
     def _level_of_layers(self):
         lv, out = 0, {}
         for l in self.net.layers:
-            if l.kind == "down2":
+            if l.kind in DOWN_KINDS:
                 lv += 1
-            elif l.kind == "up2":
+            elif l.kind in UP_KINDS:
                 lv -= 1
             out[l.name] = lv
         return out
@@ -210,7 +214,8 @@ class FramePipeline:
                 ops.npvs_build_rulebook(L.RB_SUBM3_TABLE, lv, None, lv.nbr, status=self.status, ws=self.ws)
                 if li + 1 < self.n_levels:
                     nxt = self.levels[li + 1]
-                    ops.npvs_build_rulebook(L.RB_DOWN2, lv, nxt, lv.down, lv.up, status=self.status, ws=self.ws)
+                    ops.npvs_build_rulebook(L.RB_DOWN3 if self.k3 else L.RB_DOWN2, lv, nxt, lv.down, lv.up,
+                                            status=self.status, ws=self.ws)
 
     def _build_descs(self):
         """Descriptors of every layer (fixed buffers), the shared convolution workspace sized for the
@@ -225,13 +230,13 @@ class FramePipeline:
             if l.kind == "subm3":
                 d = ops.conv_desc(L.CONV_SUBM3, self.dtype, l.cin, l.cout, l.relu, lv.nbr, lv.n_rows, lv.capacity,
                                   n_in=lv.n_rows, cap_in=lv.capacity, **common)
-            elif l.kind == "down2":
+            elif l.kind in DOWN_KINDS:   # map: the input rows of each output, map2: the level pair's other map
                 prev = self.levels[li - 1]
-                d = ops.conv_desc(L.CONV_DOWN2, self.dtype, l.cin, l.cout, l.relu, prev.down, lv.n_rows, lv.capacity,
+                d = ops.conv_desc(KIND[l.kind], self.dtype, l.cin, l.cout, l.relu, prev.down, lv.n_rows, lv.capacity,
                                   map2=prev.up, n_in=prev.n_rows, cap_in=prev.capacity, **common)
-            elif l.kind == "up2":
+            elif l.kind in UP_KINDS:
                 nxt = self.levels[li + 1]
-                d = ops.conv_desc(L.CONV_UP2, self.dtype, l.cin, l.cout, l.relu, lv.up, lv.n_rows, lv.capacity,
+                d = ops.conv_desc(KIND[l.kind], self.dtype, l.cin, l.cout, l.relu, lv.up, lv.n_rows, lv.capacity,
                                   map2=lv.down, n_in=nxt.n_rows, cap_in=nxt.capacity, **common)
                 self.skip_of[i] = self.acts[f"enc{li}b"]
             else:
@@ -267,6 +272,8 @@ class FramePipeline:
         "down2": [dict(tune_form=2), dict(tune_form=2, tune_max_split=8), dict(tune_form=1, tune_gather_warps=8),
                   dict(tune_form=1, tune_gather_warps=8, tune_max_split=1)],
         "up2": [dict(tune_form=2), dict(tune_form=1)],
+        "down3": [dict(tune_form=2), dict(tune_form=1), dict(tune_form=1, tune_max_split=1)],
+        "up3": [dict(tune_form=2), dict(tune_form=1), dict(tune_form=1, tune_max_split=1)],
         "head1": [dict()],
     }
 

@@ -28,7 +28,7 @@ import torch
 
 from . import _lib as L
 from . import ops
-from .pipeline import KIND, TORCH_DT, FramePipeline, Net
+from .pipeline import DOWN_KINDS, KIND, TORCH_DT, UP_KINDS, FramePipeline, Net
 
 ALIGN = 64  # elements between parameter tensors in the flat buffers
 
@@ -127,13 +127,13 @@ class Trainer:
         self.dacts: Dict[str, torch.Tensor] = {l.name: torch.zeros(p.acts[l.name].shape, dtype=act_dt, device=device)
                                                for l in self.layers}
         self.u: Dict[int, torch.Tensor] = {i: torch.zeros_like(p.acts[l.name]) for i, l in enumerate(self.layers)
-                                           if l.kind == "up2"}
+                                           if l.kind in UP_KINDS}
         self.skip_grad: Dict[int, str] = {}     # down-conv index -> name of the up-conv whose skip it feeds
         lv_of = p._level_of_layers()
         for i, l in enumerate(self.layers):
-            if l.kind == "down2":
+            if l.kind in DOWN_KINDS:
                 self.skip_grad[i] = next((m.name for m in self.layers
-                                          if m.kind == "up2" and lv_of[m.name] == lv_of[l.name] - 1), None)
+                                          if m.kind in UP_KINDS and lv_of[m.name] == lv_of[l.name] - 1), None)
         self.bwd_ws = ops.conv_workspace(max(ops.npvs_conv_bwd_workspace_bytes(d) for d in p.descs), device)
         self.loss_dtype = L.F64 if dtype == L.F64 else L.F32
         ldt = TORCH_DT[self.loss_dtype]
@@ -214,7 +214,7 @@ class Trainer:
             desc = p.descs[i]
             x = self._input_of(i)
             y = p.acts[l.name]
-            if l.kind == "up2":      # recompute the up-conv's own output (before the skip) for its ReLU mask
+            if l.kind in UP_KINDS:   # recompute the up-conv's own output (before the skip) for its ReLU mask
                 ops.npvs_sparse_conv_fwd(desc, x, W[i], self.params.b[i], None, self.u[i])
                 y = self.u[i]
             dx = None if i == 0 else self.dacts[self.layers[i - 1].name]

@@ -90,12 +90,12 @@ def check_frame(wl, which, dt, tune=False, chain_level=0):
         assert popcount(occ_all[b] ^ G[0]) == 0       # froxelization bit-exact per element
     for i, l in enumerate(wl.layers):
         rows, nr = nf.layer_output(i)
-        n_b = [(keep[l.name + "+skip"] if l.kind == "up2" else keep[l.name]).shape[0] for *_, keep in refs]
+        n_b = [(keep[l.name + "+skip"] if l.kind in ("up2", "up3") else keep[l.name]).shape[0] for *_, keep in refs]
         assert int(nr.item()) == sum(n_b), l.name
         got = rows[:sum(n_b)].float().cpu().numpy()
         start = 0
         for b, (*_, keep) in enumerate(refs):
-            ref = (keep[l.name + "+skip"] if l.kind == "up2" else keep[l.name]).numpy()
+            ref = (keep[l.name + "+skip"] if l.kind in ("up2", "up3") else keep[l.name]).numpy()
             err = normwise(got[start:start + n_b[b]], ref)
             assert err <= tol, (l.name, b, err)
             start += n_b[b]

@@ -37,7 +37,8 @@ def frames(name, dtype, batch, capacity_frac=1.0, tune=False):
 
 @pytest.mark.parametrize("name,dt,batch,frac,tune", [("plain64", "f32", 1, 1.0, False), ("plain64", "bf16", 2, 1.0, False),
                                                     ("city256", "bf16", 2, 0.5, True), ("city256", "f32", 1, 1.0, False),
-                                                    ("nointerleave64", "bf16", 2, 0.2, True)])
+                                                    ("nointerleave64", "bf16", 2, 0.2, True),
+                                                    ("city256_k3", "bf16", 2, 1.0, True), ("city256_k3", "f32", 1, 1.0, False)])
 def test_native_forward_equals_entry_point_sequence(name, dt, batch, frac, tune):
     L, ops, P = lib()
     wl, fp, nf = frames(name, L.F32 if dt == "f32" else L.BF16, batch, frac, tune)

@@ -419,8 +419,9 @@ def oracle_frame(wl, boxes, vc, ws, bs, keep):
     cam = ocam.frustum(vc, wl.D)
     G = ofx.froxelize(cam, boxes, wl.W, wl.H, wl.D, wl.supersample)[None]
     coords, feats, _ = oil.interleave(G, wl.W, wl.d, wl.in_ch)
-    n_levels = 1 + sum(1 for l in wl.layers if l.kind == "down2")
-    levels = onet.build_levels(coords, (1, wl.D // wl.d, wl.H // wl.d, wl.W // wl.d), n_levels)
+    n_levels = 1 + sum(1 for l in wl.layers if l.kind in ("down2", "down3"))
+    levels = onet.build_levels(coords, (1, wl.D // wl.d, wl.H // wl.d, wl.W // wl.d), n_levels,
+                               strided3=onet.unet_is_k3(wl.layers))
     W_, B_ = onet.to_torch_params(ws, bs)
     with torch.no_grad():
         logits = onet.forward(list(wl.layers), W_, B_, levels, torch.tensor(feats), keep=keep).numpy()
@@ -446,7 +447,8 @@ def gpu_frame(wl, boxes, vc, ws, bs, dtype, tune=False):
                                      ("city256", "bf16-tuned"), ("paper64", "bf16"), ("paper64", "f32"),
                                      ("paper64", "bf16-tuned"), ("nointerleave64", "bf16"), ("nointerleave64", "f32"),
                                      ("nointerleave64", "bf16-tuned"), ("paper64_d8", "bf16"), ("paper64_d8", "f32"),
-                                     ("paper64_d8", "bf16-tuned"), ("paper64_d32", "bf16"), ("paper64_d32", "f32")])
+                                     ("paper64_d8", "bf16-tuned"), ("paper64_d32", "bf16"), ("paper64_d32", "f32"),
+                                     ("city256_k3", "bf16"), ("city256_k3", "f32"), ("city256_k3", "bf16-tuned")])
 def test_frame_parity(name, dt):
     L, ops, P = lib()
     wl = I.workload(name)
@@ -466,7 +468,7 @@ def test_frame_parity(name, dt):
     lv_of = fp._level_of_layers()
     for l in wl.layers:
         n = int(fp.levels[lv_of[l.name]].n_rows.item())
-        ref = keep[l.name + "+skip"] if l.kind == "up2" else keep[l.name]   # skip add is fused
+        ref = keep[l.name + "+skip"] if l.kind in ("up2", "up3") else keep[l.name]   # skip add is fused
         err = normwise(fp.acts[l.name][:n].float().cpu().numpy(), ref.numpy())
         assert err <= tol, (l.name, err)
     # thresholded PVS: disagreements are allowed only at ties, i.e. froxels whose oracle logit is

@@ -225,7 +225,8 @@ def test_strided3_rulebook_oracle_by_brute_force():
     torch.testing.assert_close(yu, N.up3(coarse, fine, z, Wu, b[:cin]), rtol=1e-12, atol=1e-12)
 
 
-def test_unet_wiring_equals_dense_straight_line_composition():
+@pytest.mark.parametrize("strided", [False, True])
+def test_unet_wiring_equals_dense_straight_line_composition(strided):
     """Pin of the U-Net composition in `forward` (Sec. 3.3 f_theta on the interleaved grid; the
     U-Net reading: stem, per level two SubM3 then a stride-2 down conv, per decoder level the
     transposed up conv with ReLU, the encoder level's output added after that ReLU, two SubM3, a
@@ -234,22 +235,26 @@ def test_unet_wiring_equals_dense_straight_line_composition():
     active mask, the level masks from max-pooling the level-0 indicator (not from Level.parent),
     and the skip wiring as straight-line code. Every layer output kept by `forward` must equal
     the dense one at the active sites. A skip taken one layer early, a level pairing off by one
-    or a ReLU on the head would fail here."""
+    or a ReLU on the head would fail here. strided: the same with k = 3, stride 2, padding 1 down convs
+    (dense conv3d, levels from 3x3x3 max-pooling with stride 2 and padding 1) and their transposes
+    (conv_transpose3d with output padding 1)."""
     rng = np.random.default_rng(11)
     dims = (2, 8, 8, 8)
     lv0, m = random_level(rng, dims, 0.3)
-    layers = I.unet_layers(5, [4, 6, 8], 8)
+    layers = I.unet_layers(5, [4, 6, 8], 8, k3=strided)
     ws, bs = I.kaiming_uniform(layers, seed=3, bias_scale=0.2)
     W, B = N.to_torch_params(ws, bs)
     x = torch.tensor(rng.normal(size=(lv0.n, 5)))
-    levels = N.build_levels(lv0.coords.numpy(), dims, 3)
+    levels = N.build_levels(lv0.coords.numpy(), dims, 3, strided3=strided)
     keep = {}
     out = N.forward(layers, W, B, levels, x, keep=keep)
 
     P = {l.name: (W[i], B[i]) for i, l in enumerate(layers)}
     m0 = torch.tensor(m, dtype=torch.float64).unsqueeze(1)                  # B, 1, D, H, W
-    m1 = F.max_pool3d(m0, kernel_size=2, stride=2)
-    m2 = F.max_pool3d(m1, kernel_size=2, stride=2)
+    pool = (lambda a: F.max_pool3d(a, kernel_size=3, stride=2, padding=1)) if strided else \
+        (lambda a: F.max_pool3d(a, kernel_size=2, stride=2))
+    m1 = pool(m0)
+    m2 = pool(m1)
 
     def k3(name):
         w, b = P[name]
@@ -260,15 +265,19 @@ def test_unet_wiring_equals_dense_straight_line_composition():
         y = F.conv3d(a, w, b, padding=1)
         return (torch.relu(y) if relu else y) * mask
 
+    kk = 3 if strided else 2
+    pad = dict(padding=1) if strided else {}
+
     def down(name, a, mask):
         w, b = P[name]
-        wt = w.reshape(2, 2, 2, w.shape[1], w.shape[2]).permute(4, 3, 0, 1, 2)
-        return torch.relu(F.conv3d(a, wt, b, stride=2)) * mask
+        wt = w.reshape(kk, kk, kk, w.shape[1], w.shape[2]).permute(4, 3, 0, 1, 2)
+        return torch.relu(F.conv3d(a, wt, b, stride=2, **pad)) * mask
 
     def up(name, a, mask):
         w, b = P[name]
-        wt = w.reshape(2, 2, 2, w.shape[1], w.shape[2]).permute(3, 4, 0, 1, 2)
-        return torch.relu(F.conv_transpose3d(a, wt, b, stride=2)) * mask
+        wt = w.reshape(kk, kk, kk, w.shape[1], w.shape[2]).permute(3, 4, 0, 1, 2)
+        extra = dict(padding=1, output_padding=1) if strided else {}
+        return torch.relu(F.conv_transpose3d(a, wt, b, stride=2, **extra)) * mask
 
     x0 = dense_of(lv0, x)
     D = {}
