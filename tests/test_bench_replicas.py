@@ -68,8 +68,8 @@ def test_tuned_labels_and_traffic_selection():
     assert bench.tuned_label(win) == "window-nosplit"
     assert bench.tuned_label(win3) == "window3"
     assert bench.tuned_label(gat) == "gather-4w"
-    cfg = {"product": prod, "window3": win3, "window3-nosplit": dict(win3, tune_max_split=1),
-           "gather": {"tune_form": 1}}
+    cfg = {"product": prod, "product-split": {"tune_form": 2, "tune_max_split": 8}, "window3": win3,
+           "window3-nosplit": dict(win3, tune_max_split=1), "gather": {"tune_form": 1}}
     tuned = {k: (cfg[v], 1.0) for k, v in bench.FRAME_DRAM["forms"].items()}
     assert bench.frame_traffic(tuned, 1) == (bench.FRAME_DRAM["dram_bytes"], bench.FRAME_DRAM["algorithmic_bytes"])
     assert bench.frame_traffic(tuned, 1, True) == (bench.FRAME_DRAM["conv_dram_bytes"],
@@ -77,6 +77,10 @@ def test_tuned_labels_and_traffic_selection():
     assert bench.frame_traffic(tuned, 0) == (None, None) and bench.frame_traffic(tuned, 2) == (None, None)
     other = dict(tuned, stem=(win3, 1.0))
     assert bench.frame_traffic(other, 1) == (None, None)
+    # the shipped headline configuration is the one the traffic was measured with
+    import json
+    shipped = {k: (v, 1.0) for k, v in json.load(open(bench.TUNED_HEADLINE)).items()}
+    assert bench.frame_traffic(shipped, 1) == (bench.FRAME_DRAM["dram_bytes"], bench.FRAME_DRAM["algorithmic_bytes"])
 
 
 def test_step_quantiles_nearest_rank():
