@@ -1237,6 +1237,10 @@ npvs_status conv_tc_fwd(const npvs_conv_desc& d, const void* x, const void* w, c
         // k-split only when asked for explicitly: the unsplit product tiles are what the layer chain
         // reproduces bit for bit
         p.tout_split = d.tune_form == 2 && d.tune_max_split > 1;
+        if (p.tout_split) {  // the split-K partial tiles and counters (the workspace's first region)
+            p.part = part;
+            p.counters = counters;
+        }
         p.T = T;
         // TMA stores need 16-byte rows and addresses (the arena aligns T to 256 bytes)
         p.tout_tma = sh.Ntot % 16 == 0 && (reinterpret_cast<uintptr_t>(T) & 255) == 0;
