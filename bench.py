@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--frames-per-step", type=int, default=0,
                     help="frames timed per step (0: enough for about 1 s of timed frames over all steps)")
     ap.add_argument("--no-train", action="store_true", help="skip the training-step measurement")
+    ap.add_argument("--no-quality", action="store_true",
+                    help="skip the 2,000-step training run and its held-out missing-geometry rate")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-viewcell batched measurement")
     ap.add_argument("--no-highres", action="store_true", help="skip the 512x512x192 measurement")
     ap.add_argument("--no-paper256", action="store_true",
@@ -412,6 +414,21 @@ def run_reference(args):
             "e2e": {"value": round(fps, 5), "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": round(time.perf_counter() - t0, 1)}
     print(json.dumps(line), flush=True)
+
+
+def run_quality(dev):
+    """The training run of paper_2509_24677_gb300.train_eval with its defaults (4 cities x 64 training
+    and 16 held-out street viewcells of half-size 1, ground truth from 256 viewpoints per cell by GPU
+    ray casting, 2,000 steps of batch 8, BF16, Adam lr 1e-3), then the held-out cells through
+    npvs_forward: FNR = missed ground-truth froxels / ground-truth froxels (the paper's missing
+    geometry), FPR = extra froxels / ground-truth froxels."""
+    from paper_2509_24677_gb300 import train_eval
+    t0 = time.perf_counter()
+    out = train_eval.run(train_eval.parse_args([]), dev)
+    out["seconds"] = round(time.perf_counter() - t0, 1)
+    out["what"] = ("2,000 BF16 training steps on synthetic city viewcells (random-init weights), then FNR / FPR "
+                   "of the thresholded PVS on 64 held-out cells against GPU ray-cast ground truth")
+    return out
 
 
 def run_train(args, dev, flush):
@@ -1071,6 +1088,8 @@ def run_ours(args):
     if not args.no_train:
         del g16, g32, g16t
         line["train"] = run_train(args, dev, flush)
+        if not args.no_quality:
+            line["train_quality"] = run_quality(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t0 = time.perf_counter()
         cms, cstages, G, logits, coords = cpu_oracle_frame(0)

@@ -40,7 +40,7 @@ def _popcount(t: torch.Tensor) -> int:
     return int(table[v.long()].sum().item())
 
 
-def main(argv=None):
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--batch", type=int, default=8)
@@ -54,8 +54,11 @@ def main(argv=None):
     ap.add_argument("--log-every", type=int, default=100)
     ap.add_argument("--save", default=None, help="write a checkpoint here after the last step")
     ap.add_argument("--resume", default=None, help="continue from a checkpoint written by --save")
-    a = ap.parse_args(argv)
-    dev = "cuda"
+    return ap.parse_args(argv)
+
+
+def run(a, dev="cuda") -> dict:
+    """Builds the data, trains, evaluates the held-out cells; returns the summary record."""
     wl = I.workload("city256")
     t0 = time.perf_counter()
     scenes = {s: I.city_boxes(s) for s in range(4)}
@@ -156,7 +159,11 @@ def main(argv=None):
            "loss_curve": losses, "eval": {"FNR": round(fn / max(gtp, 1), 5), "FPR": round(fp / max(gtp, 1), 5),
                                           "GTP": gtp, "G_froxels": occ,
                                           "G_over_GT": round(occ / max(gtp, 1), 3)}}
-    print(json.dumps(out), flush=True)
+    return out
+
+
+def main(argv=None):
+    print(json.dumps(run(parse_args(argv))), flush=True)
 
 
 if __name__ == "__main__":
