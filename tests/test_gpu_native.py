@@ -186,3 +186,44 @@ def test_chain_level_argument_errors():
         P.NativeFrame(wl, net, 1, L.BF16, max_boxes=10, chain_level=4)
     with pytest.raises((L.NpvsError, ValueError)):
         P.NativeFrame(wl, net, 1, L.F32, max_boxes=10, chain_level=1)
+
+
+@pytest.mark.parametrize("chain_level,dtype", [(0, "bf16"), (1, "bf16"), (0, "f32")])
+def test_empty_frame_and_a_frame_behind_the_camera(chain_level, dtype):
+    """Frames with no active site: no boxes at all, and one box behind the camera, in a batch with a
+    normal viewcell. Every launch of the frame (the layer chain included) runs on zero rows for the
+    empty elements; their occupancy and PVS are all zero, the normal element equals the same frame
+    run alone, and no status is raised."""
+    L, ops, P = lib()
+    wl = I.workload("city256")
+    dt = L.BF16 if dtype == "bf16" else L.F32
+    ws, bs = I.kaiming_uniform(wl.layers, seed=0, bias_scale=0.05)
+    net = P.Net(wl.layers, ws, bs, DEV)
+    vc_city = I.city_viewcells(0, 1)[0]
+    city = I.city_boxes(0)
+    behind = np.array([[-5, -5, -30, 5, 5, -10]], np.float32)
+    vc0 = I.Viewcell(centre=(0.0, 0.0, 0.0), half=0.5, yaw=0.0)
+    words = wl.D * wl.H * (wl.W // 32)
+
+    def run(scenes, vcs):
+        boxes = np.concatenate(scenes).astype(np.float32) if sum(len(s) for s in scenes) else np.zeros((1, 6), np.float32)
+        bx = torch.from_numpy(boxes).to(DEV)
+        off = torch.tensor(np.cumsum([0] + [len(s) for s in scenes]), dtype=torch.int32, device=DEV)
+        cams = ops.cameras_to_device([ops.npvs_camera_setup(v, wl.D) for v in vcs])
+        nf = P.NativeFrame(wl, net, len(vcs), dt, max_boxes=max(1, len(boxes)), chain_level=chain_level)
+        nf.run(bx, off, int(off[-1].item()), cams)
+        assert ops.npvs_check_status(nf.status) == 0
+        return nf
+
+    empty = np.zeros((0, 6), np.float32)
+    nf = run([empty], [vc0])
+    assert int(nf.occ.count_nonzero().item()) == 0 and int(nf.pvs.count_nonzero().item()) == 0
+    nf = run([behind, city, empty], [vc0, vc_city, vc0])
+    occ, pvs = nf.occ.view(3, words), nf.pvs.view(3, words)
+    for b in (0, 2):
+        assert int(occ[b].count_nonzero().item()) == 0 and int(pvs[b].count_nonzero().item()) == 0
+    alone = run([city], [vc_city])
+    assert torch.equal(occ[1], alone.occ.view(words))
+    assert int(pvs[1].count_nonzero().item()) > 0
+    # the batch's layers see the same rows for the one non-empty element, so its PVS is the same
+    assert torch.equal(pvs[1], alone.pvs.view(words))
