@@ -428,6 +428,9 @@ def run_quality(dev):
     out["seconds"] = round(time.perf_counter() - t0, 1)
     out["what"] = ("2,000 BF16 training steps on synthetic city viewcells (random-init weights), then FNR / FPR "
                    "of the thresholded PVS on 64 held-out cells against GPU ray-cast ground truth")
+    out["ground_truth"] = ("npvs_gt_raycast (binary32), bit-exact against the oracle's binary32 mirror of the same "
+                           "ray cast (tests/test_gpu_train.py); the mirror agrees with the oracle's binary64 ray cast "
+                           "up to ties at face edges")
     return out
 
 
