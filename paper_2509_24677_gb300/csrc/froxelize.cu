@@ -6,10 +6,14 @@
 // pixels (the face clipped against half the near distance and projected, two sub-pixels of margin:
 // the float error of the projection is an order of magnitude smaller) and the froxel columns that
 // rectangle touches; a prefix sum over the per-face column counts gives a flat list of
-// (face, column) items; each item casts the rays of its column that lie in the face's rectangle
+// (face, column) items; each item tests the rays of its column that lie in the face's rectangle
 // against its one face (rays outside it cannot hit the face). Every floating-point step of the ray
 // test is an explicit round-to-nearest binary32 intrinsic in a fixed order, so the resulting
-// bits do not depend on how the work is split. A hit sets its bit with atomicOr.
+// bits do not depend on how the work is split. An item whose rays all miss the face, or all hit it
+// inside one slice, is decided from bounds on those same rounded values without casting its rays;
+// the other items' rays are cast one by one. A hit sets its bit with atomicOr.
+#include <climits>
+
 #include "common.cuh"
 
 namespace npvs {
@@ -33,11 +37,18 @@ __device__ __forceinline__ int batch_of_box(const int32_t* off, int B, int j) {
     return lo;
 }
 
+// One thread per face; threads f < sW + sH also write the normalised pixel centre f of the
+// supersampled raster, n = (2a + 1 - S) / S in one binary32 division: xs[a] for a < sW, then ys[b].
 __global__ void face_setup_kernel(const float* __restrict__ boxes, const int32_t* __restrict__ box_off,
                                   int n_boxes, const npvs_camera* __restrict__ cams, npvs_grid g, int s,
-                                  FaceRec* __restrict__ faces, int* __restrict__ counts) {
+                                  FaceRec* __restrict__ faces, int* __restrict__ counts, float* __restrict__ xs) {
     pdl_begin();
     int f = blockIdx.x * blockDim.x + threadIdx.x;
+    {
+        const int sW = s * g.W, sH = s * g.H;
+        if (f < sW) xs[f] = __fdiv_rn((float)(2 * f + 1 - sW), (float)sW);
+        else if (f < sW + sH) xs[f] = __fdiv_rn((float)(2 * (f - sW) + 1 - sH), (float)sH);
+    }
     if (f >= n_boxes * 6) return;
     int j = f / 6, fl = f % 6, axis = fl >> 1, side = fl & 1;
     FaceRec rec;
@@ -134,14 +145,74 @@ __global__ void chunk_scan_kernel(const int* __restrict__ counts, long long* __r
 }
 
 __global__ void chunk_add_kernel(long long* __restrict__ offs, int n, const int* __restrict__ chunk_off,
-                                 const int* __restrict__ counts, long long* __restrict__ total) {
+                                 const int* __restrict__ counts, long long* __restrict__ total,
+                                 unsigned long long* __restrict__ work) {
     pdl_begin();
     int i = blockIdx.x * kScanChunk + threadIdx.x;
+    if (i == 0) *work = 0ull;  // the item kernel's work counter
     if (i < n) {
         long long o = offs[i] + chunk_off[blockIdx.x];
         offs[i] = o;
         if (i == n - 1) *total = o + counts[i];
     }
+}
+
+// Exclusive scan of up to kSmallScanMax face counts into 64-bit offsets by one block, in tiles of
+// four counts per thread (coalesced 16-byte loads, a running carry between tiles), and the total.
+// Thread 0 also clears the item kernel's work counter.
+constexpr int kSmallScanThreads = 1024;
+constexpr int kSmallScanMax = 32 * kSmallScanThreads;
+
+__global__ void __launch_bounds__(kSmallScanThreads) face_scan_small_kernel(const int* __restrict__ counts,
+                                                                          long long* __restrict__ offs, int n,
+                                                                          long long* __restrict__ total,
+                                                                          unsigned long long* __restrict__ work) {
+    pdl_begin();
+    __shared__ long long sw[33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) *work = 0ull;
+    long long carry = 0;
+    for (int t0 = 0; t0 < n; t0 += 4 * (int)blockDim.x) {
+        const int i0 = t0 + 4 * (int)threadIdx.x;
+        int c[4];
+        if (i0 + 3 < n) {  // counts is 16-byte aligned and i0 a multiple of 4
+            const int4 v = *reinterpret_cast<const int4*>(counts + i0);
+            c[0] = v.x; c[1] = v.y; c[2] = v.z; c[3] = v.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) c[j] = i0 + j < n ? counts[i0 + j] : 0;
+        }
+        const long long sum = (long long)c[0] + c[1] + c[2] + c[3];
+        long long incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) sw[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const long long w = lane < nw ? sw[lane] : 0;
+            long long wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long t = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += t;
+            }
+            if (lane < nw) sw[lane] = wi - w;
+            if (lane == 31) sw[32] = wi;
+        }
+        __syncthreads();
+        long long run = carry + sw[warp] + incl - sum;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (i0 + j < n) offs[i0 + j] = run;
+            run += c[j];
+        }
+        carry += sw[32];
+        __syncthreads();  // sw is rewritten by the next tile
+    }
+    if (threadIdx.x == 0) *total = carry;
 }
 
 // Slice of t given z[0] <= t < z[D]: a guess from the exponential spacing of the slice table
@@ -169,38 +240,222 @@ __device__ __forceinline__ int slice_of(const float* __restrict__ z, int D, floa
     return lo;
 }
 
-// Normalised pixel centres n = (2a + 1 - S) / S of the supersampled raster, one binary32 division
-// each: xs[a] for a < sW, then ys[b] for b < sH.
-__global__ void __launch_bounds__(256) raster_centres_kernel(int sW, int sH, float* __restrict__ xs) {
-    pdl_begin();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < sW) xs[i] = __fdiv_rn((float)(2 * i + 1 - sW), (float)sW);
-    else if (i < sW + sH) xs[i] = __fdiv_rn((float)(2 * (i - sW) + 1 - sH), (float)sH);
+// The camera's components along a face's axis (ax) and its two other axes (j1 = ax + 1, j2 = ax + 2,
+// mod 3).
+struct AxisFrame {
+    float o_ax, o1, o2, f_ax, f1, f2, r_ax, r1, r2, u_ax, u1, u2;
+};
+
+__device__ __forceinline__ AxisFrame axis_frame(const npvs_camera& c, int ax) {
+    const int j1 = ax == 2 ? 0 : ax + 1, j2 = ax == 0 ? 2 : ax - 1;
+    AxisFrame A;
+    A.o_ax = c.origin[ax]; A.o1 = c.origin[j1]; A.o2 = c.origin[j2];
+    A.f_ax = c.fwd[ax];    A.f1 = c.fwd[j1];    A.f2 = c.fwd[j2];
+    A.r_ax = c.right[ax];  A.r1 = c.right[j1];  A.r2 = c.right[j2];
+    A.u_ax = c.up[ax];     A.u1 = c.up[j1];     A.u2 = c.up[j2];
+    return A;
+}
+
+// The rays of froxel column (x, y) that lie in the face's pixel rectangle: sub-columns i0..i1 of
+// the column and supersampled rows b0..b1 (inclusive; never empty for an item of the face).
+struct ColumnSpan {
+    int i0, i1, b0, b1;
+};
+
+__device__ __forceinline__ ColumnSpan column_span(const FaceRec& fr, int x, int y, int s) {
+    ColumnSpan sp;
+    sp.i0 = max(fr.sa0 - x * s, 0);
+    sp.i1 = min(fr.sa1 - x * s, s - 1);
+    sp.b0 = max(y * s, fr.sb0);
+    sp.b1 = min(fr.sb1, y * s + s - 1);
+    return sp;
+}
+
+// Slice constants of one camera: the table, its ends and the exponential-spacing guess.
+struct SliceTable {
+    const float* z;
+    int D;
+    float z0, zD, lz0, kscale;
+};
+
+__device__ __forceinline__ SliceTable slice_table(const npvs_camera& c, int D) {
+    SliceTable T;
+    T.z = c.slices;
+    T.D = D;
+    T.z0 = T.z[0];
+    T.zD = T.z[D];
+    T.lz0 = __log2f(T.z0);
+    T.kscale = (float)D / (__log2f(T.zD) - T.lz0);
+    return T;
+}
+
+// Bounds of one direction component over the rays of a span. Every rounded operation of
+// ray_face_slice is monotone in each input (round-to-nearest is monotone; sx and sy grow with the
+// pixel index since tan > 0), so the component's extremes over the span come from its end
+// sub-columns (sxa, sxb) and end rows (sya, syb), combined by the same rounded addition.
+__device__ __forceinline__ void dir_bounds(float f, float r, float u, float sxa, float sxb, float sya, float syb,
+                                           float& lo, float& hi) {
+    const float ca = __fadd_rn(f, __fmul_rn(sxa, r)), cb = __fadd_rn(f, __fmul_rn(sxb, r));
+    const float ua = __fmul_rn(sya, u), ub = __fmul_rn(syb, u);
+    lo = __fadd_rn(fminf(ca, cb), fminf(ua, ub));
+    hi = __fadd_rn(fmaxf(ca, cb), fmaxf(ua, ub));
+}
+
+// Bounds of h = o + t d over t in [tlo, thi] (tlo > 0) and d in [dlo, dhi]: fl(t d) grows with d for
+// t > 0 and is monotone in t for fixed d, so its extremes are products of the interval ends.
+__device__ __forceinline__ void hit_bounds(float o, float tlo, float thi, float dlo, float dhi, float& lo,
+                                           float& hi) {
+    lo = __fadd_rn(o, fminf(__fmul_rn(tlo, dlo), __fmul_rn(thi, dlo)));
+    hi = __fadd_rn(o, fmaxf(__fmul_rn(tlo, dhi), __fmul_rn(thi, dhi)));
+}
+
+__device__ __forceinline__ bool finite4(float a, float b, float c, float d) {
+    return isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d);
+}
+
+// Decides a span of rays against a face from interval bounds of ray_face_slice's intermediate values
+// (dir_bounds, hit_bounds and the monotone division): 0 when no ray of the span can hit the face, 1
+// when every ray hits it inside one slice (*k), 2 when the bounds do not decide. The bounds hold
+// every ray's exact binary32 values, so 0 and 1 give the same bits as testing the rays one by one;
+// any non-finite bound, or z_0 <= 0, gives 2.
+__device__ __forceinline__ int classify_span(const FaceRec& fr, const AxisFrame& A, float num, float tanh_,
+                                             const ColumnSpan& sp, int x, int s, const float* __restrict__ xs,
+                                             const float* __restrict__ ys, const SliceTable& T, int* k) {
+    if (!(T.z0 > 0.0f)) return 2;
+    const float sxa = __fmul_rn(xs[x * s + sp.i0], tanh_), sxb = __fmul_rn(xs[x * s + sp.i1], tanh_);
+    const float sya = __fmul_rn(ys[sp.b0], tanh_), syb = __fmul_rn(ys[sp.b1], tanh_);
+    float dlo, dhi;
+    dir_bounds(A.f_ax, A.r_ax, A.u_ax, sxa, sxb, sya, syb, dlo, dhi);
+    if (!finite4(dlo, dhi, num, 0.0f) || !(dlo > 0.0f || dhi < 0.0f)) return 2;
+    const float ta = __fdiv_rn(num, dlo), tb = __fdiv_rn(num, dhi);
+    const float tlo = fminf(ta, tb), thi = fmaxf(ta, tb);
+    if (thi < T.z0 || tlo >= T.zD) return 0;
+    if (!(tlo >= T.z0 && thi < T.zD)) return 2;
+    float e1lo, e1hi, e2lo, e2hi;
+    dir_bounds(A.f1, A.r1, A.u1, sxa, sxb, sya, syb, e1lo, e1hi);
+    dir_bounds(A.f2, A.r2, A.u2, sxa, sxb, sya, syb, e2lo, e2hi);
+    if (!finite4(e1lo, e1hi, e2lo, e2hi)) return 2;
+    float h1lo, h1hi, h2lo, h2hi;
+    hit_bounds(A.o1, tlo, thi, e1lo, e1hi, h1lo, h1hi);
+    hit_bounds(A.o2, tlo, thi, e2lo, e2hi, h2lo, h2hi);
+    if (h1hi < fr.lo1 || h1lo > fr.hi1 || h2hi < fr.lo2 || h2lo > fr.hi2) return 0;
+    if (!(h1lo >= fr.lo1 && h1hi <= fr.hi1 && h2lo >= fr.lo2 && h2hi <= fr.hi2)) return 2;
+    const int kk = slice_guess(T.z, T.D, tlo, T.lz0, T.kscale);  // slices grow with t
+    if (!(thi < T.z[kk + 1])) return 2;
+    *k = kk;
+    return 1;
+}
+
+// Casts the rays of one item (face lo, global item index item) one by one and sets (TEST: tests)
+// the slices they hit. Every operation is rounded to nearest in binary32 in the order of the per-ray
+// definition: direction component i = (f_i + (n_x tan) r_i) + (n_y tan) u_i, t = (P - o_ax) / dir_ax,
+// a hit iff z_0 <= t < z_D and o_j + t dir_j lies in the face's closed rectangle for both other axes
+// j. The sub-column parts f_i + (n_x tan) r_i are computed once per call; the call takes rows
+// q, q + nq, q + 2 nq, ... of the item's span (several threads share an item's rays).
+template <int SS, bool TEST>
+__device__ __forceinline__ void cast_item_rays(const FaceRec* __restrict__ faces, const long long* __restrict__ offs,
+                                               int lo, long long item, int q, int nq,
+                                               const npvs_camera* __restrict__ cams,
+                                               const npvs_grid& g, int s, const float* __restrict__ xs,
+                                               const float* __restrict__ ys, uint32_t* __restrict__ bits,
+                                               const uint32_t* __restrict__ test_bits, uint8_t* visible) {
+    constexpr int CAP = SS ? SS : 16;
+    if (TEST && *(volatile const uint8_t*)(visible + lo / 6)) return;  // box already kept
+    const int WW = g.W >> 5;
+    const FaceRec fr = faces[lo];
+    const int local = (int)(item - offs[lo]);
+    const int x = fr.x0 + local % fr.nx, y = fr.y0 + local / fr.nx;
+    const npvs_camera& c = cams[fr.b];
+    const AxisFrame A = axis_frame(c, fr.axis);
+    const SliceTable T = slice_table(c, g.D);
+    const float tanh_ = c.tan_half;
+    const float num = __fsub_rn(fr.P, A.o_ax);
+    const ColumnSpan sp = column_span(fr, x, y, s);
+    const size_t word_base = (((size_t)fr.b * g.D) * g.H + y) * WW + (x >> 5);
+    const uint32_t bit = 1u << (x & 31);
+    float ca_ax[CAP], ca_1[CAP], ca_2[CAP];
+#pragma unroll
+    for (int i = 0; i < CAP; ++i) {
+        if (i >= s) break;
+        const float sx = __fmul_rn(xs[x * s + i], tanh_);
+        ca_ax[i] = __fadd_rn(A.f_ax, __fmul_rn(sx, A.r_ax));
+        ca_1[i] = __fadd_rn(A.f1, __fmul_rn(sx, A.r1));
+        ca_2[i] = __fadd_rn(A.f2, __fmul_rn(sx, A.r2));
+    }
+    float zlo = 0.f, zhi = -1.f;  // slice interval of the last slice set
+    for (int bb = sp.b0 + q; bb <= sp.b1; bb += nq) {
+        const float sy = __fmul_rn(ys[bb], tanh_);
+        const float su_ax = __fmul_rn(sy, A.u_ax), su_1 = __fmul_rn(sy, A.u1), su_2 = __fmul_rn(sy, A.u2);
+#pragma unroll
+        for (int i = 0; i < CAP; ++i) {
+            if (i >= s) break;
+            if (i < sp.i0 || i > sp.i1) continue;
+            const float d_ax = __fadd_rn(ca_ax[i], su_ax);
+            if (d_ax == 0.0f) continue;
+            const float t = __fdiv_rn(num, d_ax);
+            if (!(t >= T.z0 && t < T.zD)) continue;
+            const float h1 = __fadd_rn(A.o1, __fmul_rn(t, __fadd_rn(ca_1[i], su_1)));
+            if (!(h1 >= fr.lo1 && h1 <= fr.hi1)) continue;
+            const float h2 = __fadd_rn(A.o2, __fmul_rn(t, __fadd_rn(ca_2[i], su_2)));
+            if (!(h2 >= fr.lo2 && h2 <= fr.hi2)) continue;
+            if (!(t >= zlo && t < zhi)) {
+                const int k = slice_guess(T.z, T.D, t, T.lz0, T.kscale);
+                if constexpr (TEST) {
+                    if (__ldg(test_bits + word_base + (size_t)k * g.H * WW) & bit) {
+                        visible[lo / 6] = 1;
+                        return;
+                    }
+                } else {
+                    atomicOr(bits + word_base + (size_t)k * g.H * WW, bit);
+                }
+                zlo = T.z[k];
+                zhi = T.z[k + 1];
+            }
+        }
+    }
 }
 
 // SS: the supersampling factor as a compile-time constant (0: runtime value s, up to 16).
 // Items (face, froxel column) are numbered face by face; a warp's 32 consecutive items belong to
-// one face or a few neighbouring ones, so lane 0 finds the face of the warp's first item by binary
-// search and every lane walks forward from it.
+// one face or a few neighbouring ones, found by a warp-wide search. Each thread first decides its
+// item from interval bounds (classify_span): most columns lie wholly outside the face or wholly
+// inside it within one slice, and set at most one bit. The block then gathers its undecided items
+// into shared memory and casts their rays, each item's rows split over up to s threads, so that the
+// threads that cast rays hold undecided items only, instead of waiting on a few edge columns among
+// decided ones.
 // TEST = false: a hit sets its froxel's bit in `bits`. TEST = true (pruning): a hit whose froxel
-// is set in `test_bits` marks the face's box (face index / 6) in `visible` and ends the item; items
-// of boxes already marked are skipped. The rays and their rounding are the same in both modes.
+// is set in `test_bits` marks the face's box (face index / 6) in `visible`; items of boxes already
+// marked are skipped. The rays and their rounding are the same in both modes.
+constexpr int kItemsBlock = 256;
+
 template <int SS, bool TEST>
-__global__ void __launch_bounds__(256, 4) froxel_items_kernel(
+__global__ void __launch_bounds__(kItemsBlock, 4) froxel_items_kernel(
     const FaceRec* __restrict__ faces, const long long* __restrict__ offs, int n_faces,
     const long long* __restrict__ total_p, const npvs_camera* __restrict__ cams, npvs_grid g, int s_rt,
     const float* __restrict__ centres, uint32_t* __restrict__ bits, const uint32_t* __restrict__ test_bits,
-    uint8_t* visible) {
+    uint8_t* visible, unsigned long long* __restrict__ work) {
+    __shared__ long long s_item[kItemsBlock];
+    __shared__ int s_face[kItemsBlock];
+    __shared__ int s_n;
+    __shared__ long long s_base;
     pdl_begin();
-    constexpr int CAP = SS ? SS : 16;
     const int s = SS ? SS : s_rt;
     const long long total = *total_p;
     const int sW = s * g.W, WW = g.W >> 5;
     const float* ys = centres + sW;
     const int lane = threadIdx.x & 31;
-    // the loop runs per warp (base = the warp's first item), so every lane reaches the shuffle
-    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total;
-         base += (long long)gridDim.x * blockDim.x) {
+    // The blocks take units of kItemsBlock items from a work counter (cleared by the scan before this
+    // launch), so that blocks whose items take long do not leave the others idle at the end. The loop
+    // runs per block: every thread reaches the barriers and the warp collectives.
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_n = 0;
+            s_base = (long long)atomicAdd(work, (unsigned long long)kItemsBlock);
+        }
+        __syncthreads();
+        const long long block_base = s_base;
+        if (block_base >= total) break;
+        const long long base = block_base + (threadIdx.x & ~31);  // the warp's first item
         const long long item = base + lane;
         // max f with offs[f] <= base (offs[0] = 0, non-decreasing), searched by the whole warp: each
         // round the lanes probe 32 evenly spaced faces of [flo, fhi] and a ballot keeps the span of
@@ -219,78 +474,59 @@ __global__ void __launch_bounds__(256, 4) froxel_items_kernel(
             const unsigned ok = __ballot_sync(0xffffffffu, pos <= fhi && offs[pos] <= base);
             flo += 31 - __clz(ok);
         }
+        // each lane's face, max f with offs[f] <= item: the warp loads the offsets of 32 faces from
+        // flo at a time and every lane keeps the last one at or below its item; another window
+        // follows while the window's last face starts at or before the warp's last item
         int lo = flo;
-        if (item >= total) continue;
-        while (lo + 1 < n_faces && offs[lo + 1] <= item) ++lo;
-        if (TEST && *(volatile const uint8_t*)(visible + lo / 6)) continue;  // box already kept
-        const FaceRec fr = faces[lo];
-        int local = (int)(item - offs[lo]);
-        int x = fr.x0 + local % fr.nx, y = fr.y0 + local / fr.nx;
-        const npvs_camera& c = cams[fr.b];
-        const int ax = fr.axis, j1 = ax == 2 ? 0 : ax + 1, j2 = ax == 0 ? 2 : ax - 1;
-        const float o_ax = c.origin[ax], o1 = c.origin[j1], o2 = c.origin[j2];
-        const float f_ax = c.fwd[ax], f1 = c.fwd[j1], f2 = c.fwd[j2];
-        const float r_ax = c.right[ax], r1 = c.right[j1], r2 = c.right[j2];
-        const float u_ax = c.up[ax], u1 = c.up[j1], u2 = c.up[j2];
-        const float tanh_ = c.tan_half;
-        const float* z = c.slices;
-        const float z0 = z[0], zD = z[g.D];
-        const float lz0 = __log2f(z0), kscale = (float)g.D / (__log2f(zD) - lz0);
-        const float num = __fsub_rn(fr.P, o_ax);
-        size_t word_base = (((size_t)fr.b * g.D) * g.H + y) * WW + (x >> 5);
-        const uint32_t bit = 1u << (x & 31);
-        // ray direction parts that depend on the sub-column a only: f_i + (n_x tan) r_i, each
-        // operation rounded as in the per-ray definition
-        float ca_ax[CAP], ca_1[CAP], ca_2[CAP];
+        for (int wf = flo;; wf += 32) {
+            const long long o = wf + lane < n_faces ? offs[wf + lane] : LLONG_MAX;
 #pragma unroll
-        for (int i = 0; i < CAP; ++i) {
-            if (i >= s) break;
-            const float nx = centres[x * s + i];
-            const float sx = __fmul_rn(nx, tanh_);
-            ca_ax[i] = __fadd_rn(f_ax, __fmul_rn(sx, r_ax));
-            ca_1[i] = __fadd_rn(f1, __fmul_rn(sx, r1));
-            ca_2[i] = __fadd_rn(f2, __fmul_rn(sx, r2));
+            for (int j = 0; j < 32; ++j)
+                if (__shfl_sync(0xffffffffu, o, j) <= item) lo = wf + j;
+            if (!(__shfl_sync(0xffffffffu, o, 31) <= base + 31)) break;
         }
-        int last_k = -1;
-        float zlo = 0.f, zhi = -1.f;  // slice interval of last_k
-        bool kept = false;            // TEST: the item found a froxel of the PVS
-        // the column's rays inside the face's pixel rectangle
-        const int i0 = max(fr.sa0 - x * s, 0), i1 = min(fr.sa1 - x * s, s - 1);
-        const int b_end = min(fr.sb1 + 1, y * s + s);
-        for (int bb = max(y * s, fr.sb0); bb < b_end && !kept; ++bb) {
-            const float ny = ys[bb];
-            const float sy = __fmul_rn(ny, tanh_);
-            const float su_ax = __fmul_rn(sy, u_ax), su_1 = __fmul_rn(sy, u1), su_2 = __fmul_rn(sy, u2);
-#pragma unroll
-            for (int i = 0; i < CAP; ++i) {
-                if (i >= s) break;
-                if (i < i0 || i > i1) continue;
-                const float d_ax = __fadd_rn(ca_ax[i], su_ax);
-                if (d_ax == 0.0f) continue;
-                const float t = __fdiv_rn(num, d_ax);
-                if (!(t >= z0 && t < zD)) continue;
-                const float h1 = __fadd_rn(o1, __fmul_rn(t, __fadd_rn(ca_1[i], su_1)));
-                if (!(h1 >= fr.lo1 && h1 <= fr.hi1)) continue;
-                const float h2 = __fadd_rn(o2, __fmul_rn(t, __fadd_rn(ca_2[i], su_2)));
-                if (!(h2 >= fr.lo2 && h2 <= fr.hi2)) continue;
-                if (!(t >= zlo && t < zhi)) {
-                    const int k = slice_guess(z, g.D, t, lz0, kscale);
+        if (item < total) {
+            if (!(TEST && *(volatile const uint8_t*)(visible + lo / 6))) {  // box not kept yet
+                const FaceRec fr = faces[lo];
+                const int local = (int)(item - offs[lo]);
+                const int x = fr.x0 + local % fr.nx, y = fr.y0 + local / fr.nx;
+                const npvs_camera& c = cams[fr.b];
+                const AxisFrame A = axis_frame(c, fr.axis);
+                const SliceTable T = slice_table(c, g.D);
+                const ColumnSpan sp = column_span(fr, x, y, s);
+                int k = -1;
+                const int cls = (sp.i0 <= sp.i1 && sp.b0 <= sp.b1)
+                                    ? classify_span(fr, A, __fsub_rn(fr.P, A.o_ax), c.tan_half, sp, x, s, centres,
+                                                    ys, T, &k)
+                                    : 0;
+                if (cls == 1) {
+                    const size_t w = (((size_t)fr.b * g.D + k) * g.H + y) * WW + (x >> 5);
+                    const uint32_t bit = 1u << (x & 31);
                     if constexpr (TEST) {
-                        if (__ldg(test_bits + word_base + (size_t)k * g.H * WW) & bit) {
-                            visible[lo / 6] = 1;
-                            kept = true;
-                            break;
-                        }
+                        if (__ldg(test_bits + w) & bit) visible[lo / 6] = 1;
                     } else {
-                        atomicOr(bits + word_base + (size_t)k * g.H * WW, bit);
+                        atomicOr(bits + w, bit);
                     }
-                    last_k = k;
-                    zlo = z[k];
-                    zhi = z[k + 1];
+                } else if (cls == 2) {
+                    const int j = atomicAdd(&s_n, 1);
+                    s_item[j] = item;
+                    s_face[j] = lo;
                 }
             }
         }
-        (void)last_k;
+        __syncthreads();
+        // nq threads per undecided item (a power of two, at most s rows each), so that the whole
+        // block casts rays when few items are undecided
+        const int n_slow = s_n;
+        if (n_slow > 0) {
+            int nq = 1;
+            while (2 * nq * n_slow <= kItemsBlock && 2 * nq <= s) nq *= 2;
+            const int j = (int)threadIdx.x / nq;
+            if (j < n_slow)
+                cast_item_rays<SS, TEST>(faces, offs, s_face[j], s_item[j], (int)threadIdx.x % nq, nq, cams, g, s,
+                                         centres, ys, bits, test_bits, visible);
+        }
+        __syncthreads();  // the list and s_base are read before the next unit resets them
     }
 }
 
@@ -304,7 +540,7 @@ static size_t froxel_ws(int n_boxes) {
     size_t nchunk = (F + kScanChunk - 1) / kScanChunk;
     return Arena::round(F * sizeof(FaceRec)) + Arena::round(F * sizeof(int)) +
            Arena::round(F * sizeof(long long)) + 2 * Arena::round((nchunk + 1) * sizeof(int)) +
-           Arena::round(sizeof(long long)) + Arena::round(2 * 65536 * sizeof(float)) + 256;
+           2 * Arena::round(sizeof(long long)) + Arena::round(2 * 65536 * sizeof(float)) + 256;
 }
 
 extern "C" size_t npvs_froxelize_workspace_bytes(int32_t n_boxes) { return froxel_ws(n_boxes); }
@@ -339,20 +575,28 @@ static npvs_status froxel_run(const float* boxes, const int32_t* box_offsets, in
     int* csum = ar.take<int>(nchunk + 1);
     int* coff = ar.take<int>(nchunk + 1);
     long long* total = ar.take<long long>(1);
+    unsigned long long* work = ar.take<unsigned long long>(1);
     float* centres = ar.take<float>((size_t)s * g.W + (size_t)s * g.H);
-    launch_k(raster_centres_kernel, ceil_div((long long)s * (g.W + g.H), 256), 256, 0, st, s * g.W, s * g.H, centres);
-    NPVS_TRY(check_launch("raster_centres_kernel"));
-    launch_k(face_setup_kernel, ceil_div(F, 256), 256, 0, st, boxes, box_offsets, n_boxes, cams, g, (int)s, faces, counts);
+    // 64-thread blocks: the per-face set-up is latency bound, so it is spread over as many SMs as
+    // the faces allow
+    const long long setup_threads = std::max<long long>(F, (long long)s * (g.W + g.H));
+    launch_k(face_setup_kernel, ceil_div(setup_threads, 64), 64, 0, st, boxes, box_offsets, n_boxes, cams, g, (int)s,
+             faces, counts, centres);
     NPVS_TRY(check_launch("face_setup_kernel"));
-    launch_k(chunk_scan_kernel, nchunk, kScanChunk, 0, st, counts, offs, F, csum);
-    NPVS_TRY(check_launch("chunk_scan_kernel"));
-    NPVS_TRY(scan_block_counts(csum, coff, nchunk, csum + nchunk, -1, nullptr, st));
-    launch_k(chunk_add_kernel, nchunk, kScanChunk, 0, st, offs, F, coff, counts, total);
-    NPVS_TRY(check_launch("chunk_add_kernel"));
-    const int grid = kNumSMs * 8;
+    if (F <= kSmallScanMax) {
+        launch_k(face_scan_small_kernel, 1, kSmallScanThreads, 0, st, counts, offs, F, total, work);
+        NPVS_TRY(check_launch("face_scan_small_kernel"));
+    } else {
+        launch_k(chunk_scan_kernel, nchunk, kScanChunk, 0, st, counts, offs, F, csum);
+        NPVS_TRY(check_launch("chunk_scan_kernel"));
+        NPVS_TRY(scan_block_counts(csum, coff, nchunk, csum + nchunk, -1, nullptr, st));
+        launch_k(chunk_add_kernel, nchunk, kScanChunk, 0, st, offs, F, coff, counts, total, work);
+        NPVS_TRY(check_launch("chunk_add_kernel"));
+    }
+    const int grid = kNumSMs * 4;  // resident blocks (4 per SM); the work counter balances them
 #define NPVS_ITEMS(SSV, T)                                                                                           \
-    launch_k(froxel_items_kernel<SSV, T>, grid, 256, 0, st, faces, offs, F, total, cams, g, s, centres, bits, test_bits, \
-             visible)
+    launch_k(froxel_items_kernel<SSV, T>, grid, kItemsBlock, 0, st, faces, offs, F, total, cams, g, s, centres, bits, test_bits, \
+             visible, work)
     if (test_bits) {
         switch (s) {
             case 4: NPVS_ITEMS(4, true); break;

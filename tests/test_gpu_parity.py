@@ -110,6 +110,21 @@ def test_froxelize_city256_full_size_sampled_columns():
     assert 0.02 <= occ <= 0.08, occ
 
 
+@pytest.mark.parametrize("vc_index,height,s", [(3, (2.0, 2.0), 8), (1, (30.0, 60.0), 4)])
+def test_froxelize_city256_whole_frame_bit_exact(vc_index, height, s):
+    """Whole 256x256x128 frames of the 2,001-box city against the oracle's full grid: a street-level
+    viewcell at s = 8 (the ground at grazing angles, walls edge-on) and one 30-60 units up at s = 4
+    (roofs from above). Every column the kernel settles from interval bounds must give the same bits
+    as casting its rays."""
+    wl = I.workload("city256")
+    boxes = I.city_boxes(0)
+    vc = I.city_viewcells(0, vc_index + 1, height=height)[vc_index]
+    got = gpu_froxelize([boxes], [vc], wl.W, wl.H, wl.D, s)[0]
+    ref = ofx.froxelize(ocam.frustum(vc, wl.D), boxes, wl.W, wl.H, wl.D, s)
+    assert popcount(ref) > 20000
+    assert popcount(got ^ ref) == 0
+
+
 # ------------------------------------------------------------------------------------------
 # a3 interleave, a7 de-interleave
 # ------------------------------------------------------------------------------------------
