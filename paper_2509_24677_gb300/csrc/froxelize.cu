@@ -37,21 +37,12 @@ __device__ __forceinline__ int batch_of_box(const int32_t* off, int B, int j) {
     return lo;
 }
 
-// One thread per face; threads f < sW + sH also write the normalised pixel centre f of the
-// supersampled raster, n = (2a + 1 - S) / S in one binary32 division: xs[a] for a < sW, then ys[b].
-__global__ void face_setup_kernel(const float* __restrict__ boxes, const int32_t* __restrict__ box_off,
-                                  int n_boxes, const npvs_camera* __restrict__ cams, npvs_grid g, int s,
-                                  FaceRec* __restrict__ faces, int* __restrict__ counts, float* __restrict__ xs) {
-    pdl_begin();
-    int f = blockIdx.x * blockDim.x + threadIdx.x;
-    {
-        const int sW = s * g.W, sH = s * g.H;
-        if (f < sW) xs[f] = __fdiv_rn((float)(2 * f + 1 - sW), (float)sW);
-        else if (f < sW + sH) xs[f] = __fdiv_rn((float)(2 * (f - sW) + 1 - sH), (float)sH);
-    }
-    if (f >= n_boxes * 6) return;
+// The record of face f (box f / 6, face f % 6) and the number of froxel columns its pixel
+// rectangle touches.
+__device__ __forceinline__ int face_record(const float* __restrict__ boxes, const int32_t* __restrict__ box_off,
+                                           const npvs_camera* __restrict__ cams, const npvs_grid& g, int s, int f,
+                                           FaceRec& rec) {
     int j = f / 6, fl = f % 6, axis = fl >> 1, side = fl & 1;
-    FaceRec rec;
     rec.nx = rec.ny = 0;
     rec.x0 = rec.y0 = 0;
     rec.sa0 = rec.sb0 = 0;
@@ -127,8 +118,53 @@ __global__ void face_setup_kernel(const float* __restrict__ boxes, const int32_t
     } else {
         rec.b = 0; rec.axis = 0; rec.P = rec.lo1 = rec.hi1 = rec.lo2 = rec.hi2 = 0.f;
     }
-    faces[f] = rec;
-    counts[f] = cnt;
+    return cnt;
+}
+
+// One thread per face (64-thread blocks: the set-up is latency bound, so it is spread over as many
+// SMs as the faces allow): the face record, its column count, the exclusive prefix of the counts
+// within the block (offs) and the block's total (block_sum). Threads f < sW + sH also write the
+// normalised pixel centre f of the supersampled raster, n = (2a + 1 - S) / S in one binary32
+// division: xs[a] for a < sW, then ys[b].
+constexpr int kSetupBlock = 64;
+
+__global__ void __launch_bounds__(kSetupBlock) face_setup_kernel(
+    const float* __restrict__ boxes, const int32_t* __restrict__ box_off, int n_boxes,
+    const npvs_camera* __restrict__ cams, npvs_grid g, int s, FaceRec* __restrict__ faces, int* __restrict__ counts,
+    long long* __restrict__ offs, long long* __restrict__ block_sum, float* __restrict__ xs) {
+    __shared__ long long warp_sum[kSetupBlock / 32];
+    pdl_begin();
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    {
+        const int sW = s * g.W, sH = s * g.H;
+        if (f < sW) xs[f] = __fdiv_rn((float)(2 * f + 1 - sW), (float)sW);
+        else if (f < sW + sH) xs[f] = __fdiv_rn((float)(2 * (f - sW) + 1 - sH), (float)sH);
+    }
+    const bool own = f < n_boxes * 6;
+    int cnt = 0;
+    if (own) {
+        FaceRec rec;
+        cnt = face_record(boxes, box_off, cams, g, s, f, rec);
+        faces[f] = rec;
+        counts[f] = cnt;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_sum[warp] = incl;
+    __syncthreads();
+    long long before = 0, all = 0;
+#pragma unroll
+    for (int w = 0; w < kSetupBlock / 32; ++w) {
+        if (w < warp) before += warp_sum[w];
+        all += warp_sum[w];
+    }
+    if (own) offs[f] = before + incl - cnt;
+    if (threadIdx.x == 0) block_sum[blockIdx.x] = all;
 }
 
 // Per-chunk exclusive scan of counts into 64-bit offsets; chunk sums for the second level.
@@ -157,62 +193,61 @@ __global__ void chunk_add_kernel(long long* __restrict__ offs, int n, const int*
     }
 }
 
-// Exclusive scan of up to kSmallScanMax face counts into 64-bit offsets by one block, in tiles of
-// four counts per thread (coalesced 16-byte loads, a running carry between tiles), and the total.
-// Thread 0 also clears the item kernel's work counter.
+// The global offsets of up to kSmallScanMax faces by one block: the exclusive scan of the set-up
+// kernel's block totals, added to its block-local prefixes; the total; and the item kernel's work
+// counter cleared.
 constexpr int kSmallScanThreads = 1024;
-constexpr int kSmallScanMax = 32 * kSmallScanThreads;
+constexpr int kSmallScanMax = kSetupBlock * kSmallScanThreads;
 
-__global__ void __launch_bounds__(kSmallScanThreads) face_scan_small_kernel(const int* __restrict__ counts,
-                                                                          long long* __restrict__ offs, int n,
-                                                                          long long* __restrict__ total,
-                                                                          unsigned long long* __restrict__ work) {
-    pdl_begin();
+__global__ void __launch_bounds__(kSmallScanThreads) face_offsets_small_kernel(
+    const long long* __restrict__ block_sum, long long* __restrict__ offs, int n, long long* __restrict__ total,
+    unsigned long long* __restrict__ work) {
     __shared__ long long sw[33];
+    __shared__ long long block_off[kSmallScanThreads];
+    pdl_begin();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (threadIdx.x == 0) *work = 0ull;
-    long long carry = 0;
-    for (int t0 = 0; t0 < n; t0 += 4 * (int)blockDim.x) {
-        const int i0 = t0 + 4 * (int)threadIdx.x;
-        int c[4];
-        if (i0 + 3 < n) {  // counts is 16-byte aligned and i0 a multiple of 4
-            const int4 v = *reinterpret_cast<const int4*>(counts + i0);
-            c[0] = v.x; c[1] = v.y; c[2] = v.z; c[3] = v.w;
-        } else {
+    const int nb = (n + kSetupBlock - 1) / kSetupBlock;
+    const long long v = (int)threadIdx.x < nb ? block_sum[threadIdx.x] : 0;
+    long long incl = v;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) c[j] = i0 + j < n ? counts[i0 + j] : 0;
-        }
-        const long long sum = (long long)c[0] + c[1] + c[2] + c[3];
-        long long incl = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) sw[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const long long w = lane < nw ? sw[lane] : 0;
+        long long wi = w;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const long long t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
+            const long long t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
         }
-        if (lane == 31) sw[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            const long long w = lane < nw ? sw[lane] : 0;
-            long long wi = w;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const long long t = __shfl_up_sync(0xffffffffu, wi, o);
-                if (lane >= o) wi += t;
-            }
-            if (lane < nw) sw[lane] = wi - w;
-            if (lane == 31) sw[32] = wi;
-        }
-        __syncthreads();
-        long long run = carry + sw[warp] + incl - sum;
+        if (lane < nw) sw[lane] = wi - w;
+        if (lane == 31) sw[32] = wi;
+    }
+    __syncthreads();
+    block_off[threadIdx.x] = sw[warp] + incl - v;
+    __syncthreads();
+    // four independent loads in flight per thread before their stores
+    for (int f0 = threadIdx.x; f0 < n; f0 += 4 * blockDim.x) {
+        long long v[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            if (i0 + j < n) offs[i0 + j] = run;
-            run += c[j];
+            const int f = f0 + j * (int)blockDim.x;
+            v[j] = f < n ? offs[f] : 0;
         }
-        carry += sw[32];
-        __syncthreads();  // sw is rewritten by the next tile
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int f = f0 + j * (int)blockDim.x;
+            if (f < n) offs[f] = v[j] + block_off[f / kSetupBlock];
+        }
     }
-    if (threadIdx.x == 0) *total = carry;
+    if (threadIdx.x == 0) {
+        *total = sw[32];
+        *work = 0ull;
+    }
 }
 
 // Slice of t given z[0] <= t < z[D]: a guess from the exponential spacing of the slice table
@@ -538,7 +573,9 @@ using namespace npvs;
 static size_t froxel_ws(int n_boxes) {
     size_t F = (size_t)n_boxes * 6;
     size_t nchunk = (F + kScanChunk - 1) / kScanChunk;
-    return Arena::round(F * sizeof(FaceRec)) + Arena::round(F * sizeof(int)) +
+    // block totals of the set-up kernel: its grid covers max(F, s W + s H <= 2 * 65536) threads
+    size_t nsetup = (std::max<size_t>(F, 2 * 65536) + kSetupBlock - 1) / kSetupBlock;
+    return Arena::round(F * sizeof(FaceRec)) + Arena::round(F * sizeof(int)) + Arena::round(nsetup * sizeof(long long)) +
            Arena::round(F * sizeof(long long)) + 2 * Arena::round((nchunk + 1) * sizeof(int)) +
            2 * Arena::round(sizeof(long long)) + Arena::round(2 * 65536 * sizeof(float)) + 256;
 }
@@ -576,17 +613,16 @@ static npvs_status froxel_run(const float* boxes, const int32_t* box_offsets, in
     int* coff = ar.take<int>(nchunk + 1);
     long long* total = ar.take<long long>(1);
     unsigned long long* work = ar.take<unsigned long long>(1);
-    float* centres = ar.take<float>((size_t)s * g.W + (size_t)s * g.H);
-    // 64-thread blocks: the per-face set-up is latency bound, so it is spread over as many SMs as
-    // the faces allow
     const long long setup_threads = std::max<long long>(F, (long long)s * (g.W + g.H));
-    launch_k(face_setup_kernel, ceil_div(setup_threads, 64), 64, 0, st, boxes, box_offsets, n_boxes, cams, g, (int)s,
-             faces, counts, centres);
+    long long* block_sum = ar.take<long long>((size_t)ceil_div(setup_threads, kSetupBlock));
+    float* centres = ar.take<float>((size_t)s * g.W + (size_t)s * g.H);
+    launch_k(face_setup_kernel, ceil_div(setup_threads, kSetupBlock), kSetupBlock, 0, st, boxes, box_offsets, n_boxes,
+             cams, g, (int)s, faces, counts, offs, block_sum, centres);
     NPVS_TRY(check_launch("face_setup_kernel"));
     if (F <= kSmallScanMax) {
-        launch_k(face_scan_small_kernel, 1, kSmallScanThreads, 0, st, counts, offs, F, total, work);
-        NPVS_TRY(check_launch("face_scan_small_kernel"));
-    } else {
+        launch_k(face_offsets_small_kernel, 1, kSmallScanThreads, 0, st, block_sum, offs, F, total, work);
+        NPVS_TRY(check_launch("face_offsets_small_kernel"));
+    } else {  // the offsets again from the counts, by chunks
         launch_k(chunk_scan_kernel, nchunk, kScanChunk, 0, st, counts, offs, F, csum);
         NPVS_TRY(check_launch("chunk_scan_kernel"));
         NPVS_TRY(scan_block_counts(csum, coff, nchunk, csum + nchunk, -1, nullptr, st));
