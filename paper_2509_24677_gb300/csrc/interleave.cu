@@ -239,7 +239,7 @@ __global__ void deinterleave_kernel(const float* __restrict__ logits, const int3
     const int n = *n_active;
     const int Xc = g.W >> ld, Yc = g.H >> ld, Zc = g.D >> ld, d3 = d * d * d, dm = d - 1;
     for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < n_words; w += gridDim.x * blockDim.x) {
-        uint32_t m = mask_bits[w];
+        const uint32_t m = mask_bits[w];
         uint32_t out = 0;
         if (m) {
             const uint32_t xw = w % WW, t = w / WW;
@@ -248,14 +248,25 @@ __global__ void deinterleave_kernel(const float* __restrict__ logits, const int3
             const int k = (int)(t2 % D), b = (int)(t2 / D);
             const int Y = y >> ld, dy = y & dm, Z = k >> ld, dz = k & dm;
             const long long rowbase = (((long long)b * Zc + Z) * Yc + Y) * Xc;
-            while (m) {
-                const int i = __ffs(m) - 1;
-                m &= m - 1;
-                const int x = (int)xw * 32 + i, X = x >> ld, dx = x & dm;
-                const int row = table[rowbase + X];
-                if (row >= 0 && row < n) {
-                    float z = logits[(size_t)row * d3 + (dz * d + dy) * d + dx];
-                    float pr = 1.0f / (1.0f + expf(-z));
+            const int chan = (dz * d + dy) * d;
+            // the word's occupied froxels in two rounds of independent loads (their sites' rows,
+            // then their logits) before any threshold, instead of a dependent pair per froxel
+            int row[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                row[i] = -1;
+                if ((m >> i) & 1u) row[i] = table[rowbase + ((xw * 32 + i) >> ld)];
+            }
+            float z[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                z[i] = 0.f;
+                if (row[i] >= 0 && row[i] < n) z[i] = logits[(size_t)row[i] * d3 + chan + ((xw * 32 + i) & dm)];
+            }
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                if (row[i] >= 0 && row[i] < n) {
+                    const float pr = 1.0f / (1.0f + expf(-z[i]));
                     if (pr >= tau) out |= 1u << i;
                 }
             }
