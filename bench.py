@@ -216,6 +216,8 @@ def tuned_label(cfg: dict) -> str:
         name += "-nosplit"
     if cfg.get("tune_gather_warps") == 4:
         name += "-4w"
+    if cfg.get("tune_stages", 0) > 0:   # a stage count set by hand
+        name += f"-s{cfg['tune_stages']}"
     return name
 
 
@@ -640,6 +642,7 @@ def run_batched(args, dev, net, tuned):
     occs = [o for _, _, o in picked]
     return {"viewcells": B, "scenes": "4 cities of 2k/6k/12k/24k buildings, seeds 0-3",
             "stage_ms": dict(sorted(stages.items(), key=lambda kv: -kv[1])),
+            "conv_layer_ms": {k[5:]: round(v, 3) for k, v in acc.items() if k.startswith("conv:")},
             "occupancy_range": [round(min(occs), 4), round(max(occs), 4)],
             "batch_ms": round(batch_ms, 4), "frames_per_s": round(B * 1000.0 / batch_ms, 2),
             "chain": {"level": chain_b, "ms_per_batch_by_level": chain_b_ms},

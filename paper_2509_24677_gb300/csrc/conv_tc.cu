@@ -277,9 +277,10 @@ __global__ void __launch_bounds__(threads_for(PW), 1)
     const int n_rows = min(*p.n_rows, p.cap_rows);
     const int tiles = ((n_rows + kBM - 1) / kBM) * p.n_tiles;
     int ksplit = 1, kbc = p.KB;
-    if (p.part != nullptr && (!p.tout || p.tout_split) && tiles > 0 && 2 * tiles <= (int)gridDim.x &&
-        p.max_split > 1) {
-        ksplit = min(min(p.KB, p.max_split), (int)gridDim.x / tiles);
+    // units = tiles x ksplit index the partial tiles and counters: at most kSplitSlots of them
+    const int slots = min((int)gridDim.x, kSplitSlots);
+    if (p.part != nullptr && (!p.tout || p.tout_split) && tiles > 0 && 2 * tiles <= slots && p.max_split > 1) {
+        ksplit = min(min(p.KB, p.max_split), slots / tiles);
         kbc = (p.KB + ksplit - 1) / ksplit;
         ksplit = (p.KB + kbc - 1) / kbc;
     }

@@ -68,6 +68,7 @@ def test_tuned_labels_and_traffic_selection():
     assert bench.tuned_label(win) == "window-nosplit"
     assert bench.tuned_label(win3) == "window3"
     assert bench.tuned_label(gat) == "gather-4w"
+    assert bench.tuned_label({"tune_form": 1, "tune_gather": 4, "tune_stages": 2}) == "window3-s2"
     cfg = {"product": prod, "product-split": {"tune_form": 2, "tune_max_split": 8}, "window3": win3,
            "window3-nosplit": dict(win3, tune_max_split=1), "gather": {"tune_form": 1}}
     tuned = {k: (cfg[v], 1.0) for k, v in bench.FRAME_DRAM["forms"].items()}

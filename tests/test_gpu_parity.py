@@ -300,13 +300,14 @@ CONV_CASES = [
 ]
 
 
-WINDOW_MODES = ("window", "window-split", "window-s2", "window3", "window3-split")
+WINDOW_MODES = ("window", "window-split", "window-s2", "window3", "window3-split", "window3-s2")
 
 
 @pytest.mark.parametrize("dt,mode", [("f32", None), ("bf16", "gather"), ("bf16", "gather-split"),
                                      ("bf16", "product"), ("bf16", "product-split"), ("bf16", "window"),
                                      ("bf16", "window-split"),
-                                     ("bf16", "window3"), ("f32", "product"), ("f32", "gather")])
+                                     ("bf16", "window3"), ("bf16", "window3-s2"), ("bf16", "gather-s4"),
+                                     ("f32", "product"), ("f32", "gather")])
 @pytest.mark.parametrize("kind,cin,cout", CONV_CASES)
 def test_single_conv_parity(kind, cin, cout, dt, mode):
     if dt == "bf16" and kind == "up2" and cout % 16 and cin % 8 == 0 and cout % 8 == 0:
@@ -405,11 +406,11 @@ def single_conv(kind, cin, cout, dt, mode, occ, rng, want_ref=True):
     desc = ops.conv_desc(kid, dtype, cin, cout, True, mp, lv_out.n_rows, lv_out.capacity, out_f32=out_f32,
                          map2=lvs[0].down if kind == "up2" else None, n_in=lv_in.n_rows, cap_in=lv_in.capacity,
                          status=status, form={"gather": 1, "gather-split": 1, "product": 2,
-                                              "product-split": 2}.get(mode, 0),
+                                              "product-split": 2, "gather-s4": 1}.get(mode, 0),
                          gather=(4 if mode.startswith("window3") else 3) if mode in WINDOW_MODES else 0,
                          max_split=1 if mode in ("window", "window-s2", "window3") else
                          (8 if mode == "product-split" else 0),
-                         stages=2 if mode == "window-s2" else 0)
+                         stages=2 if mode in ("window-s2", "window3-s2") else (4 if mode == "gather-s4" else 0))
     if mode in ("gather-split", "product", "product-split", "window-split", "window3-split"):
         ws = ops.conv_workspace(ops.npvs_conv_workspace_bytes(desc), DEV)
         desc.workspace, desc.workspace_bytes = ws.data_ptr(), ws.numel()
