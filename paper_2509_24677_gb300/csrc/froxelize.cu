@@ -123,7 +123,8 @@ __device__ __forceinline__ int face_record(const float* __restrict__ boxes, cons
 
 // One thread per face (64-thread blocks: the set-up is latency bound, so it is spread over as many
 // SMs as the faces allow): the face record, its column count, the exclusive prefix of the counts
-// within the block (offs) and the block's total (block_sum). Threads f < sW + sH also write the
+// within the block (offs) and the block's total (block_sum); it also clears the item kernel's work
+// counter. Threads f < sW + sH also write the
 // normalised pixel centre f of the supersampled raster, n = (2a + 1 - S) / S in one binary32
 // division: xs[a] for a < sW, then ys[b].
 constexpr int kSetupBlock = 64;
@@ -131,10 +132,12 @@ constexpr int kSetupBlock = 64;
 __global__ void __launch_bounds__(kSetupBlock) face_setup_kernel(
     const float* __restrict__ boxes, const int32_t* __restrict__ box_off, int n_boxes,
     const npvs_camera* __restrict__ cams, npvs_grid g, int s, FaceRec* __restrict__ faces, int* __restrict__ counts,
-    long long* __restrict__ offs, long long* __restrict__ block_sum, float* __restrict__ xs) {
+    long long* __restrict__ offs, long long* __restrict__ block_sum, float* __restrict__ xs,
+    unsigned long long* __restrict__ work) {
     __shared__ long long warp_sum[kSetupBlock / 32];
     pdl_begin();
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f == 0) *work = 0ull;  // the item kernel's work counter
     {
         const int sW = s * g.W, sH = s * g.H;
         if (f < sW) xs[f] = __fdiv_rn((float)(2 * f + 1 - sW), (float)sW);
@@ -193,61 +196,14 @@ __global__ void chunk_add_kernel(long long* __restrict__ offs, int n, const int*
     }
 }
 
-// The global offsets of up to kSmallScanMax faces by one block: the exclusive scan of the set-up
-// kernel's block totals, added to its block-local prefixes; the total; and the item kernel's work
-// counter cleared.
-constexpr int kSmallScanThreads = 1024;
-constexpr int kSmallScanMax = kSetupBlock * kSmallScanThreads;
+// Up to kFusedFaceMax faces (at most 1,024 set-up blocks), the item kernel adds the scanned block
+// totals to the set-up kernel's block-local prefixes itself; more faces take the chunked scan.
+constexpr int kFusedFaceMax = kSetupBlock * 1024;
 
-__global__ void __launch_bounds__(kSmallScanThreads) face_offsets_small_kernel(
-    const long long* __restrict__ block_sum, long long* __restrict__ offs, int n, long long* __restrict__ total,
-    unsigned long long* __restrict__ work) {
-    __shared__ long long sw[33];
-    __shared__ long long block_off[kSmallScanThreads];
-    pdl_begin();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int nb = (n + kSetupBlock - 1) / kSetupBlock;
-    const long long v = (int)threadIdx.x < nb ? block_sum[threadIdx.x] : 0;
-    long long incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const long long t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) sw[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        const long long w = lane < nw ? sw[lane] : 0;
-        long long wi = w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long t = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += t;
-        }
-        if (lane < nw) sw[lane] = wi - w;
-        if (lane == 31) sw[32] = wi;
-    }
-    __syncthreads();
-    block_off[threadIdx.x] = sw[warp] + incl - v;
-    __syncthreads();
-    // four independent loads in flight per thread before their stores
-    for (int f0 = threadIdx.x; f0 < n; f0 += 4 * blockDim.x) {
-        long long v[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int f = f0 + j * (int)blockDim.x;
-            v[j] = f < n ? offs[f] : 0;
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int f = f0 + j * (int)blockDim.x;
-            if (f < n) offs[f] = v[j] + block_off[f / kSetupBlock];
-        }
-    }
-    if (threadIdx.x == 0) {
-        *total = sw[32];
-        *work = 0ull;
-    }
+// The global item offset of face f: offs[f], plus its set-up block's offset when offs holds the
+// block-local prefixes (boff != nullptr).
+__device__ __forceinline__ long long face_off(const long long* __restrict__ offs, const long long* boff, int f) {
+    return boff ? offs[f] + boff[f / kSetupBlock] : offs[f];
 }
 
 // Slice of t given z[0] <= t < z[D]: a guess from the exponential spacing of the slice table
@@ -389,7 +345,7 @@ __device__ __forceinline__ int classify_span(const FaceRec& fr, const AxisFrame&
 // q, q + nq, q + 2 nq, ... of the item's span (several threads share an item's rays).
 template <int SS, bool TEST>
 __device__ __forceinline__ void cast_item_rays(const FaceRec* __restrict__ faces, const long long* __restrict__ offs,
-                                               int lo, long long item, int q, int nq,
+                                               const long long* boff, int lo, long long item, int q, int nq,
                                                const npvs_camera* __restrict__ cams,
                                                const npvs_grid& g, int s, const float* __restrict__ xs,
                                                const float* __restrict__ ys, uint32_t* __restrict__ bits,
@@ -398,7 +354,7 @@ __device__ __forceinline__ void cast_item_rays(const FaceRec* __restrict__ faces
     if (TEST && *(volatile const uint8_t*)(visible + lo / 6)) return;  // box already kept
     const int WW = g.W >> 5;
     const FaceRec fr = faces[lo];
-    const int local = (int)(item - offs[lo]);
+    const int local = (int)(item - face_off(offs, boff, lo));
     const int x = fr.x0 + local % fr.nx, y = fr.y0 + local / fr.nx;
     const npvs_camera& c = cams[fr.b];
     const AxisFrame A = axis_frame(c, fr.axis);
@@ -466,22 +422,69 @@ constexpr int kItemsBlock = 256;
 template <int SS, bool TEST>
 __global__ void __launch_bounds__(kItemsBlock, 4) froxel_items_kernel(
     const FaceRec* __restrict__ faces, const long long* __restrict__ offs, int n_faces,
-    const long long* __restrict__ total_p, const npvs_camera* __restrict__ cams, npvs_grid g, int s_rt,
-    const float* __restrict__ centres, uint32_t* __restrict__ bits, const uint32_t* __restrict__ test_bits,
-    uint8_t* visible, unsigned long long* __restrict__ work) {
+    const long long* __restrict__ total_p, const long long* __restrict__ block_sum,
+    const npvs_camera* __restrict__ cams, npvs_grid g, int s_rt, const float* __restrict__ centres,
+    uint32_t* __restrict__ bits, const uint32_t* __restrict__ test_bits, uint8_t* visible,
+    unsigned long long* __restrict__ work) {
     __shared__ long long s_item[kItemsBlock];
     __shared__ int s_face[kItemsBlock];
     __shared__ int s_n;
     __shared__ long long s_base;
+    __shared__ long long s_boff[kFusedFaceMax / kSetupBlock];
+    __shared__ long long s_wsum[kItemsBlock / 32 + 1];
     pdl_begin();
     const int s = SS ? SS : s_rt;
-    const long long total = *total_p;
     const int sW = s * g.W, WW = g.W >> 5;
     const float* ys = centres + sW;
-    const int lane = threadIdx.x & 31;
-    // The blocks take units of kItemsBlock items from a work counter (cleared by the scan before this
-    // launch), so that blocks whose items take long do not leave the others idle at the end. The loop
-    // runs per block: every thread reaches the barriers and the warp collectives.
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // block_sum != nullptr: offs holds the set-up kernel's block-local prefixes; every block scans
+    // the block totals (four per thread) into s_boff and takes the total from it. Else offs holds
+    // the global offsets and *total_p the total.
+    const long long* boff = nullptr;
+    long long total;
+    if (block_sum) {
+        constexpr int kPer = kFusedFaceMax / kSetupBlock / kItemsBlock;
+        const int nbs = (n_faces + kSetupBlock - 1) / kSetupBlock;
+        long long v[kPer], sum = 0;
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int i = threadIdx.x * kPer + j;
+            v[j] = i < nbs ? block_sum[i] : 0;
+            sum += v[j];
+        }
+        long long incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_wsum[warp] = incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long r = 0;
+            for (int w = 0; w < kItemsBlock / 32; ++w) {
+                const long long t = s_wsum[w];
+                s_wsum[w] = r;
+                r += t;
+            }
+            s_wsum[kItemsBlock / 32] = r;
+        }
+        __syncthreads();
+        long long run = s_wsum[warp] + incl - sum;
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            s_boff[threadIdx.x * kPer + j] = run;
+            run += v[j];
+        }
+        total = s_wsum[kItemsBlock / 32];
+        boff = s_boff;
+        __syncthreads();
+    } else {
+        total = *total_p;
+    }
+    // The blocks take units of kItemsBlock items from a work counter (cleared before this launch),
+    // so that blocks whose items take long do not leave the others idle at the end. The loop runs
+    // per block: every thread reaches the barriers and the warp collectives.
     for (;;) {
         if (threadIdx.x == 0) {
             s_n = 0;
@@ -499,14 +502,14 @@ __global__ void __launch_bounds__(kItemsBlock, 4) froxel_items_kernel(
         while (fhi - flo >= 32) {
             const int step = (fhi - flo + 32) / 32;
             const int pos = min(flo + lane * step, fhi);
-            const unsigned ok = __ballot_sync(0xffffffffu, offs[pos] <= base);  // lane 0 (pos = flo) holds
+            const unsigned ok = __ballot_sync(0xffffffffu, face_off(offs, boff, pos) <= base);  // lane 0 (pos = flo) holds
             const int k = 31 - __clz(ok);
             flo = min(flo + k * step, fhi);
             fhi = min(flo + step - 1, fhi);
         }
         {
             const int pos = flo + lane;
-            const unsigned ok = __ballot_sync(0xffffffffu, pos <= fhi && offs[pos] <= base);
+            const unsigned ok = __ballot_sync(0xffffffffu, pos <= fhi && face_off(offs, boff, pos) <= base);
             flo += 31 - __clz(ok);
         }
         // each lane's face, max f with offs[f] <= item: the warp loads the offsets of 32 faces from
@@ -514,7 +517,7 @@ __global__ void __launch_bounds__(kItemsBlock, 4) froxel_items_kernel(
         // follows while the window's last face starts at or before the warp's last item
         int lo = flo;
         for (int wf = flo;; wf += 32) {
-            const long long o = wf + lane < n_faces ? offs[wf + lane] : LLONG_MAX;
+            const long long o = wf + lane < n_faces ? face_off(offs, boff, wf + lane) : LLONG_MAX;
 #pragma unroll
             for (int j = 0; j < 32; ++j)
                 if (__shfl_sync(0xffffffffu, o, j) <= item) lo = wf + j;
@@ -523,7 +526,7 @@ __global__ void __launch_bounds__(kItemsBlock, 4) froxel_items_kernel(
         if (item < total) {
             if (!(TEST && *(volatile const uint8_t*)(visible + lo / 6))) {  // box not kept yet
                 const FaceRec fr = faces[lo];
-                const int local = (int)(item - offs[lo]);
+                const int local = (int)(item - face_off(offs, boff, lo));
                 const int x = fr.x0 + local % fr.nx, y = fr.y0 + local / fr.nx;
                 const npvs_camera& c = cams[fr.b];
                 const AxisFrame A = axis_frame(c, fr.axis);
@@ -558,7 +561,7 @@ __global__ void __launch_bounds__(kItemsBlock, 4) froxel_items_kernel(
             while (2 * nq * n_slow <= kItemsBlock && 2 * nq <= s) nq *= 2;
             const int j = (int)threadIdx.x / nq;
             if (j < n_slow)
-                cast_item_rays<SS, TEST>(faces, offs, s_face[j], s_item[j], (int)threadIdx.x % nq, nq, cams, g, s,
+                cast_item_rays<SS, TEST>(faces, offs, boff, s_face[j], s_item[j], (int)threadIdx.x % nq, nq, cams, g, s,
                                          centres, ys, bits, test_bits, visible);
         }
         __syncthreads();  // the list and s_base are read before the next unit resets them
@@ -617,12 +620,10 @@ static npvs_status froxel_run(const float* boxes, const int32_t* box_offsets, in
     long long* block_sum = ar.take<long long>((size_t)ceil_div(setup_threads, kSetupBlock));
     float* centres = ar.take<float>((size_t)s * g.W + (size_t)s * g.H);
     launch_k(face_setup_kernel, ceil_div(setup_threads, kSetupBlock), kSetupBlock, 0, st, boxes, box_offsets, n_boxes,
-             cams, g, (int)s, faces, counts, offs, block_sum, centres);
+             cams, g, (int)s, faces, counts, offs, block_sum, centres, work);
     NPVS_TRY(check_launch("face_setup_kernel"));
-    if (F <= kSmallScanMax) {
-        launch_k(face_offsets_small_kernel, 1, kSmallScanThreads, 0, st, block_sum, offs, F, total, work);
-        NPVS_TRY(check_launch("face_offsets_small_kernel"));
-    } else {  // the offsets again from the counts, by chunks
+    const bool fused = F <= kFusedFaceMax;  // the item kernel adds the block offsets itself
+    if (!fused) {  // the offsets again from the counts, by chunks
         launch_k(chunk_scan_kernel, nchunk, kScanChunk, 0, st, counts, offs, F, csum);
         NPVS_TRY(check_launch("chunk_scan_kernel"));
         NPVS_TRY(scan_block_counts(csum, coff, nchunk, csum + nchunk, -1, nullptr, st));
@@ -631,8 +632,8 @@ static npvs_status froxel_run(const float* boxes, const int32_t* box_offsets, in
     }
     const int grid = kNumSMs * 4;  // resident blocks (4 per SM); the work counter balances them
 #define NPVS_ITEMS(SSV, T)                                                                                           \
-    launch_k(froxel_items_kernel<SSV, T>, grid, kItemsBlock, 0, st, faces, offs, F, total, cams, g, s, centres, bits, test_bits, \
-             visible, work)
+    launch_k(froxel_items_kernel<SSV, T>, grid, kItemsBlock, 0, st, faces, offs, F, total, fused ? block_sum : nullptr,  \
+             cams, g, s, centres, bits, test_bits, visible, work)
     if (test_bits) {
         switch (s) {
             case 4: NPVS_ITEMS(4, true); break;

@@ -15,6 +15,8 @@ namespace npvs {
 namespace {
 
 constexpr int kSitesPerCta = 256;
+// grids of at most this many CTAs sum the counts before each CTA in the write kernel (no scan launch)
+constexpr int kFusedScanCtas = 1024;
 
 struct ILParams {
     const uint32_t* bits;
@@ -151,8 +153,12 @@ __device__ __forceinline__ void il_write_slab(const ILParams& p, int4 st, int r,
 }
 
 // write_feats == 0: coordinates and table only (the features follow in il_feats_kernel).
+// block_off == nullptr: the CTA sums the counts of the CTAs before it itself (grids of at most
+// kFusedScanCtas CTAs), and the last CTA writes the row count (n_active, clamped to the capacity)
+// that the separate scan would have written.
 template <int DD>
 __global__ void __launch_bounds__(kSitesPerCta) il_write_kernel(ILParams p, const int* __restrict__ block_off,
+                                                                const int* __restrict__ counts, int32_t* n_active,
                                                                 int32_t* __restrict__ coords, void* __restrict__ feats,
                                                                 int32_t* __restrict__ table, int32_t* status,
                                                                 int write_feats) {
@@ -170,7 +176,23 @@ __global__ void __launch_bounds__(kSitesPerCta) il_write_kernel(ILParams p, cons
     }
     int nloc;
     int loc = block_exclusive_scan(f, sw, &nloc);
-    int rank = block_off[blockIdx.x] + loc;
+    int off;
+    if (block_off) {
+        off = block_off[blockIdx.x];
+    } else {
+        int v = 0;
+        for (int i = threadIdx.x; i < (int)blockIdx.x; i += kSitesPerCta) v += counts[i];
+        block_exclusive_scan(v, sw, &off);  // the block total of v: the sites before this CTA
+        if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+            int t = off + nloc;
+            if (p.cap >= 0 && t > p.cap) {
+                raise_status(status, NPVS_ERR_CAPACITY);
+                t = p.cap;
+            }
+            *n_active = t;
+        }
+    }
+    int rank = off + loc;
     if (in && table) table[site] = (f && rank < p.cap) ? rank : -1;
     if (f) {
         if (rank < p.cap) {
@@ -294,16 +316,20 @@ static bool valid_d(int d) { return d == 1 || d == 2 || d == 4 || d == 8 || d ==
 // Compaction, coordinates and table; the features in the same kernel for d <= 8, in a separate
 // device-wide kernel for d >= 16 (a site's d slabs of d^2 values are too much work for 256 sites
 // per CTA). n_active: the device row count the compaction writes.
-static void launch_il_write(const ILParams& p, int nb, const int* offs, int32_t* coords, void* feats, int32_t* table,
-                            int32_t* status, const int32_t* n_active, cudaStream_t st) {
+// offs == nullptr: il_write_kernel computes the CTA offsets from counts and writes n_active.
+static void launch_il_write(const ILParams& p, int nb, const int* offs, const int* counts, int32_t* coords, void* feats,
+                            int32_t* table, int32_t* status, int32_t* n_active, cudaStream_t st) {
     const int wf = p.d >= 16 ? 0 : 1;
+#define NPVS_IL_WRITE(DDV) \
+    launch_k(il_write_kernel<DDV>, nb, kSitesPerCta, 0, st, p, offs, counts, n_active, coords, feats, table, status, wf)
     switch (p.d) {
-        case 2: launch_k(il_write_kernel<2>, nb, kSitesPerCta, 0, st, p, offs, coords, feats, table, status, wf); break;
-        case 4: launch_k(il_write_kernel<4>, nb, kSitesPerCta, 0, st, p, offs, coords, feats, table, status, wf); break;
-        case 8: launch_k(il_write_kernel<8>, nb, kSitesPerCta, 0, st, p, offs, coords, feats, table, status, wf); break;
-        case 16: launch_k(il_write_kernel<16>, nb, kSitesPerCta, 0, st, p, offs, coords, feats, table, status, wf); break;
-        default: launch_k(il_write_kernel<0>, nb, kSitesPerCta, 0, st, p, offs, coords, feats, table, status, wf);
+        case 2: NPVS_IL_WRITE(2); break;
+        case 4: NPVS_IL_WRITE(4); break;
+        case 8: NPVS_IL_WRITE(8); break;
+        case 16: NPVS_IL_WRITE(16); break;
+        default: NPVS_IL_WRITE(0);
     }
+#undef NPVS_IL_WRITE
     if (wf) return;
     const int grid =
         (int)std::max<long long>(1, std::min<long long>(ceil_div((long long)p.cap * p.d * p.d, 256), kNumSMs * 8));
@@ -377,8 +403,12 @@ extern "C" npvs_status npvs_interleave(const uint32_t* occ_bits, npvs_grid g, in
     }
     launch_il_count(p, nb, counts, st);
     NPVS_TRY(check_launch("il_count_kernel"));
+    if (nb <= kFusedScanCtas) {  // the write kernel sums the counts before each CTA itself
+        launch_il_write(p, nb, nullptr, counts, coords, feats, table, status, n_active, st);
+        return check_launch("il_write_kernel");
+    }
     NPVS_TRY(scan_block_counts(counts, offs, nb, n_active, capacity, status, st));
-    launch_il_write(p, nb, offs, coords, feats, table, status, n_active, st);
+    launch_il_write(p, nb, offs, counts, coords, feats, table, status, n_active, st);
     return check_launch("il_write_kernel");
 }
 
@@ -494,7 +524,11 @@ extern "C" npvs_status npvs_interleave_noalloc(const uint32_t* occ_bits, npvs_gr
     int* offs = scratch + kNoAllocMaxCtas + 1;  // likewise
     launch_il_count(p, nb, counts, st);
     NPVS_TRY(check_launch("il_count_kernel"));
+    if (nb <= kFusedScanCtas) {  // the write kernel sums the counts before each CTA itself
+        launch_il_write(p, nb, nullptr, counts, coords, feats, table, status, n_active, st);
+        return check_launch("il_write_kernel");
+    }
     NPVS_TRY(scan_block_counts(counts, offs, nb, n_active, capacity, status, st));
-    launch_il_write(p, nb, offs, coords, feats, table, status, n_active, st);
+    launch_il_write(p, nb, offs, counts, coords, feats, table, status, n_active, st);
     return check_launch("il_write_kernel");
 }
