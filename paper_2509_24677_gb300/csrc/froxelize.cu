@@ -443,6 +443,7 @@ __global__ void __launch_bounds__(kItemsBlock, 4) froxel_items_kernel(
     const long long* boff = nullptr;
     long long total;
     if (block_sum) {
+        static_assert((kFusedFaceMax / kSetupBlock) % kItemsBlock == 0, "block totals split evenly over threads");
         constexpr int kPer = kFusedFaceMax / kSetupBlock / kItemsBlock;
         const int nbs = (n_faces + kSetupBlock - 1) / kSetupBlock;
         long long v[kPer], sum = 0;
