@@ -125,6 +125,21 @@ def test_froxelize_city256_whole_frame_bit_exact(vc_index, height, s):
     assert popcount(got ^ ref) == 0
 
 
+def test_froxelize_more_faces_than_the_fused_offsets_bit_exact():
+    """A batch of two viewcells of the 12,000-building city (144,012 faces, more than the 65,536 whose
+    offsets the item kernel adds itself): the chunked scan path, bit for bit against the oracle."""
+    p = dataclasses.replace(I.CityParams(), n_buildings=12000, mu=2.3, sigma=0.7)
+    boxes = I.city_boxes(2, p)
+    vcs = I.city_viewcells(2, 2, p, height=(2.0, 60.0))
+    W, H, D, s = 32, 32, 16, 2
+    assert 2 * 6 * len(boxes) > 65536
+    got = gpu_froxelize([boxes, boxes], vcs, W, H, D, s)
+    for b in range(2):
+        ref = ofx.froxelize(ocam.frustum(vcs[b], D), boxes, W, H, D, s)
+        assert popcount(ref) > 100
+        assert popcount(got[b] ^ ref) == 0, b
+
+
 # ------------------------------------------------------------------------------------------
 # a3 interleave, a7 de-interleave
 # ------------------------------------------------------------------------------------------

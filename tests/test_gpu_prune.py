@@ -41,6 +41,23 @@ def gpu_prune(scenes, vcs, W, H, D, s, pvs):
     return vis[:len(boxes)].cpu().numpy(), boxes
 
 
+def test_prune_more_faces_than_the_fused_offsets():
+    """The 12,000-building city (72,006 faces, more than the 65,536 whose offsets the item kernel adds
+    itself) against a random 5 % subset of its G: the chunked scan path, box by box."""
+    p = dataclasses.replace(I.CityParams(), n_buildings=12000, mu=2.3, sigma=0.7)
+    boxes = I.city_boxes(2, p)
+    vc = I.city_viewcells(2, 1, p, height=(2.0, 60.0))[0]
+    W, H, D, s = 32, 32, 16, 2
+    cam = ocam.frustum(vc, D)
+    G = ofx.froxelize(cam, boxes, W, H, D, s)
+    rng = np.random.default_rng(5)
+    pvs = oil.pack_bits(oil.unpack_bits(G, W) & (rng.random((D, H, W)) < 0.05))
+    ref = ofx.prune(cam, boxes, W, H, D, s, pvs)
+    got, _ = gpu_prune([boxes], [vc], W, H, D, s, pvs[None])
+    assert 6 * len(boxes) > 65536 and 0 < int(ref.sum()) < len(boxes)
+    np.testing.assert_array_equal(got, ref)
+
+
 def test_prune_plain64_bit_exact():
     boxes, vc = I.plain64_scene()
     W, H, D, s = 64, 64, 32, 8
