@@ -192,6 +192,39 @@ def test_interleave_bit_exact(d, in_ch, dt):
     np.testing.assert_array_equal(got, exp)
 
 
+@pytest.mark.parametrize("cap_frac", [1.0, 0.5])
+def test_interleave_large_grid_scan_path(cap_frac):
+    """524,288 coarse sites at d = 1 (2,048 CTAs, more than the 1,024 whose offsets the write kernel
+    sums itself): the single-CTA scan path, bit-exact against the oracle; with half the needed
+    capacity, the capacity status and the clamped row count."""
+    L, ops, _ = lib()
+    rng = np.random.default_rng(11)
+    B, D, H, W = 1, 64, 64, 128
+    occ = clustered_bits(rng, B, D, H, W, frac=0.03)
+    bits = oil.pack_bits(occ)
+    coords_ref, feats_ref, active = oil.interleave(bits, W, 1, 2)
+    N = len(coords_ref)
+    cap = max(1, int(cap_frac * N))
+    g = ops.grid(W, H, D, B)
+    coords = torch.zeros(cap, 4, dtype=torch.int32, device=DEV)
+    feats = torch.zeros(cap, 2, dtype=torch.float32, device=DEV)
+    n = torch.zeros(1, dtype=torch.int32, device=DEV)
+    table = torch.zeros(active.size, dtype=torch.int32, device=DEV)
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+    ops.npvs_interleave(torch.from_numpy(bits.view(np.int32)).to(DEV), g, 1, 2, L.F32, cap, coords, feats, n,
+                        table=table, status=status)
+    st = ops.npvs_check_status(status)
+    m = min(cap, N)
+    assert int(n.item()) == m
+    assert st == (0 if cap >= N else L.ERR_CAPACITY)
+    np.testing.assert_array_equal(coords.cpu().numpy()[:m], coords_ref[:m])
+    np.testing.assert_array_equal(feats.cpu().numpy()[:m], feats_ref[:m].astype(np.float32))
+    exp_table = np.full(active.size, -1)
+    idx = np.flatnonzero(active.ravel())[:m]
+    exp_table[idx] = np.arange(m)
+    np.testing.assert_array_equal(table.cpu().numpy(), exp_table)
+
+
 def test_interleave_empty_full_and_overflow():
     L, ops, _ = lib()
     d, B, D, H, W = 4, 1, 8, 8, 32
