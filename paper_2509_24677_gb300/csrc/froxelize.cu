@@ -124,7 +124,7 @@ __device__ __forceinline__ int face_record(const float* __restrict__ boxes, cons
 // One thread per face (64-thread blocks: the set-up is latency bound, so it is spread over as many
 // SMs as the faces allow): the face record, its column count, the exclusive prefix of the counts
 // within the block (offs) and the block's total (block_sum); it also clears the item kernel's work
-// counter. Threads f < sW + sH also write the
+// counter and, when given, the n_zero words of the output bit grid. Threads f < sW + sH also write the
 // normalised pixel centre f of the supersampled raster, n = (2a + 1 - S) / S in one binary32
 // division: xs[a] for a < sW, then ys[b].
 constexpr int kSetupBlock = 64;
@@ -133,11 +133,13 @@ __global__ void __launch_bounds__(kSetupBlock) face_setup_kernel(
     const float* __restrict__ boxes, const int32_t* __restrict__ box_off, int n_boxes,
     const npvs_camera* __restrict__ cams, npvs_grid g, int s, FaceRec* __restrict__ faces, int* __restrict__ counts,
     long long* __restrict__ offs, long long* __restrict__ block_sum, float* __restrict__ xs,
-    unsigned long long* __restrict__ work) {
+    unsigned long long* __restrict__ work, uint32_t* __restrict__ zero_words, long long n_zero) {
     __shared__ long long warp_sum[kSetupBlock / 32];
     pdl_begin();
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f == 0) *work = 0ull;  // the item kernel's work counter
+    // the bit grid the item kernel ORs into (froxelization only), cleared here
+    for (long long w = f; w < n_zero; w += (long long)gridDim.x * blockDim.x) zero_words[w] = 0u;
     {
         const int sW = s * g.W, sH = s * g.H;
         if (f < sW) xs[f] = __fdiv_rn((float)(2 * f + 1 - sW), (float)sW);
@@ -621,7 +623,8 @@ static npvs_status froxel_run(const float* boxes, const int32_t* box_offsets, in
     long long* block_sum = ar.take<long long>((size_t)ceil_div(setup_threads, kSetupBlock));
     float* centres = ar.take<float>((size_t)s * g.W + (size_t)s * g.H);
     launch_k(face_setup_kernel, ceil_div(setup_threads, kSetupBlock), kSetupBlock, 0, st, boxes, box_offsets, n_boxes,
-             cams, g, (int)s, faces, counts, offs, block_sum, centres, work);
+             cams, g, (int)s, faces, counts, offs, block_sum, centres, work, bits,
+             bits ? (long long)g.B * g.D * g.H * (g.W / 32) : 0ll);
     NPVS_TRY(check_launch("face_setup_kernel"));
     const bool fused = F <= kFusedFaceMax;  // the item kernel adds the block offsets itself
     if (!fused) {  // the offsets again from the counts, by chunks
@@ -661,8 +664,10 @@ extern "C" npvs_status npvs_froxelize(const float* boxes, const int32_t* box_off
     NPVS_REQUIRE(g.W > 0 && g.H > 0 && g.D > 0 && g.B > 0 && g.W % 32 == 0, NPVS_ERR_UNSUPPORTED,
                  "npvs_froxelize: need W % 32 == 0 and positive sizes");
     cudaStream_t st = as_stream(stream);
-    const size_t nbytes = (size_t)g.B * g.D * g.H * (g.W / 32) * sizeof(uint32_t);
-    if (cudaMemsetAsync(occ_bits, 0, nbytes, st) != cudaSuccess) return check_launch("npvs_froxelize memset");
+    if (n_boxes == 0) {  // no face set-up kernel runs to clear the grid
+        const size_t nbytes = (size_t)g.B * g.D * g.H * (g.W / 32) * sizeof(uint32_t);
+        if (cudaMemsetAsync(occ_bits, 0, nbytes, st) != cudaSuccess) return check_launch("npvs_froxelize memset");
+    }
     return froxel_run(boxes, box_offsets, n_boxes, cams, g, s, occ_bits, nullptr, nullptr, workspace, workspace_bytes,
                       st, "npvs_froxelize");
 }
