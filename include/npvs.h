@@ -239,7 +239,8 @@ size_t npvs_froxelize_workspace_bytes(int32_t n_boxes);
  *  boxes: device float [n_boxes][6] (min xyz, max xyz); box_offsets: device int32 [B+1], element
  *  e owns boxes [box_offsets[e], box_offsets[e+1]); cams: device npvs_camera [B] with
  *  n_slices == grid.D; occ_bits: device, zeroed and written here.
- *  Errors: W % 32 != 0, D > NPVS_MAX_SLICES, s < 1, s*W or s*H > 65536, workspace too small. */
+ *  Errors: W % 32 != 0, D > NPVS_MAX_SLICES, s < 1 or s > 16, s*W or s*H > 65536, workspace too
+ *  small. */
 npvs_status npvs_froxelize(const float* boxes, const int32_t* box_offsets, int32_t n_boxes,
                            const npvs_camera* cams, npvs_grid grid, int32_t supersample,
                            uint32_t* occ_bits, void* workspace, size_t workspace_bytes, void* stream);
